@@ -1,0 +1,27 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def tiny():
+    from paper_2503_01074_gb300 import scenes
+    mesh, mu = scenes.tiny_scene()
+    return mesh, mu
+
+
+@pytest.fixture(scope="session")
+def single_scene():
+    from paper_2503_01074_gb300 import scenes
+    mesh, mu, hfn = scenes.single_frame_scene()
+    return mesh, mu, hfn
