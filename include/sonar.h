@@ -1,0 +1,292 @@
+/*
+ * sonar.h -- C ABI of libsonar: forward-looking imaging-sonar rendering on one
+ * GB300 (sm_103a).
+ *
+ * Method: OceanSim (arXiv 2503.01074), Sec. III-A-2.  Each (beam, elevation)
+ * sample of the sonar field of view casts one ray into a triangle scene; a
+ * return scores mu[m] * cos * exp(-2 alpha r) * gain (Eq. 2 in its two-way
+ * form: the paper's alpha equals 2 alpha here); returns are summed into a
+ * range x azimuth polar grid; additive Rayleigh and multiplicative Gaussian
+ * noise are applied per bin (Eq. 3-6); each range row is normalised
+ * (range-wise normalisation, end of Sec. III-A-2); the polar image is
+ * resampled into a Cartesian fan image (the "plot styles" of the same
+ * paragraph).  The gradient entry points are an addition: the analytic
+ * adjoint of that pipeline with respect to (alpha, gain, mu).
+ *
+ * Conventions for every entry point
+ *  - Pointers named d_* are DEVICE pointers on the context's GPU, owned by
+ *    the caller and borrowed for the call; all others are host pointers read
+ *    before the call returns.
+ *  - Every call that takes a stream only enqueues work on it (cudaStream_t
+ *    passed as void*; 0 = the legacy default stream); outputs are valid once
+ *    that stream has reached the call.  No call aborts, traps or prints.
+ *  - Argument errors are detected on the host before anything is enqueued and
+ *    return SONAR_ERR_ARG; sonar_last_error() then holds a message.
+ *  - Kernels that detect a fault (a traversal stack overflow, a wait that
+ *    timed out, an index out of range) set a sticky device error word instead
+ *    of trapping; sonar_check(ctx) synchronises and reports it as
+ *    SONAR_ERR_DEVICE, then clears it.
+ *  - A context is used by one host thread at a time.
+ *
+ * World frame: z up.  Sensor frame: +y forward, +x right, +z up.  Ray (i, j)
+ * of beam i in [0, n_beams) and elevation j in [0, n_elev) has azimuth
+ * phi_i = -hfov/2 + (i + 1/2) hfov / n_beams and elevation
+ * theta_j = -vfov/2 + (j + 1/2) vfov / n_elev; its sensor-frame direction is
+ * (sin phi cos theta, cos phi cos theta, sin theta), rotated by `rot`.  The
+ * canonical ray index is k = i * n_elev + j.
+ */
+#ifndef SONAR_H
+#define SONAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sonar_ctx* sonar_ctx_t;
+typedef struct sonar_batch* sonar_batch_t;
+
+typedef enum {
+    SONAR_OK = 0,
+    SONAR_ERR_ARG = 1,      /* invalid argument; nothing was enqueued */
+    SONAR_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    SONAR_ERR_OOM = 3,      /* device allocation failed */
+    SONAR_ERR_TIMEOUT = 4,  /* a bounded device wait gave up */
+    SONAR_ERR_DEVICE = 5,   /* the sticky device error word was set */
+    SONAR_ERR_STATE = 6     /* call not valid in the object's current state */
+} sonar_status;
+
+/* Sticky device error bits (sonar_check reports their OR in *bits). */
+#define SONAR_DEVERR_STACK 0x1u    /* BVH traversal stack overflow */
+#define SONAR_DEVERR_INDEX 0x2u    /* an index read from memory was out of range */
+#define SONAR_DEVERR_TIMEOUT 0x4u  /* a bounded spin-wait ran out */
+
+/* Sonar geometry and pose.  rot is the sensor->world rotation, row-major:
+ * d_world[a] = sum_b rot[3a + b] d_sensor[b].  hfov, vfov in radians, in
+ * (0, pi]; 0 <= r_min < r_max in metres.  Range bin b_r covers
+ * [r_min + b_r dr, r_min + (b_r + 1) dr), dr = (r_max - r_min) / n_range_bins;
+ * azimuth bin b_a covers [-hfov/2 + b_a da, -hfov/2 + (b_a + 1) da),
+ * da = hfov / n_az_bins.  Ray (i, j) falls into azimuth bin
+ * floor((2i + 1) n_az_bins / (2 n_beams)). */
+typedef struct {
+    float pos[3];
+    float rot[9];
+    int32_t n_beams, n_elev, n_range_bins, n_az_bins;
+    float hfov, vfov;
+    float r_min, r_max;
+} sonar_sensor;
+
+/* Non-differentiable configuration. */
+typedef struct {
+    float sigma_sa;      /* Rayleigh scale of the additive noise (Eq. 3-4), >= 0 */
+    float sigma_sm;      /* std deviation of the multiplicative noise (Eq. 5-6), >= 0 */
+    float sigma_phi;     /* beam-pattern width in Eq. 3 (rad^2), > 0 */
+    int32_t normalise;   /* 0 none, 1 range-row maximum (default), 2 global maximum */
+    int32_t two_sided;   /* 1: incidence factor |d.n| (default); 0: max(0, -d.n) */
+    int32_t clip_tmax;   /* 1: only hits with r < r_max count; 0: trace to infinity */
+    int32_t accumulate;  /* 0: deterministic sort-by-bin segmented fold (default);
+                            1: warp-aggregated shared-memory atomics */
+    int32_t reserved;
+} sonar_params;
+
+/* Per-ray hit record, 16 bytes, indexed by the canonical ray index.
+ * key = b_r * n_az_bins + b_a, or 0xFFFFFFFF if the return is not binned
+ * (miss, or r outside [r_min, r_max)); tri = the caller's triangle index, or
+ * 0xFFFFFFFF on a miss; r = hit range in metres (+inf on a miss);
+ * cos = the incidence factor used in the score (0 on a miss). */
+typedef struct {
+    uint32_t key;
+    uint32_t tri;
+    float r;
+    float cos;
+} sonar_hit;
+
+/* Outputs of one render.  polar is required; the rest may be NULL.
+ *   polar   [n_range_bins][n_az_bins] f32: the normalised image N
+ *   noised  [n_range_bins][n_az_bins] f32: I~ after Eq. 5, before normalisation
+ *           (the backward pass needs it)
+ *   binned  [n_range_bins][n_az_bins] f32: P, the summed intensities before noise
+ *   hits    [n_beams * n_elev] sonar_hit
+ *   fan     [fan_h][fan_w] f32 (row 0 = far edge), requires fan_w, fan_h > 0 */
+typedef struct {
+    float* polar;
+    float* noised;
+    float* binned;
+    sonar_hit* hits;
+    float* fan;
+    int32_t fan_w, fan_h;
+} sonar_outputs;
+
+/* Library version and build information (static string). */
+const char* sonar_version(void);
+
+/* Creates a context on CUDA device `device` (which becomes current for the
+ * calling thread).  *out receives the handle. */
+sonar_status sonar_create(int32_t device, sonar_ctx_t* out);
+
+/* Synchronises the device, frees every scene, batch and scratch buffer the
+ * context owns.  NULL is accepted. */
+sonar_status sonar_destroy(sonar_ctx_t ctx);
+
+/* Message describing the last failed call on this context (static storage
+ * owned by the context; "" if none).  ctx may be NULL for creation errors. */
+const char* sonar_last_error(sonar_ctx_t ctx);
+
+/* Synchronises the device and reports the sticky device error word:
+ * SONAR_ERR_DEVICE if any bit was set (bits in *bits if non-NULL), after
+ * which the word is cleared. */
+sonar_status sonar_check(sonar_ctx_t ctx, uint32_t* bits);
+
+/* Builds the scene's bounding-volume hierarchy (the geometry query of
+ * Sec. III-A-2: Morton codes, radix sort, Karras hierarchy, bottom-up box
+ * refit, node packing).  d_verts [n_verts][3] f32, d_tris [n_tris][3] int32
+ * vertex indices, d_mat [n_tris] int32 material ids >= 0 (the reflectivity
+ * A_r of Eq. 2 per semantic class).  The inputs are read during the call and
+ * not retained.  Validates indices and vertex finiteness (synchronises the
+ * stream once).  n_tris may be 0 (every ray misses) and must be < 2^28 - 2.
+ * *scene_id receives the handle used by the render calls. */
+sonar_status sonar_scene_upload(sonar_ctx_t ctx, const float* d_verts, int64_t n_verts,
+                                const int32_t* d_tris, const int32_t* d_mat, int64_t n_tris,
+                                void* stream, int32_t* scene_id);
+
+/* Releases a scene (synchronises the device first). */
+sonar_status sonar_scene_release(sonar_ctx_t ctx, int32_t scene_id);
+
+/* Scene statistics: out[0] triangles, out[1] internal nodes, out[2] tree
+ * height, out[3] maximum material id, out[4] device bytes held. */
+sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t scene_id, int64_t out[5]);
+
+/* One sonar frame (Sec. III-A-2): ray cast, intensity (Eq. 2), polar
+ * binning, noise (Eq. 3-6) with Philox4x32-10 keyed by `seed`, counter
+ * (bin, frame lo32, 0, frame hi32), range-wise normalisation and, if
+ * out->fan is set, the fan image.
+ * d_theta [2 + n_mat] f32 = (alpha, gain, mu[0], ..., mu[n_mat - 1]);
+ * n_mat must exceed the scene's largest material id, 1 <= n_mat <= 1024. */
+sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                          const sonar_params* params, const float* d_theta, int32_t n_mat,
+                          uint64_t seed, uint64_t frame, const sonar_outputs* out,
+                          void* stream);
+
+/* Resamples any polar image d_polar [n_range_bins][n_az_bins] into a fan
+ * image d_fan [fan_h][fan_w]: square pixels, sensor at the bottom centre,
+ * scale = min(fan_w / (2 r_max sin(hfov/2)), fan_h / r_max) pixels per metre;
+ * bilinear over bin centres, clamped to the edge bins; 0 outside the fan. */
+sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* sensor,
+                                const float* d_polar, int32_t fan_w, int32_t fan_h,
+                                float* d_fan, void* stream);
+
+/* Adjoint of sonar_render.  d_grad_polar = dL/dN [n_range_bins][n_az_bins];
+ * d_noised = the I~ that sonar_render wrote for the same (scene, sensor,
+ * params, theta, seed, frame); d_hits = that render's hit records, or NULL to
+ * recompute them by re-casting the rays (bitwise the same records).
+ * Writes d_dtheta [2 + n_mat] f32 = (dL/dalpha, dL/dgain, dL/dmu[...]),
+ * overwriting it.  Deterministic: the same inputs give the same bits. */
+sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
+                                   const sonar_sensor* sensor, const sonar_params* params,
+                                   const float* d_theta, int32_t n_mat, uint64_t seed,
+                                   uint64_t frame, const float* d_grad_polar,
+                                   const float* d_noised, const sonar_hit* d_hits,
+                                   float* d_dtheta, void* stream);
+
+/* ---- batched rendering: many sensors, several scenes, one persistent launch ---- */
+
+/* One sensor of a batch.  Offsets are element offsets into the packed output
+ * buffers passed to sonar_render_batch (polar/noised/binned share
+ * polar_offset; hits use hits_offset; the fan uses fan_offset).  fan_w,
+ * fan_h = 0 skips the fan for this sensor. */
+typedef struct {
+    int32_t scene_id;
+    int32_t fan_w, fan_h;
+    int32_t reserved;
+    sonar_sensor sensor;
+    uint64_t seed, frame;
+    int64_t polar_offset, hits_offset, fan_offset;
+} sonar_batch_item;
+
+/* Packed outputs of a batch; as sonar_outputs, with per-item offsets.
+ * polar is required; others may be NULL (fan is skipped for every item if
+ * NULL). */
+typedef struct {
+    float* polar;
+    float* noised;
+    float* binned;
+    sonar_hit* hits;
+    float* fan;
+} sonar_batch_outputs;
+
+/* Plans a batch: validates the items, splits every sensor into work units of
+ * whole azimuth columns (shapes from the autotuner's cache when it has an
+ * entry for the sensor shape, defaults otherwise), orders the units
+ * largest-first for the persistent launch, and uploads the descriptors
+ * (synchronous).  n_items >= 1. */
+sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_item* items,
+                                int32_t n_items, sonar_batch_t* out);
+
+/* Replaces poses, seeds and frames (and scene ids) of a planned batch.  Item
+ * count, shapes and offsets must match the plan.  Enqueued on `stream` from
+ * host staging memory owned by the batch; `items` may be reused at once. */
+sonar_status sonar_batch_update(sonar_batch_t batch, const sonar_batch_item* items,
+                                int32_t n_items, void* stream);
+
+/* Renders every item of the batch: one persistent launch traces, bins and
+ * adds noise for all work units (dynamic work list), a second normalises and
+ * resamples every fan.  The first call for a given (params, theta, outputs)
+ * captures the launches in a CUDA graph; later calls with the same arguments
+ * replay it.  Results per item equal sonar_render's for the same item and
+ * tile shape (bitwise, in deterministic accumulation). */
+sonar_status sonar_render_batch(sonar_batch_t batch, const sonar_params* params,
+                                const float* d_theta, int32_t n_mat,
+                                const sonar_batch_outputs* out, void* stream);
+
+/* Adjoint of sonar_render_batch for the loss summed over items: d_grad_polar
+ * and d_noised packed like the polar output, d_hits packed like the hit
+ * output or NULL (recompute).  Writes d_dtheta [2 + n_mat], the gradient
+ * summed over items.  Graph-captured like the forward. */
+sonar_status sonar_render_batch_backward(sonar_batch_t batch, const sonar_params* params,
+                                         const float* d_theta, int32_t n_mat,
+                                         const float* d_grad_polar, const float* d_noised,
+                                         const sonar_hit* d_hits, float* d_dtheta,
+                                         void* stream);
+
+/* Plan statistics: out[0] work units, out[1] total rays, out[2] persistent
+ * grid size, out[3] block size, out[4] graphs captured so far. */
+sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
+
+sonar_status sonar_batch_destroy(sonar_batch_t batch);
+
+/* ---- autotuner ---- */
+
+/* Times candidate tile shapes (columns per work unit, ray-to-lane mapping,
+ * block size) on the batch's own sensors and records the fastest per sensor
+ * shape (n_beams, n_elev, n_range_bins, n_az_bins) in the context's tuning
+ * cache; later sonar_batch_create and sonar_render calls use it.  Runs
+ * renders on `stream` and synchronises it.  Outputs of `out` are
+ * overwritten. */
+sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
+                            const float* d_theta, int32_t n_mat,
+                            const sonar_batch_outputs* out, void* stream);
+
+/* Tuning cache entries: writes up to `cap` rows of 8 int32
+ * (n_beams, n_elev, n_range_bins, n_az_bins, cols, mapping, block, reserved)
+ * and returns the number of entries in *count. */
+sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count);
+
+/* Adds or replaces cache entries (rows as above), e.g. loaded from a file. */
+sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int32_t count);
+
+/* ---- counters (roofline evidence) ---- */
+
+/* Re-casts the rays of one sensor and counts, per ray, BVH node pairs
+ * visited and triangles tested; also marks every node pair and triangle
+ * touched.  out[0] node-pair visits, out[1] triangle tests, out[2] distinct
+ * node pairs touched, out[3] distinct triangles touched, out[4] rays,
+ * out[5] triangle tests resolved in FP64.  Synchronises the stream. */
+sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                               const sonar_params* params, void* stream, int64_t out[6]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SONAR_H */

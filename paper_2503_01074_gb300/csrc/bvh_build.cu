@@ -1,0 +1,537 @@
+// LBVH construction for the sonar geometry query (OceanSim Sec. III-A-2:
+// the scene is queried by ray casting; this builds the acceleration structure).
+//
+//   1. validate + centroid bounds     one thread per triangle, block-reduced atomics
+//   2. Morton codes                   63-bit keys (21 bits per axis) of triangle centroids
+//   3. radix sort                     stable LSD, 8-bit digits, histogram / scan / scatter
+//   4. Karras hierarchy               one thread per internal node (Karras, HPG 2012)
+//   5. bottom-up refit                leaf-to-root climb, second visitor merges boxes
+//   6. packing                        64-byte child-pair nodes, runs of <= kLeafMax
+//                                     triangles collapsed into leaves, 48-byte triangles
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sonar_internal.cuh"
+#include "sonar_host.h"
+
+namespace sonar {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kThreads * kRsItems;   // keys per sort block
+
+// ---------------------------------------------------------------------------
+// 1. validation and centroid bounds
+// ---------------------------------------------------------------------------
+
+struct BuildStats {
+    uint32_t flags;        // 1: index out of range, 2: negative material, 4: non-finite vertex
+    int32_t max_mat;
+    uint32_t lo[3], hi[3]; // ordered-encoded centroid bounds
+};
+
+__device__ __forceinline__ float3 load_v(const float* v, int32_t i) {
+    return make_float3(v[3 * (int64_t)i], v[3 * (int64_t)i + 1], v[3 * (int64_t)i + 2]);
+}
+
+__global__ void k_validate(const float* verts, int64_t nv, const int32_t* tris, const int32_t* mat,
+                           int64_t nt, BuildStats* st) {
+    __shared__ uint32_t s_lo[3], s_hi[3], s_flags;
+    __shared__ int32_t s_mat;
+    if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0xFFFFFFFFu; s_hi[threadIdx.x] = 0u; }
+    if (threadIdx.x == 0) { s_flags = 0; s_mat = -1; }
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) {
+        const int32_t a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        uint32_t f = 0;
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) f |= 1u;
+        const int32_t m = mat[t];
+        if (m < 0) f |= 2u;
+        if (!f) {
+            const float3 p = load_v(verts, a), q = load_v(verts, b), r = load_v(verts, c);
+            const bool fin = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(q.x) &&
+                             isfinite(q.y) && isfinite(q.z) && isfinite(r.x) && isfinite(r.y) &&
+                             isfinite(r.z);
+            if (!fin) {
+                f |= 4u;
+            } else {
+                const float cx = (p.x + q.x + r.x) * (1.0f / 3.0f);
+                const float cy = (p.y + q.y + r.y) * (1.0f / 3.0f);
+                const float cz = (p.z + q.z + r.z) * (1.0f / 3.0f);
+                atomicMin(&s_lo[0], ord_enc(cx)); atomicMax(&s_hi[0], ord_enc(cx));
+                atomicMin(&s_lo[1], ord_enc(cy)); atomicMax(&s_hi[1], ord_enc(cy));
+                atomicMin(&s_lo[2], ord_enc(cz)); atomicMax(&s_hi[2], ord_enc(cz));
+            }
+        }
+        if (f) atomicOr(&s_flags, f);
+        atomicMax(&s_mat, m);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        atomicMin(&st->lo[threadIdx.x], s_lo[threadIdx.x]);
+        atomicMax(&st->hi[threadIdx.x], s_hi[threadIdx.x]);
+    }
+    if (threadIdx.x == 0) {
+        if (s_flags) atomicOr(&st->flags, s_flags);
+        atomicMax(&st->max_mat, s_mat);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Morton codes
+// ---------------------------------------------------------------------------
+
+__global__ void k_morton(const float* verts, const int32_t* tris, int64_t nt, const BuildStats* st,
+                         uint64_t* keys, uint32_t* vals) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const float3 p = load_v(verts, tris[3 * t]), q = load_v(verts, tris[3 * t + 1]),
+                 r = load_v(verts, tris[3 * t + 2]);
+    const float c[3] = {(p.x + q.x + r.x) * (1.0f / 3.0f), (p.y + q.y + r.y) * (1.0f / 3.0f),
+                        (p.z + q.z + r.z) * (1.0f / 3.0f)};
+    uint32_t g[3];
+    for (int a = 0; a < 3; ++a) {
+        const float lo = ord_dec(st->lo[a]), hi = ord_dec(st->hi[a]);
+        const float ext = hi - lo;
+        float u = ext > 0.0f ? (c[a] - lo) / ext : 0.0f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        g[a] = (uint32_t)fminf(u * 2097152.0f, 2097151.0f);    // 21 bits
+    }
+    uint64_t key = 0;
+    for (int b = 20; b >= 0; --b) {
+        key = (key << 3) | ((uint64_t)((g[0] >> b) & 1u) << 2) | ((uint64_t)((g[1] >> b) & 1u) << 1) |
+              (uint64_t)((g[2] >> b) & 1u);
+    }
+    keys[t] = key;
+    vals[t] = (uint32_t)t;
+}
+
+// ---------------------------------------------------------------------------
+// 3. stable LSD radix sort (8-bit digits)
+// ---------------------------------------------------------------------------
+
+__global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, uint32_t* hist, int nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+    for (int k = 0; k < kRsItems; ++k) {
+        const int64_t i = base + k * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of a u32 array in three passes (chunk sums, scan of sums, apply).
+constexpr int kScanChunk = kThreads * 16;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[(blockDim.x >> 5) - 1];
+    const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_sums(const uint32_t* in, int64_t n, uint32_t* sums) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * 16;
+    uint32_t v = 0;
+    for (int k = 0; k < 16; ++k)
+        if (base + k < n) v += in[base + k];
+    uint32_t total;
+    block_exclusive_scan(v, s_warp, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_top(uint32_t* sums, int64_t n) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < n ? sums[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, s_warp, total);
+        const uint32_t carry = s_carry;
+        if (i < n) sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + total;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_apply(const uint32_t* in, int64_t n, const uint32_t* sums, uint32_t* out) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * 16;
+    uint32_t loc[16];
+    uint32_t v = 0;
+    for (int k = 0; k < 16; ++k) {
+        loc[k] = base + k < n ? in[base + k] : 0u;
+        v += loc[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(v, s_warp, total) + sums[blockIdx.x];
+    for (int k = 0; k < 16; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += loc[k];
+    }
+}
+
+// Stable scatter: rounds of 256 consecutive keys; within a round, rank =
+// (keys of the same digit in earlier warps) + (earlier lanes of this warp);
+// rounds advance a running per-digit offset.
+__global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                             int64_t n, int shift, const uint32_t* offs, int nblocks) {
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wc[kThreads / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    run[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    for (int w = 0; w < kThreads / 32; ++w) wc[w][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int k = 0; k < kRsItems; ++k) {
+        const int64_t i = base + k * kThreads + threadIdx.x;
+        const bool ok = i < n;
+        const uint64_t key = ok ? kin[i] : 0ull;
+        const uint32_t val = ok ? vin[i] : 0u;
+        const uint32_t digit = ok ? (uint32_t)((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
+        const uint32_t rank = __popc(peers & lt);
+        if (ok && rank == 0) wc[warp][digit] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t r = run[threadIdx.x];
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const uint32_t c = wc[w][threadIdx.x];
+                wc[w][threadIdx.x] = r;
+                r += c;
+            }
+            run[threadIdx.x] = r;
+        }
+        __syncthreads();
+        if (ok) {
+            const uint32_t pos = wc[warp][digit] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        for (int w = 0; w < kThreads / 32; ++w) wc[w][threadIdx.x] = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4. Karras hierarchy
+// ---------------------------------------------------------------------------
+
+// Length of the common prefix of keys i and j; equal keys are told apart by
+// their indices (64 + common prefix of i and j); -1 outside [0, n).
+__device__ __forceinline__ int delta(const uint64_t* k, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    const uint64_t a = k[i], b = k[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+// child[2p], child[2p+1]: internal c >= 0 or leaf ~c; parent[p] for internal
+// nodes, parent[n - 1 + i] for leaf i; range[p] = covered leaves [lo, hi].
+__global__ void k_karras(const uint64_t* keys, int64_t n, int32_t* child, int32_t* parent,
+                         int2* range) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = delta(keys, n, i, i + 1) > delta(keys, n, i, i - 1) ? 1 : -1;
+    const int dmin = delta(keys, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(keys, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    const int32_t left = lo == gamma ? ~(int32_t)gamma : (int32_t)gamma;
+    const int32_t right = hi == gamma + 1 ? ~(int32_t)(gamma + 1) : (int32_t)(gamma + 1);
+    child[2 * i] = left;
+    child[2 * i + 1] = right;
+    parent[left >= 0 ? left : (n - 1) + ~left] = (int32_t)i;
+    parent[right >= 0 ? right : (n - 1) + ~right] = (int32_t)i;
+    range[i] = make_int2((int)lo, (int)hi);
+    if (i == 0) parent[0] = -1;
+}
+
+// ---------------------------------------------------------------------------
+// 5. bottom-up refit
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tri_box(const float* verts, const int32_t* tris, uint32_t orig,
+                                        float3& lo, float3& hi) {
+    const float3 p = load_v(verts, tris[3 * (int64_t)orig]), q = load_v(verts, tris[3 * (int64_t)orig + 1]),
+                 r = load_v(verts, tris[3 * (int64_t)orig + 2]);
+    lo = make_float3(fminf(p.x, fminf(q.x, r.x)), fminf(p.y, fminf(q.y, r.y)), fminf(p.z, fminf(q.z, r.z)));
+    hi = make_float3(fmaxf(p.x, fmaxf(q.x, r.x)), fmaxf(p.y, fmaxf(q.y, r.y)), fmaxf(p.z, fmaxf(q.z, r.z)));
+}
+
+__device__ __forceinline__ void child_box(int32_t c, const float* verts, const int32_t* tris,
+                                          const uint32_t* vals, const float4* blo, const float4* bhi,
+                                          float3& lo, float3& hi, int& h) {
+    if (c < 0) {
+        tri_box(verts, tris, vals[~c], lo, hi);
+        h = 0;
+    } else {
+        const float4 a = __ldcg(blo + c), b = __ldcg(bhi + c);
+        lo = make_float3(a.x, a.y, a.z);
+        hi = make_float3(b.x, b.y, b.z);
+        h = __float_as_int(b.w);
+    }
+}
+
+__global__ void k_refit(const float* verts, const int32_t* tris, const uint32_t* vals, int64_t n,
+                        const int32_t* child, const int32_t* parent, int32_t* visits, float4* blo,
+                        float4* bhi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t p = parent[(n - 1) + i];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&visits[p], 1) == 0) return;   // the other child is still on its way
+        float3 l0, h0, l1, h1;
+        int e0, e1;
+        child_box(child[2 * p], verts, tris, vals, blo, bhi, l0, h0, e0);
+        child_box(child[2 * p + 1], verts, tris, vals, blo, bhi, l1, h1, e1);
+        const int h = 1 + (e0 > e1 ? e0 : e1);
+        __stcg(blo + p, make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.0f));
+        __stcg(bhi + p, make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), __int_as_float(h)));
+        __threadfence();
+        p = parent[p];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 6. packing
+// ---------------------------------------------------------------------------
+
+__global__ void k_pack_nodes(const float* verts, const int32_t* tris, const uint32_t* vals, int64_t n,
+                             const int32_t* child, const int2* range, const float4* blo,
+                             const float4* bhi, float pad, float4* nodes) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n - 1) return;
+    for (int side = 0; side < 2; ++side) {
+        const int32_t c = child[2 * p + side];
+        float3 lo, hi;
+        int32_t handle;
+        if (c < 0) {
+            tri_box(verts, tris, vals[~c], lo, hi);
+            handle = leaf_handle(~c, 1);
+        } else {
+            const float4 a = blo[c], b = bhi[c];
+            lo = make_float3(a.x, a.y, a.z);
+            hi = make_float3(b.x, b.y, b.z);
+            const int2 r = range[c];
+            const int cnt = r.y - r.x + 1;
+            handle = cnt <= kLeafMax ? leaf_handle(r.x, cnt) : c;
+        }
+        nodes[4 * p + 2 * side] = make_float4(lo.x - pad, lo.y - pad, lo.z - pad, __int_as_float(handle));
+        nodes[4 * p + 2 * side + 1] = make_float4(hi.x + pad, hi.y + pad, hi.z + pad, 0.0f);
+    }
+}
+
+__global__ void k_pack_tris(const float* verts, const int32_t* tris, const int32_t* mat,
+                            const uint32_t* vals, int64_t n, float4* out, int32_t* mat_orig) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t o = vals[k];
+    const float3 p = load_v(verts, tris[3 * (int64_t)o]), q = load_v(verts, tris[3 * (int64_t)o + 1]),
+                 r = load_v(verts, tris[3 * (int64_t)o + 2]);
+    const int32_t m = mat[o];
+    out[3 * k] = make_float4(p.x, p.y, p.z, __int_as_float(m));
+    out[3 * k + 1] = make_float4(q.x, q.y, q.z, __uint_as_float(o));
+    out[3 * k + 2] = make_float4(r.x, r.y, r.z, 0.0f);
+    mat_orig[o] = m;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// Temporary device buffers of one build, freed in stream order on exit.
+struct BuildScratch {
+    cudaStream_t st;
+    void* ptrs[16] = {};
+    int n = 0;
+    cudaError_t err = cudaSuccess;
+    template <class T>
+    T* get(size_t count) {
+        void* p = nullptr;
+        if (err == cudaSuccess) err = cudaMallocAsync(&p, count * sizeof(T) + 16, st);
+        if (err != cudaSuccess) return nullptr;
+        ptrs[n++] = p;
+        return (T*)p;
+    }
+    ~BuildScratch() {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], st);
+    }
+};
+
+sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, const int32_t* mat,
+                         int64_t nt, cudaStream_t st, SceneStore* out, std::string* msg) {
+    *out = SceneStore{};
+    out->n_tris = nt;
+    out->max_mat = -1;
+    if (nt == 0) {
+        out->root = kEmpty;
+        return SONAR_OK;
+    }
+    BuildScratch S{st};
+    BuildStats* d_stats = S.get<BuildStats>(1);
+    if (!d_stats) { *msg = "out of device memory (build statistics)"; return SONAR_ERR_OOM; }
+    BuildStats init{};
+    init.flags = 0;
+    init.max_mat = -1;
+    for (int a = 0; a < 3; ++a) { init.lo[a] = 0xFFFFFFFFu; init.hi[a] = 0u; }
+    if (cudaMemcpyAsync(d_stats, &init, sizeof init, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        *msg = "cudaMemcpyAsync failed"; return SONAR_ERR_CUDA;
+    }
+    k_validate<<<blocks_for(nt, kThreads), kThreads, 0, st>>>(verts, nv, tris, mat, nt, d_stats);
+    BuildStats hs{};
+    cudaError_t e = cudaMemcpyAsync(&hs, d_stats, sizeof hs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { *msg = std::string("validation failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
+    if (hs.flags & 1u) { *msg = "triangle vertex index out of range"; return SONAR_ERR_ARG; }
+    if (hs.flags & 2u) { *msg = "negative material id"; return SONAR_ERR_ARG; }
+    if (hs.flags & 4u) { *msg = "non-finite vertex coordinate"; return SONAR_ERR_ARG; }
+    out->max_mat = hs.max_mat;
+
+    // box padding: covers the difference between the FP32 traversal ray and
+    // the exact ray, so that the FP32 box test never culls an exact hit
+    float ext = 0.0f, mag = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        const uint32_t lo = hs.lo[a], hi = hs.hi[a];
+        auto dec = [](uint32_t v) {
+            uint32_t b = (v & 0x80000000u) ? (v & 0x7FFFFFFFu) : ~v;
+            float f;
+            memcpy(&f, &b, 4);
+            return f;
+        };
+        const float l = dec(lo), h = dec(hi);
+        ext = fmaxf(ext, h - l);
+        mag = fmaxf(mag, fmaxf(fabsf(l), fabsf(h)));
+    }
+    const float pad = fmaxf(1e-5f * (ext + mag), 1e-6f);
+
+    const int64_t n = nt;
+    uint64_t* k0 = S.get<uint64_t>(n);
+    uint64_t* k1 = S.get<uint64_t>(n);
+    uint32_t* v0 = S.get<uint32_t>(n);
+    uint32_t* v1 = S.get<uint32_t>(n);
+    const int nblocks = (int)blocks_for(n, kRsTile);
+    const int64_t hn = 256ll * nblocks;
+    uint32_t* hist = S.get<uint32_t>(hn);
+    uint32_t* offs = S.get<uint32_t>(hn);
+    const int64_t nchunks = (hn + kScanChunk - 1) / kScanChunk;
+    uint32_t* sums = S.get<uint32_t>(nchunks);
+    int32_t* child = S.get<int32_t>(2 * n);
+    int32_t* parent = S.get<int32_t>(2 * n);
+    int2* range = S.get<int2>(n);
+    int32_t* visits = S.get<int32_t>(n);
+    float4* blo = S.get<float4>(n);
+    float4* bhi = S.get<float4>(n);
+    if (S.err != cudaSuccess) { *msg = "out of device memory (build scratch)"; return SONAR_ERR_OOM; }
+
+    k_morton<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, n, d_stats, k0, v0);
+    for (int shift = 0; shift < 63; shift += 8) {
+        k_rs_hist<<<nblocks, kThreads, 0, st>>>(k0, n, shift, hist, nblocks);
+        k_scan_sums<<<(unsigned)nchunks, kThreads, 0, st>>>(hist, hn, sums);
+        k_scan_top<<<1, 1024, 0, st>>>(sums, nchunks);
+        k_scan_apply<<<(unsigned)nchunks, kThreads, 0, st>>>(hist, hn, sums, offs);
+        k_rs_scatter<<<nblocks, kThreads, 0, st>>>(k0, v0, k1, v1, n, shift, offs, nblocks);
+        uint64_t* tk = k0; k0 = k1; k1 = tk;
+        uint32_t* tv = v0; v0 = v1; v1 = tv;
+    }
+
+    // persistent buffers
+    const int64_t n_pairs = n > 1 ? n - 1 : 1;
+    float4* nodes = nullptr;
+    float4* tri_out = nullptr;
+    int32_t* mat_orig = nullptr;
+    if (cudaMalloc(&nodes, sizeof(float4) * 4 * n_pairs) != cudaSuccess ||
+        cudaMalloc(&tri_out, sizeof(float4) * 3 * n) != cudaSuccess ||
+        cudaMalloc(&mat_orig, sizeof(int32_t) * n) != cudaSuccess) {
+        cudaFree(nodes); cudaFree(tri_out); cudaFree(mat_orig);
+        *msg = "out of device memory (scene)";
+        return SONAR_ERR_OOM;
+    }
+    out->nodes = nodes;
+    out->tris = tri_out;
+    out->mat_orig = mat_orig;
+    out->n_pairs = n > 1 ? n - 1 : 0;
+    out->bytes = sizeof(float4) * (4 * n_pairs + 3 * n) + sizeof(int32_t) * n;
+
+    k_pack_tris<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, mat, v0, n, tri_out, mat_orig);
+    int height = 0;
+    if (n == 1) {
+        out->root = leaf_handle(0, 1);
+    } else {
+        k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(k0, n, child, parent, range);
+        cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
+        k_refit<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, parent, visits,
+                                                               blo, bhi);
+        k_pack_nodes<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, range,
+                                                                        blo, bhi, pad, nodes);
+        float4 root_hi;
+        e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { *msg = std::string("build failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
+        memcpy(&height, &root_hi.w, 4);
+        out->root = n <= kLeafMax ? leaf_handle(0, (int32_t)n) : 0;
+    }
+    out->height = height;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { *msg = std::string("build kernel launch failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
+    if (height >= kStackMax) {
+        *msg = "hierarchy too deep for the traversal stack (height " + std::to_string(height) + ")";
+        return SONAR_ERR_ARG;
+    }
+    return SONAR_OK;
+}
+
+void free_scene(SceneStore* s) {
+    cudaFree(s->nodes);
+    cudaFree(s->tris);
+    cudaFree(s->mat_orig);
+    *s = SceneStore{};
+}
+
+}  // namespace sonar

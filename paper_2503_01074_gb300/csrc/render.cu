@@ -1,0 +1,880 @@
+// Sonar rendering kernels (OceanSim, arXiv 2503.01074, Sec. III-A-2).
+//
+// phase 1 (k_phase1)  one work unit = whole azimuth columns of one sensor:
+//                     ray generation -> closest hit (LBVH walk, Moller-Trumbore)
+//                     -> intensity (Eq. 2, two-way) -> polar binning into a
+//                     shared-memory column block -> Eq. 3-6 noise per bin ->
+//                     I~ to HBM + per-row maxima (ordered-int atomicMax).
+//                     Because a unit owns its columns, every polar bin is written
+//                     exactly once: no global atomics, no memset of the image.
+// phase 2 (k_phase2)  range-wise normalisation of every bin and the fan resample
+//                     of every pixel (bilinear over normalised bin centres).
+// adjoint             per-group (row) Jacobian terms, then a per-ray gather of
+//                     dL/dP into (dalpha, dgain, dmu), deterministic reduction.
+//
+// Ray casting precision: the walk and the triangle tests run in FP32.  A test
+// whose barycentric or distance outcome lies inside a certified FP32 error
+// bound, and any two candidates within 2e-5 t of each other, are re-decided in
+// FP64 against the exact ray (direction from FP64 trigonometry), so hit
+// decisions agree with an FP64 reference except for genuinely ambiguous rays.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "sonar_host.h"
+#include "sonar_internal.cuh"
+
+namespace sonar {
+namespace {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 sub(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float l1(float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); }
+
+// ---------------------------------------------------------------------------
+// rays
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float3 ray_dir32(const SensorDev& s, int i, int j) {
+    const float phi = fmaf((float)i + 0.5f, s.hfov / (float)s.nb, -0.5f * s.hfov);
+    const float th = fmaf((float)j + 0.5f, s.vfov / (float)s.ne, -0.5f * s.vfov);
+    float sp, cp, st, ct;
+    sincosf(phi, &sp, &cp);
+    sincosf(th, &st, &ct);
+    const float dx = sp * ct, dy = cp * ct, dz = st;
+    const float3 w = f3(fmaf(s.rot[0], dx, fmaf(s.rot[1], dy, s.rot[2] * dz)),
+                        fmaf(s.rot[3], dx, fmaf(s.rot[4], dy, s.rot[5] * dz)),
+                        fmaf(s.rot[6], dx, fmaf(s.rot[7], dy, s.rot[8] * dz)));
+    const float inv = 1.0f / sqrtf(dot3(w, w));
+    return f3(w.x * inv, w.y * inv, w.z * inv);
+}
+
+// The exact ray direction, computed as the definition states, in FP64.
+__device__ void ray_dir64(const SensorDev& s, int i, int j, double d[3]) {
+    const double H = s.hfov, V = s.vfov;
+    const double phi = -H / 2.0 + (i + 0.5) * H / s.nb;
+    const double th = -V / 2.0 + (j + 0.5) * V / s.ne;
+    double sp, cp, st, ct;
+    sincos(phi, &sp, &cp);
+    sincos(th, &st, &ct);
+    const double ds[3] = {sp * ct, cp * ct, st};
+    double w[3];
+    for (int a = 0; a < 3; ++a)
+        w[a] = (double)s.rot[3 * a] * ds[0] + (double)s.rot[3 * a + 1] * ds[1] + (double)s.rot[3 * a + 2] * ds[2];
+    const double n = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    d[0] = w[0] / n;
+    d[1] = w[1] / n;
+    d[2] = w[2] / n;
+}
+
+// ---------------------------------------------------------------------------
+// ray / triangle
+// ---------------------------------------------------------------------------
+
+// FP32 Moller-Trumbore with a certified error bound.  Returns 0 for a certain
+// miss, 1 for a certain hit (t set), 2 when FP32 cannot decide.  Each bound is
+// g * (product of the magnitudes entering the numerator) / |det|, g = 32 ulp,
+// which covers the rounding of the edge vectors, of the FP32 direction against
+// the exact one, and of the cross and dot products.
+__device__ __forceinline__ int mt32(float3 o, float3 d, float4 a, float4 b, float4 c, float& t) {
+    const float3 v0 = f3(a.x, a.y, a.z);
+    const float3 e1 = sub(f3(b.x, b.y, b.z), v0), e2 = sub(f3(c.x, c.y, c.z), v0);
+    const float3 p = cross3(d, e2);
+    const float det = dot3(e1, p);
+    const float3 s = sub(o, v0);
+    const float3 q = cross3(s, e1);
+    const float un = dot3(s, p), vn = dot3(d, q), tn = dot3(e2, q);
+    const float g = 0x1p-19f;
+    const float ad = l1(d), as = l1(s), ae1 = l1(e1), ae2 = l1(e2);
+    const float Edet = g * ae1 * ad * ae2;
+    const float adet = fabsf(det);
+    if (adet <= Edet) return 2;   // near-parallel: decided in FP64
+    const float inv = 1.0f / det;
+    const float u = un * inv, v = vn * inv, w = 1.0f - u - v;
+    t = tn * inv;
+    const float ia = 1.0f / adet;
+    const float eu = (g * as * ad * ae2 + fabsf(u) * Edet) * ia;
+    const float ev = (g * ad * as * ae1 + fabsf(v) * Edet) * ia;
+    const float ew = eu + ev + 0x1p-22f;
+    const float et = (g * ae2 * as * ae1 + fabsf(t) * Edet) * ia;
+    if (u < -eu || v < -ev || w < -ew || t < -et) return 0;
+    if (u > eu && v > ev && w > ew && t > et) return 1;
+    return 2;
+}
+
+// FP64 Moller-Trumbore on the exact ray: hit iff det != 0, u >= 0, v >= 0,
+// u + v <= 1, t > 0.
+__device__ bool mt64(const double o[3], const double d[3], float4 a, float4 b, float4 c, double& t) {
+    const double v0[3] = {a.x, a.y, a.z};
+    const double e1[3] = {(double)b.x - v0[0], (double)b.y - v0[1], (double)b.z - v0[2]};
+    const double e2[3] = {(double)c.x - v0[0], (double)c.y - v0[1], (double)c.z - v0[2]};
+    const double p[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
+    const double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+    if (det == 0.0) return false;
+    const double inv = 1.0 / det;
+    const double s[3] = {o[0] - v0[0], o[1] - v0[1], o[2] - v0[2]};
+    const double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) * inv;
+    if (u < 0.0 || u > 1.0) return false;
+    const double q[3] = {s[1] * e1[2] - s[2] * e1[1], s[2] * e1[0] - s[0] * e1[2], s[0] * e1[1] - s[1] * e1[0]};
+    const double v = (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]) * inv;
+    if (v < 0.0 || u + v > 1.0) return false;
+    const double tt = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * inv;
+    if (!(tt > 0.0)) return false;
+    t = tt;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// closest hit: LBVH walk with a short stack
+// ---------------------------------------------------------------------------
+
+struct Exact {
+    double o[3], d[3];
+    bool ready;
+};
+
+template <bool STATS>
+__device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int rj, float3 o,
+                             float3 d, float tlimit, float& t_out, uint32_t* err,
+                             const TraceCounters* tc) {
+    if (sc.root == kEmpty) return -1;
+    const float tiny = 1e-20f;
+    const float3 inv = f3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+                          1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+                          1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    int32_t stack[kStackMax];
+    int sp = 0;
+    int32_t node = sc.root;
+    int best = -1;
+    uint32_t best_id = 0xFFFFFFFFu;
+    float best_t = tlimit;
+    bool best_exact = false;
+    double best_t64 = 0.0;
+    Exact ex;
+    ex.ready = false;
+    uint64_t visits = 0, tests = 0, exact_n = 0;
+
+    for (;;) {
+        if (node >= 0) {
+            const float4* p = sc.nodes + 4 * (int64_t)node;
+            const float4 a0 = __ldg(p), b0 = __ldg(p + 1), a1 = __ldg(p + 2), b1 = __ldg(p + 3);
+            if (STATS) {
+                ++visits;
+                atomicOr(tc->node_bits + (node >> 5), 1u << (node & 31));
+            }
+            const float tcut = best_t * 1.00002f;
+            float t0 = fmaf(a0.x, inv.x, -oinv.x), t1 = fmaf(b0.x, inv.x, -oinv.x);
+            float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
+            t0 = fmaf(a0.y, inv.y, -oinv.y); t1 = fmaf(b0.y, inv.y, -oinv.y);
+            lo0 = fmaxf(lo0, fminf(t0, t1)); hi0 = fminf(hi0, fmaxf(t0, t1));
+            t0 = fmaf(a0.z, inv.z, -oinv.z); t1 = fmaf(b0.z, inv.z, -oinv.z);
+            lo0 = fmaxf(fmaxf(lo0, fminf(t0, t1)), 0.0f); hi0 = fminf(fminf(hi0, fmaxf(t0, t1)), tcut);
+            t0 = fmaf(a1.x, inv.x, -oinv.x); t1 = fmaf(b1.x, inv.x, -oinv.x);
+            float lo1 = fminf(t0, t1), hi1 = fmaxf(t0, t1);
+            t0 = fmaf(a1.y, inv.y, -oinv.y); t1 = fmaf(b1.y, inv.y, -oinv.y);
+            lo1 = fmaxf(lo1, fminf(t0, t1)); hi1 = fminf(hi1, fmaxf(t0, t1));
+            t0 = fmaf(a1.z, inv.z, -oinv.z); t1 = fmaf(b1.z, inv.z, -oinv.z);
+            lo1 = fmaxf(fmaxf(lo1, fminf(t0, t1)), 0.0f); hi1 = fminf(fminf(hi1, fmaxf(t0, t1)), tcut);
+            const bool h0 = lo0 <= hi0 * 1.0000005f, h1 = lo1 <= hi1 * 1.0000005f;
+            const int32_t c0 = __float_as_int(a0.w), c1 = __float_as_int(a1.w);
+            if (h0 && h1) {
+                if (sp >= kStackMax) {
+                    atomicOr(err, SONAR_DEVERR_STACK);
+                    best = -1;
+                    break;
+                }
+                const bool first0 = lo0 <= lo1;
+                stack[sp++] = first0 ? c1 : c0;
+                node = first0 ? c0 : c1;
+            } else if (h0) {
+                node = c0;
+            } else if (h1) {
+                node = c1;
+            } else {
+                if (sp == 0) break;
+                node = stack[--sp];
+            }
+            continue;
+        }
+        // leaf: a run of triangles in leaf order
+        const int32_t x = ~node;
+        const int32_t first = x >> 3, count = (x & 7) + 1;
+        for (int k = 0; k < count; ++k) {
+            const int32_t f = first + k;
+            if (f >= sc.n_tris) {
+                atomicOr(err, SONAR_DEVERR_INDEX);
+                break;
+            }
+            const float4* tp = sc.tris + 3 * (int64_t)f;
+            const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+            if (STATS) {
+                ++tests;
+                atomicOr(tc->tri_bits + (f >> 5), 1u << (f & 31));
+            }
+            float t;
+            const int r = mt32(o, d, a, b, c, t);
+            if (r == 0) continue;
+            bool exact = false;
+            double t64 = 0.0;
+            if (r == 2) {
+                if (!ex.ready) {
+                    ex.o[0] = s.pos[0]; ex.o[1] = s.pos[1]; ex.o[2] = s.pos[2];
+                    ray_dir64(s, ri, rj, ex.d);
+                    ex.ready = true;
+                }
+                if (STATS) ++exact_n;
+                if (!mt64(ex.o, ex.d, a, b, c, t64)) continue;
+                t = (float)t64;
+                exact = true;
+            }
+            if (!(t < tlimit)) continue;
+            const uint32_t id = __float_as_uint(b.w);
+            bool take;
+            if (best < 0) {
+                take = true;
+            } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
+                // near tie: decide on the exact distances, then on the caller's index
+                if (!ex.ready) {
+                    ex.o[0] = s.pos[0]; ex.o[1] = s.pos[1]; ex.o[2] = s.pos[2];
+                    ray_dir64(s, ri, rj, ex.d);
+                    ex.ready = true;
+                }
+                if (!exact) {
+                    if (STATS) ++exact_n;
+                    if (!mt64(ex.o, ex.d, a, b, c, t64)) continue;
+                    exact = true;
+                }
+                if (!best_exact) {
+                    const float4* bp = sc.tris + 3 * (int64_t)best;
+                    double bt;
+                    if (STATS) ++exact_n;
+                    best_t64 = mt64(ex.o, ex.d, __ldg(bp), __ldg(bp + 1), __ldg(bp + 2), bt) ? bt : CUDART_INF;
+                    best_exact = true;
+                }
+                take = t64 < best_t64 || (t64 == best_t64 && id < best_id);
+            } else {
+                take = t < best_t;
+            }
+            if (take) {
+                best = f;
+                best_id = id;
+                best_t = exact ? (float)t64 : t;
+                best_exact = exact;
+                best_t64 = t64;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    if (STATS) {
+        atomicAdd(tc->visits, (unsigned long long)visits);
+        atomicAdd(tc->tests, (unsigned long long)tests);
+        atomicAdd(tc->exact, (unsigned long long)exact_n);
+    }
+    t_out = best_t;
+    return best;
+}
+
+struct Cast {
+    uint32_t orig;   // caller's triangle index (0xFFFFFFFF: miss)
+    int32_t mat;
+    float t;
+    float cosf;      // incidence factor
+};
+
+template <bool STATS>
+__device__ __forceinline__ Cast cast_ray(const SensorDev& s, const SceneDev& sc, int i, int j,
+                                         const sonar_params& p, uint32_t* err,
+                                         const TraceCounters* tc) {
+    const float3 o = f3(s.pos[0], s.pos[1], s.pos[2]);
+    const float3 d = ray_dir32(s, i, j);
+    float t;
+    const int f = trace_closest<STATS>(sc, s, i, j, o, d, p.clip_tmax ? s.rmax : CUDART_INF_F, t, err, tc);
+    Cast c;
+    if (f < 0) {
+        c.orig = 0xFFFFFFFFu;
+        c.mat = 0;
+        c.t = CUDART_INF_F;
+        c.cosf = 0.0f;
+        return c;
+    }
+    const float4* tp = sc.tris + 3 * (int64_t)f;
+    const float4 a = __ldg(tp), b = __ldg(tp + 1), cc = __ldg(tp + 2);
+    const float3 v0 = f3(a.x, a.y, a.z);
+    const float3 n = cross3(sub(f3(b.x, b.y, b.z), v0), sub(f3(cc.x, cc.y, cc.z), v0));
+    const float dn = dot3(d, n) / sqrtf(dot3(n, n));
+    c.orig = __float_as_uint(b.w);
+    c.mat = __float_as_int(a.w);
+    c.t = t;
+    c.cosf = p.two_sided ? fabsf(dn) : fmaxf(-dn, 0.0f);
+    return c;
+}
+
+// Range bin of a hit, or -1 when r is outside [r_min, r_max).
+__device__ __forceinline__ int range_bin(const SensorDev& s, float r) {
+    if (!(r >= s.rmin && r < s.rmax)) return -1;
+    const int br = (int)floorf((r - s.rmin) * s.inv_dr);
+    return br < s.nr - 1 ? br : s.nr - 1;
+}
+
+__device__ __forceinline__ int az_bin(const SensorDev& s, int i) {
+    return (int)(((2ll * i + 1) * s.naz) / (2ll * s.nb));
+}
+
+// ---------------------------------------------------------------------------
+// phase 1: trace + bin + noise, one work unit per block iteration
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void load_unit(const Phase1Args& a, int u, SensorDev* S, SceneDev* SC, Unit* U) {
+    if (a.units) {
+        *U = a.units[u];
+        *S = a.sensors[U->sensor];
+        *SC = a.scenes[S->scene];
+    } else {
+        *S = a.one;
+        *SC = a.one_scene;
+        U->sensor = 0;
+        U->c0 = u * a.one.cols;
+        U->c1 = min(U->c0 + a.one.cols, a.one.naz);
+        U->rays = 0;
+    }
+}
+
+template <int DET>
+__global__ void __launch_bounds__(512) k_phase1(Phase1Args a) {
+    extern __shared__ float acc[];
+    __shared__ SensorDev S;
+    __shared__ SceneDev SC;
+    __shared__ Unit U;
+    __shared__ int s_unit;
+    __shared__ float s_red[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
+    for (int iter = 0;; ++iter) {
+        int u;
+        if (a.work_counter) {
+            if (tid == 0) s_unit = atomicAdd(a.work_counter, 1);
+            __syncthreads();
+            u = s_unit;
+        } else {
+            if (iter > 0) break;
+            u = blockIdx.x;
+        }
+        if (u >= a.n_units) break;
+        if (tid == 0) load_unit(a, u, &S, &SC, &U);
+        __syncthreads();
+        const int cw = U.c1 - U.c0;
+        const int i0 = first_beam_of_col(U.c0, S.nb, S.naz), i1 = first_beam_of_col(U.c1, S.nb, S.naz);
+        const int nbeam = i1 - i0;
+        const int R = nbeam * S.ne;
+        const int nbin = S.nr * cw;
+        for (int k = tid; k < nbin; k += nt) acc[k] = 0.0f;
+        __syncthreads();
+        for (int base = 0; base < R; base += nt) {
+            const int r = base + tid;
+            uint32_t lkey = kNoKey;
+            float score = 0.0f;
+            if (r < R) {
+                int bi, ej;
+                if (S.mapping == 0) { bi = r / S.ne; ej = r - bi * S.ne; }
+                else { ej = r / nbeam; bi = r - ej * nbeam; }
+                const int i = i0 + bi, j = ej;
+                const Cast c = cast_ray<false>(S, SC, i, j, a.params, a.err, nullptr);
+                uint32_t gkey = kNoKey;
+                if (c.orig != 0xFFFFFFFFu) {
+                    const int br = range_bin(S, c.t);
+                    if (br >= 0) {
+                        const int ba = az_bin(S, i);
+                        gkey = (uint32_t)(br * S.naz + ba);
+                        lkey = (uint32_t)(br * cw + (ba - U.c0));
+                        const int m = c.mat < a.n_mat ? c.mat : a.n_mat - 1;
+                        score = __ldg(a.theta + 2 + m) * c.cosf * expf(-2.0f * alpha * c.t) * gain;
+                    }
+                }
+                if (a.hits) {
+                    uint4 rec = make_uint4(gkey, c.orig, __float_as_uint(c.t), __float_as_uint(c.cosf));
+                    *reinterpret_cast<uint4*>(a.hits + S.hits_off + (int64_t)i * S.ne + j) = rec;
+                }
+            }
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, lkey);
+            const int leader = __ffs(peers) - 1;
+            if (DET) {
+                // sequential fold in ray order: warps take turns, lanes of a
+                // group are added by their leader in lane order
+                for (int w = 0; w < nw; ++w) {
+                    if (warp == w && lkey != kNoKey) {
+                        float v = lane == leader ? acc[lkey] : 0.0f;
+                        for (uint32_t m = peers; m; m &= m - 1) {
+                            const float x = __shfl_sync(peers, score, __ffs(m) - 1);
+                            v += x;
+                        }
+                        if (lane == leader) acc[lkey] = v;
+                    }
+                    __syncthreads();
+                }
+            } else {
+                if (lkey != kNoKey) {
+                    float v = 0.0f;
+                    for (uint32_t m = peers; m; m &= m - 1) v += __shfl_sync(peers, score, __ffs(m) - 1);
+                    if (lane == leader) atomicAdd(&acc[lkey], v);
+                }
+            }
+        }
+        __syncthreads();
+        // Eq. 3-6 per bin, I~ to HBM, kept in shared memory for the maxima
+        const float dr = (S.rmax - S.rmin) / (float)S.nr, da = S.hfov / (float)S.naz;
+        const float inv_rmax2 = 1.0f / (S.rmax * S.rmax);
+        const float inv_sphi = 1.0f / a.params.sigma_phi;
+        for (int k = tid; k < nbin; k += nt) {
+            const int row = k / cw, col = U.c0 + (k - row * cw);
+            const uint32_t b = (uint32_t)(row * S.naz + col);
+            const float P = acc[k];
+            float w_sa, w_sm;
+            bin_noise(b, S, a.params.sigma_sa, a.params.sigma_sm, w_sa, w_sm);
+            const float rc = fmaf((float)row + 0.5f, dr, S.rmin);
+            const float pc = fmaf((float)col + 0.5f, da, -0.5f * S.hfov);
+            const float additive = rc * rc * inv_rmax2 * (1.0f + 0.5f * expf(-pc * pc * inv_sphi) * w_sa);
+            const float In = P * (0.5f + w_sm) + additive;
+            a.noised[S.polar_off + b] = In;
+            if (a.binned) a.binned[S.polar_off + b] = P;
+            acc[k] = In;
+        }
+        __syncthreads();
+        if (a.params.normalise == 1) {
+            for (int row = tid; row < S.nr; row += nt) {
+                float m = acc[row * cw];
+                for (int c = 1; c < cw; ++c) m = fmaxf(m, acc[row * cw + c]);
+                atomicMax(a.rowmax + S.rowmax_off + row, ord_enc(m));
+            }
+        } else if (a.params.normalise == 2) {
+            float m = -CUDART_INF_F;
+            for (int k = tid; k < nbin; k += nt) m = fmaxf(m, acc[k]);
+            for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+            if (lane == 0) s_red[warp] = m;
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < nw; ++w) m = fmaxf(m, s_red[w]);
+                atomicMax(a.rowmax + S.rowmax_off, ord_enc(fmaxf(m, s_red[0])));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 2: normalisation + fan
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float group_max(const uint32_t* rowmax, const SensorDev& s, int mode, int row) {
+    return ord_dec(rowmax[s.rowmax_off + (mode == 1 ? row : 0)]);
+}
+
+__device__ __forceinline__ float norm_value(float In, float m, int mode) {
+    return (mode != 0 && m > 0.0f) ? In / m : In;
+}
+
+// Fan pixel value; `val(row, col)` returns the normalised polar value.
+template <class F>
+__device__ __forceinline__ float fan_pixel(const SensorDev& s, int64_t pix, F val) {
+    const int v = (int)(pix / s.fan_w), u = (int)(pix - (int64_t)v * s.fan_w);
+    const float x = ((float)u + 0.5f - 0.5f * (float)s.fan_w) / s.fan_scale;
+    const float y = ((float)s.fan_h - (float)v - 0.5f) / s.fan_scale;
+    const float r = sqrtf(x * x + y * y);
+    const float phi = atan2f(x, y);
+    if (r < s.rmin || r > s.rmax || fabsf(phi) > 0.5f * s.hfov) return 0.0f;
+    const float fr = (r - s.rmin) * s.inv_dr - 0.5f;
+    const float fa = (phi + 0.5f * s.hfov) * ((float)s.naz / s.hfov) - 0.5f;
+    const float i0f = floorf(fr), j0f = floorf(fa);
+    const float wr = fr - i0f, wa = fa - j0f;
+    const int i0 = (int)i0f, j0 = (int)j0f;
+    const int ia = min(max(i0, 0), s.nr - 1), ib = min(max(i0 + 1, 0), s.nr - 1);
+    const int ja = min(max(j0, 0), s.naz - 1), jb = min(max(j0 + 1, 0), s.naz - 1);
+    return (1.0f - wr) * ((1.0f - wa) * val(ia, ja) + wa * val(ia, jb)) +
+           wr * ((1.0f - wa) * val(ib, ja) + wa * val(ib, jb));
+}
+
+__device__ __forceinline__ int find_sensor(const int64_t* prefix, int n, int64_t e) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_phase2(Phase2Args a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.total; e += stride) {
+        const SensorDev* sp;
+        int64_t local;
+        if (a.sensors) {
+            const int si = find_sensor(a.prefix, a.n_sensors, e);
+            sp = a.sensors + si;
+            local = e - a.prefix[si];
+        } else {
+            sp = &a.one;
+            local = e;
+        }
+        const SensorDev& s = *sp;
+        const int64_t npol = (int64_t)s.nr * s.naz;
+        if (local < npol) {
+            const int row = (int)(local / s.naz);
+            const float m = group_max(a.rowmax, s, a.normalise, row);
+            a.polar[s.polar_off + local] = norm_value(a.noised[s.polar_off + local], m, a.normalise);
+        } else if (a.fan) {
+            const int64_t pix = local - npol;
+            const float* In = a.noised + s.polar_off;
+            const uint32_t* rm = a.rowmax;
+            const int mode = a.normalise;
+            a.fan[s.fan_off + pix] = fan_pixel(s, pix, [&](int row, int col) {
+                return norm_value(In[(int64_t)row * s.naz + col], group_max(rm, s, mode, row), mode);
+            });
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fan(SensorDev s, const float* polar, float* fan) {
+    const int64_t n = (int64_t)s.fan_w * s.fan_h;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        fan[p] = fan_pixel(s, p, [&](int row, int col) { return polar[(int64_t)row * s.naz + col]; });
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+
+// Group terms of the normalisation Jacobian: m, argmax (lowest index on
+// ties) and c = sum G I~ / m^2.  Mode 1: one warp per range row; mode 2: one
+// block per sensor image.
+__global__ void k_adj_rows(const SensorDev* sensors, SensorDev one, int n_sensors, int64_t total,
+                           int mode, const float* noised, const float* grad, RowInfo* info) {
+    const int lane = threadIdx.x & 31;
+    __shared__ float s_m[32];
+    __shared__ int s_a[32];
+    __shared__ double s_d[32];
+    if (mode == 1) {
+        const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (g >= total) return;
+        int si = 0;
+        if (sensors) {
+            int lo = 0, hi = n_sensors - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sensors[mid].rowmax_off <= g) lo = mid; else hi = mid - 1;
+            }
+            si = lo;
+        }
+        const SensorDev& s = sensors ? sensors[si] : one;
+        const int row = (int)(g - s.rowmax_off);
+        const float* In = noised + s.polar_off + (int64_t)row * s.naz;
+        const float* G = grad + s.polar_off + (int64_t)row * s.naz;
+        float m = -CUDART_INF_F;
+        int am = 0x7FFFFFFF;
+        double dot = 0.0;
+        for (int j = lane; j < s.naz; j += 32) {
+            const float x = In[j];
+            if (x > m) { m = x; am = j; }
+            dot += (double)G[j] * (double)x;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+            const int a2 = __shfl_xor_sync(0xFFFFFFFFu, am, o);
+            if (m2 > m || (m2 == m && a2 < am)) { m = m2; am = a2; }
+            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, o);
+        }
+        if (lane == 0) {
+            RowInfo r;
+            r.m = m;
+            r.valid = m > 0.0f;
+            r.c = r.valid ? (float)(dot / ((double)m * (double)m)) : 0.0f;
+            r.arg = row * s.naz + am;
+            info[g] = r;
+        }
+    } else {
+        const int si = blockIdx.x;
+        if (si >= total) return;
+        const SensorDev& s = sensors ? sensors[si] : one;
+        const int64_t n = (int64_t)s.nr * s.naz;
+        const float* In = noised + s.polar_off;
+        const float* G = grad + s.polar_off;
+        float m = -CUDART_INF_F;
+        int am = 0x7FFFFFFF;
+        double dot = 0.0;
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const float x = In[j];
+            if (x > m) { m = x; am = (int)j; }
+            dot += (double)G[j] * (double)x;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+            const int a2 = __shfl_xor_sync(0xFFFFFFFFu, am, o);
+            if (m2 > m || (m2 == m && a2 < am)) { m = m2; am = a2; }
+            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, o);
+        }
+        const int w = threadIdx.x >> 5;
+        if (lane == 0) { s_m[w] = m; s_a[w] = am; s_d[w] = dot; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                if (s_m[k] > m || (s_m[k] == m && s_a[k] < am)) { m = s_m[k]; am = s_a[k]; }
+                dot += s_d[k];
+            }
+            RowInfo r;
+            r.m = m;
+            r.valid = m > 0.0f;
+            r.c = r.valid ? (float)(dot / ((double)m * (double)m)) : 0.0f;
+            r.arg = am;
+            info[s.rowmax_off] = r;
+        }
+    }
+}
+
+__device__ __forceinline__ void load_unit_adj(const AdjArgs& a, int u, SensorDev* S, SceneDev* SC, Unit* U) {
+    if (a.units) {
+        *U = a.units[u];
+        *S = a.sensors[U->sensor];
+        *SC = a.scenes[S->scene];
+    } else {
+        *S = a.one;
+        *SC = a.one_scene;
+        U->sensor = 0;
+        U->c0 = u * a.one.cols;
+        U->c1 = min(U->c0 + a.one.cols, a.one.naz);
+        U->rays = 0;
+    }
+}
+
+// Per-ray gather of dL/dP and accumulation of dtheta.  Units are the forward's
+// column tiles; each unit's sums go to its own row of `partials` (per-warp
+// material slabs in lane order, per-thread alpha/gain, fixed-order block
+// reductions), and the last block to finish adds the rows in unit order.
+template <bool RECOMPUTE>
+__global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
+    extern __shared__ double slab[];   // [n_warps][n_mat]
+    __shared__ SensorDev S;
+    __shared__ SceneDev SC;
+    __shared__ Unit U;
+    __shared__ int s_unit, s_last;
+    __shared__ double s_ag[2][32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int nm = a.n_mat, nq = nm + 2;
+    const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
+    const int mode = a.params.normalise;
+    for (int iter = 0;; ++iter) {
+        int u;
+        if (a.work_counter) {
+            if (tid == 0) s_unit = atomicAdd(a.work_counter, 1);
+            __syncthreads();
+            u = s_unit;
+        } else {
+            if (iter > 0) break;
+            u = blockIdx.x;
+        }
+        if (u >= a.n_units) break;
+        if (tid == 0) load_unit_adj(a, u, &S, &SC, &U);
+        for (int k = tid; k < nw * nm; k += nt) slab[k] = 0.0;
+        __syncthreads();
+        const int i0 = first_beam_of_col(U.c0, S.nb, S.naz), i1 = first_beam_of_col(U.c1, S.nb, S.naz);
+        const int nbeam = i1 - i0;
+        const int R = nbeam * S.ne;
+        const int mapping = S.mapping;
+        double acc_a = 0.0, acc_g = 0.0;
+        for (int base = 0; base < R; base += nt) {
+            const int r = base + tid;
+            bool valid = false;
+            int mat = 0;
+            double v_mu = 0.0;
+            if (r < R) {
+                int bi, ej;
+                if (mapping == 0) { bi = r / S.ne; ej = r - bi * S.ne; }
+                else { ej = r / nbeam; bi = r - ej * nbeam; }
+                const int i = i0 + bi, j = ej;
+                uint32_t key, orig;
+                float rr, cf;
+                if (RECOMPUTE) {
+                    const Cast c = cast_ray<false>(S, SC, i, j, a.params, a.err, nullptr);
+                    key = kNoKey;
+                    if (c.orig != 0xFFFFFFFFu) {
+                        const int br = range_bin(S, c.t);
+                        if (br >= 0) key = (uint32_t)(br * S.naz + az_bin(S, i));
+                    }
+                    orig = c.orig;
+                    rr = c.t;
+                    cf = c.cosf;
+                } else {
+                    const uint4 h = *reinterpret_cast<const uint4*>(a.hits + S.hits_off + (int64_t)i * S.ne + j);
+                    key = h.x;
+                    orig = h.y;
+                    rr = __uint_as_float(h.z);
+                    cf = __uint_as_float(h.w);
+                }
+                if (key != kNoKey) {
+                    if (key >= (uint32_t)(S.nr * S.naz) || orig >= (uint32_t)SC.n_tris) {
+                        atomicOr(a.err, SONAR_DEVERR_INDEX);
+                    } else {
+                        const float G = a.grad[S.polar_off + key];
+                        float gI = G;
+                        if (mode != 0) {
+                            const RowInfo ri = a.rowinfo[S.rowmax_off + (mode == 1 ? (int)(key / S.naz) : 0)];
+                            if (ri.valid) gI = G / ri.m - ((int)key == ri.arg ? ri.c : 0.0f);
+                        }
+                        const float gP = gI * (0.5f + w_sm_of(key, S, a.params.sigma_sm));
+                        mat = SC.mat_orig[orig];
+                        mat = mat < nm ? mat : nm - 1;
+                        const float mu = __ldg(a.theta + 2 + mat);
+                        const float att = expf(-2.0f * alpha * rr);
+                        const double ca = (double)gP * (double)(cf * att);
+                        v_mu = ca * gain;
+                        acc_a += ca * gain * mu * (-2.0 * rr);
+                        acc_g += ca * mu;
+                        valid = true;
+                    }
+                }
+            }
+            // material slab of this warp, lanes in order
+            for (int l = 0; l < 32; ++l) {
+                if (lane == l && valid) slab[warp * nm + mat] += v_mu;
+                __syncwarp();
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            acc_a += __shfl_down_sync(0xFFFFFFFFu, acc_a, o);
+            acc_g += __shfl_down_sync(0xFFFFFFFFu, acc_g, o);
+        }
+        if (lane == 0) { s_ag[0][warp] = acc_a; s_ag[1][warp] = acc_g; }
+        __syncthreads();
+        double* out = a.partials + (int64_t)u * nq;
+        for (int m = tid; m < nm; m += nt) {
+            double v = 0.0;
+            for (int w = 0; w < nw; ++w) v += slab[w * nm + m];
+            out[2 + m] = v;
+        }
+        if (tid == 0) {
+            double va = 0.0, vg = 0.0;
+            for (int w = 0; w < nw; ++w) { va += s_ag[0][w]; vg += s_ag[1][w]; }
+            out[0] = va;
+            out[1] = vg;
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(a.done_counter, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int q = tid; q < nq; q += nt) {
+            double v = 0.0;
+            for (int u = 0; u < a.n_units; ++u) v += __ldcg(a.partials + (int64_t)u * nq + q);
+            a.dtheta[q] = (float)v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// counters
+// ---------------------------------------------------------------------------
+
+__global__ void k_stats(SensorDev s, SceneDev sc, sonar_params p, TraceCounters tc, uint32_t* err) {
+    const int64_t n = (int64_t)s.nb * s.ne;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)(k / s.ne), j = (int)(k - (int64_t)i * s.ne);
+    cast_ray<true>(s, sc, i, j, p, err, &tc);
+}
+
+__global__ void k_popcount(const uint32_t* bits, int64_t words, unsigned long long* out) {
+    unsigned long long c = 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x)
+        c += __popc(bits[w]);
+    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+void set_kernel_attributes() {
+    cudaFuncSetAttribute(k_phase1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_phase1<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
+
+cudaError_t launch_phase1(const Phase1Args& a, int det, int grid, int block, size_t smem, cudaStream_t st) {
+    if (det) k_phase1<1><<<grid, block, smem, st>>>(a);
+    else k_phase1<0><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int phase1_blocks_per_sm(int det, int block, size_t smem) {
+    int n = 0;
+    const void* f = det ? (const void*)k_phase1<1> : (const void*)k_phase1<0>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_phase2(const Phase2Args& a, int grid, int block, cudaStream_t st) {
+    k_phase2<<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fan(const SensorDev& s, const float* polar, float* fan, cudaStream_t st) {
+    const int64_t n = (int64_t)s.fan_w * s.fan_h;
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_fan<<<grid > 0 ? grid : 1, 256, 0, st>>>(s, polar, fan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rows(const SensorDev* sensors, const SensorDev& one, int n_sensors,
+                            int64_t total_groups, int normalise, const float* noised,
+                            const float* grad, RowInfo* info, cudaStream_t st) {
+    if (normalise == 1) {
+        const int64_t threads = total_groups * 32;
+        k_adj_rows<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sensors, one, n_sensors, total_groups,
+                                                                      1, noised, grad, info);
+    } else if (normalise == 2) {
+        k_adj_rows<<<(unsigned)total_groups, 1024, 0, st>>>(sensors, one, n_sensors, total_groups, 2, noised,
+                                                            grad, info);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjArgs& a, bool recompute, int grid, int block, size_t smem,
+                           cudaStream_t st) {
+    if (recompute) k_adjoint<true><<<grid, block, smem, st>>>(a);
+    else k_adjoint<false><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int adjoint_blocks_per_sm(bool recompute, int block, size_t smem) {
+    int n = 0;
+    const void* f = recompute ? (const void*)k_adjoint<true> : (const void*)k_adjoint<false>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
+                         const TraceCounters& tc, uint32_t* err, cudaStream_t st) {
+    const int64_t n = (int64_t)s.nb * s.ne;
+    k_stats<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(s, sc, p, tc, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out, cudaStream_t st) {
+    k_popcount<<<1024, 256, 0, st>>>(bits, words, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sonar

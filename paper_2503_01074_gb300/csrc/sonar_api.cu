@@ -1,0 +1,997 @@
+// C ABI of libsonar: contexts, scenes, single-frame and batched rendering,
+// the adjoint, the autotuner and the counter mode.  Host code only; kernels
+// live in bvh_build.cu and render.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sonar_host.h"
+#include "sonar_internal.cuh"
+
+using namespace sonar;
+
+namespace {
+
+struct Tune {
+    int cols = 0;     // azimuth columns per work unit (0: derive)
+    int mapping = 0;  // 0: lanes along elevation, 1: lanes along beams
+    int block = 128;
+};
+
+using ShapeKey = std::array<int, 4>;   // n_beams, n_elev, n_range_bins, n_az_bins
+
+// A device buffer that grows on demand (stream-ordered allocation).
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct sonar_ctx {
+    int device = 0;
+    int sm_count = 1;
+    std::vector<SceneStore> scenes;
+    std::vector<bool> alive;
+    std::string last_error;
+    uint32_t* d_err = nullptr;
+    Scratch rowmax, noised, rowinfo, partials, counters;
+    std::map<ShapeKey, Tune> tune;
+};
+
+struct sonar_batch;
+
+namespace {
+
+sonar_status fail(sonar_ctx* ctx, sonar_status st, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+sonar_status cuda_fail(sonar_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? SONAR_ERR_OOM : SONAR_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+cudaError_t grow(Scratch& s, size_t bytes, cudaStream_t st) {
+    if (s.bytes >= bytes && s.p) return cudaSuccess;
+    if (s.p) cudaFreeAsync(s.p, st);
+    s.p = nullptr;
+    s.bytes = 0;
+    size_t want = std::max(bytes, (size_t)256);
+    cudaError_t e = cudaMallocAsync(&s.p, want, st);
+    if (e == cudaSuccess) s.bytes = want;
+    return e;
+}
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+sonar_status check_sensor(sonar_ctx* ctx, const sonar_sensor* s) {
+    if (!s) return fail(ctx, SONAR_ERR_ARG, "sensor is NULL");
+    if (s->n_beams < 1 || s->n_elev < 1 || s->n_range_bins < 1 || s->n_az_bins < 1)
+        return fail(ctx, SONAR_ERR_ARG, "sensor counts must be >= 1");
+    if ((int64_t)s->n_beams * s->n_elev > 0x7FFFFFFFll)
+        return fail(ctx, SONAR_ERR_ARG, "n_beams * n_elev exceeds 2^31 - 1");
+    if ((int64_t)s->n_range_bins * s->n_az_bins > 0x7FFFFFFEll)
+        return fail(ctx, SONAR_ERR_ARG, "n_range_bins * n_az_bins exceeds 2^31 - 2");
+    for (int k = 0; k < 3; ++k)
+        if (!finite_f(s->pos[k])) return fail(ctx, SONAR_ERR_ARG, "sensor position not finite");
+    for (int k = 0; k < 9; ++k)
+        if (!finite_f(s->rot[k])) return fail(ctx, SONAR_ERR_ARG, "sensor rotation not finite");
+    const float pi = 3.14159265358979f;
+    if (!(s->hfov > 0.0f && s->hfov <= pi)) return fail(ctx, SONAR_ERR_ARG, "hfov must be in (0, pi]");
+    if (!(s->vfov > 0.0f && s->vfov <= pi)) return fail(ctx, SONAR_ERR_ARG, "vfov must be in (0, pi]");
+    if (!(s->r_min >= 0.0f && s->r_max > s->r_min && finite_f(s->r_max)))
+        return fail(ctx, SONAR_ERR_ARG, "need 0 <= r_min < r_max < inf");
+    return SONAR_OK;
+}
+
+sonar_status check_params(sonar_ctx* ctx, const sonar_params* p) {
+    if (!p) return fail(ctx, SONAR_ERR_ARG, "params is NULL");
+    if (!(p->sigma_sa >= 0.0f && finite_f(p->sigma_sa))) return fail(ctx, SONAR_ERR_ARG, "sigma_sa must be >= 0");
+    if (!(p->sigma_sm >= 0.0f && finite_f(p->sigma_sm))) return fail(ctx, SONAR_ERR_ARG, "sigma_sm must be >= 0");
+    if (!(p->sigma_phi > 0.0f && finite_f(p->sigma_phi))) return fail(ctx, SONAR_ERR_ARG, "sigma_phi must be > 0");
+    if (p->normalise < 0 || p->normalise > 2) return fail(ctx, SONAR_ERR_ARG, "normalise must be 0, 1 or 2");
+    if (p->two_sided < 0 || p->two_sided > 1) return fail(ctx, SONAR_ERR_ARG, "two_sided must be 0 or 1");
+    if (p->clip_tmax < 0 || p->clip_tmax > 1) return fail(ctx, SONAR_ERR_ARG, "clip_tmax must be 0 or 1");
+    if (p->accumulate < 0 || p->accumulate > 1) return fail(ctx, SONAR_ERR_ARG, "accumulate must be 0 or 1");
+    return SONAR_OK;
+}
+
+sonar_status check_scene(sonar_ctx* ctx, int32_t id) {
+    if (id < 0 || id >= (int32_t)ctx->scenes.size() || !ctx->alive[id])
+        return fail(ctx, SONAR_ERR_ARG, "unknown scene id " + std::to_string(id));
+    return SONAR_OK;
+}
+
+sonar_status check_nmat(sonar_ctx* ctx, int32_t scene, int32_t n_mat) {
+    if (n_mat < 1 || n_mat > kMaxMat) return fail(ctx, SONAR_ERR_ARG, "n_mat must be in [1, 1024]");
+    if (ctx->scenes[scene].max_mat >= n_mat)
+        return fail(ctx, SONAR_ERR_ARG, "scene uses material id " + std::to_string(ctx->scenes[scene].max_mat) +
+                                             " >= n_mat " + std::to_string(n_mat));
+    return SONAR_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Tile shape for a sensor: the tuning cache entry, else one block-wide ray
+// tile per unit, bounded by the shared-memory column block.
+Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
+    Tune t;
+    auto it = ctx->tune.find(ShapeKey{s.n_beams, s.n_elev, s.n_range_bins, s.n_az_bins});
+    if (it != ctx->tune.end()) t = it->second;
+    const int bpc = std::max(1, s.n_beams / std::max(1, s.n_az_bins));
+    if (t.cols <= 0) t.cols = std::max(1, t.block / std::max(1, s.n_elev * bpc));
+    const int max_cols_smem = std::max(1, (int)(kMaxDynSmem / 4 / 2) / s.n_range_bins);
+    t.cols = std::max(1, std::min({t.cols, s.n_az_bins, max_cols_smem}));
+    if (t.block < 32 || t.block > 512 || (t.block & 31)) t.block = 128;
+    return t;
+}
+
+SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, const Tune& t, int fan_w,
+                      int fan_h) {
+    SensorDev d{};
+    memcpy(d.pos, s.pos, sizeof d.pos);
+    memcpy(d.rot, s.rot, sizeof d.rot);
+    d.nb = s.n_beams;
+    d.ne = s.n_elev;
+    d.nr = s.n_range_bins;
+    d.naz = s.n_az_bins;
+    d.hfov = s.hfov;
+    d.vfov = s.vfov;
+    d.rmin = s.r_min;
+    d.rmax = s.r_max;
+    d.inv_dr = (float)((double)s.n_range_bins / ((double)s.r_max - (double)s.r_min));
+    d.fan_w = fan_w;
+    d.fan_h = fan_h;
+    if (fan_w > 0 && fan_h > 0) {
+        const double sx = fan_w / (2.0 * (double)s.r_max * std::sin((double)s.hfov / 2.0));
+        const double sy = fan_h / (double)s.r_max;
+        d.fan_scale = (float)std::min(sx, sy);
+    }
+    d.seed_lo = (uint32_t)seed;
+    d.seed_hi = (uint32_t)(seed >> 32);
+    d.frame_lo = (uint32_t)frame;
+    d.frame_hi = (uint32_t)(frame >> 32);
+    d.cols = t.cols;
+    d.mapping = t.mapping;
+    d.n_tiles = (s.n_az_bins + t.cols - 1) / t.cols;
+    return d;
+}
+
+int grid2_for(const sonar_ctx* ctx, int64_t total) {
+    const int64_t g = (total + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)ctx->sm_count * 8));
+}
+
+}  // namespace
+
+// ===========================================================================
+// context
+// ===========================================================================
+
+extern "C" const char* sonar_version(void) {
+    return "libsonar 1.0 (sm_103a; LBVH + FP32/FP64-certified Moller-Trumbore; Philox4x32-10)";
+}
+
+extern "C" sonar_status sonar_create(int32_t device, sonar_ctx_t* out) {
+    if (!out) return SONAR_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SONAR_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SONAR_ERR_CUDA;
+    sonar_ctx* ctx = new sonar_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+        delete ctx;
+        return SONAR_ERR_OOM;
+    }
+    set_kernel_attributes();
+    cudaGetLastError();
+    *out = ctx;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_destroy(sonar_ctx_t ctx) {
+    if (!ctx) return SONAR_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& s : ctx->scenes) free_scene(&s);
+    for (Scratch* s : {&ctx->rowmax, &ctx->noised, &ctx->rowinfo, &ctx->partials, &ctx->counters})
+        if (s->p) cudaFreeAsync(s->p, 0);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->d_err);
+    delete ctx;
+    return SONAR_OK;
+}
+
+extern "C" const char* sonar_last_error(sonar_ctx_t ctx) {
+    return ctx ? ctx->last_error.c_str() : "";
+}
+
+extern "C" sonar_status sonar_check(sonar_ctx_t ctx, uint32_t* bits) {
+    if (!ctx) return SONAR_ERR_ARG;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CU(cudaDeviceSynchronize(), "device synchronisation");
+    uint32_t w = 0;
+    CU(cudaMemcpy(&w, ctx->d_err, sizeof w, cudaMemcpyDeviceToHost), "reading the error word");
+    if (bits) *bits = w;
+    if (w) {
+        CU(cudaMemset(ctx->d_err, 0, sizeof(uint32_t)), "clearing the error word");
+        return fail(ctx, SONAR_ERR_DEVICE, "device error word 0x" + std::to_string(w));
+    }
+    return SONAR_OK;
+}
+
+// ===========================================================================
+// scenes
+// ===========================================================================
+
+extern "C" sonar_status sonar_scene_upload(sonar_ctx_t ctx, const float* d_verts, int64_t n_verts,
+                                           const int32_t* d_tris, const int32_t* d_mat, int64_t n_tris,
+                                           void* stream, int32_t* scene_id) {
+    if (!ctx || !scene_id) return fail(ctx, SONAR_ERR_ARG, "NULL context or scene_id");
+    if (n_tris < 0 || n_verts < 0) return fail(ctx, SONAR_ERR_ARG, "negative counts");
+    if (n_tris >= (1ll << 28) - 2) return fail(ctx, SONAR_ERR_ARG, "n_tris must be < 2^28 - 2");
+    if (n_verts >= (1ll << 31)) return fail(ctx, SONAR_ERR_ARG, "n_verts must be < 2^31");
+    if (n_tris > 0 && (!d_verts || !d_tris || !d_mat || n_verts == 0))
+        return fail(ctx, SONAR_ERR_ARG, "NULL scene arrays");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    SceneStore s;
+    std::string msg;
+    const sonar_status st = build_scene(d_verts, n_verts, d_tris, d_mat, n_tris, (cudaStream_t)stream, &s, &msg);
+    if (st != SONAR_OK) {
+        free_scene(&s);
+        return fail(ctx, st, msg);
+    }
+    ctx->scenes.push_back(s);
+    ctx->alive.push_back(true);
+    *scene_id = (int32_t)ctx->scenes.size() - 1;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_scene_release(sonar_ctx_t ctx, int32_t id) {
+    if (!ctx) return SONAR_ERR_ARG;
+    sonar_status st = check_scene(ctx, id);
+    if (st) return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CU(cudaDeviceSynchronize(), "device synchronisation");
+    free_scene(&ctx->scenes[id]);
+    ctx->alive[id] = false;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t id, int64_t out[5]) {
+    if (!ctx || !out) return fail(ctx, SONAR_ERR_ARG, "NULL argument");
+    sonar_status st = check_scene(ctx, id);
+    if (st) return st;
+    const SceneStore& s = ctx->scenes[id];
+    out[0] = s.n_tris;
+    out[1] = s.n_pairs;
+    out[2] = s.height;
+    out[3] = s.max_mat;
+    out[4] = (int64_t)s.bytes;
+    return SONAR_OK;
+}
+
+// ===========================================================================
+// single-frame rendering
+// ===========================================================================
+
+namespace {
+
+size_t phase1_smem(const SensorDev& s) { return (size_t)s.nr * s.cols * sizeof(float); }
+
+}  // namespace
+
+extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                                     const sonar_params* params, const float* d_theta, int32_t n_mat,
+                                     uint64_t seed, uint64_t frame, const sonar_outputs* out,
+                                     void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    sonar_status st;
+    if ((st = check_scene(ctx, scene_id)) || (st = check_sensor(ctx, sensor)) || (st = check_params(ctx, params)) ||
+        (st = check_nmat(ctx, scene_id, n_mat)))
+        return st;
+    if (!d_theta) return fail(ctx, SONAR_ERR_ARG, "d_theta is NULL");
+    if (!out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "outputs or outputs->polar is NULL");
+    if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
+    if (out->fan && (out->fan_w < 1 || out->fan_h < 1)) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const Tune t = tune_for(ctx, *sensor);
+    SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
+    const int64_t npol = (int64_t)S.nr * S.naz;
+    float* noised = out->noised;
+    if (!noised) {
+        CU(grow(ctx->noised, sizeof(float) * npol, s), "scratch allocation");
+        noised = (float*)ctx->noised.p;
+    }
+    const int groups = params->normalise == 1 ? S.nr : 1;
+    CU(grow(ctx->rowmax, sizeof(uint32_t) * groups, s), "scratch allocation");
+    CU(cudaMemsetAsync(ctx->rowmax.p, 0, sizeof(uint32_t) * groups, s), "cudaMemsetAsync");
+
+    Phase1Args a{};
+    a.n_units = S.n_tiles;
+    a.n_mat = n_mat;
+    a.one = S;
+    a.one_scene = scene_dev(ctx->scenes[scene_id]);
+    a.theta = d_theta;
+    a.params = *params;
+    a.noised = noised;
+    a.binned = out->binned;
+    a.hits = out->hits;
+    a.rowmax = (uint32_t*)ctx->rowmax.p;
+    a.err = ctx->d_err;
+    CU(launch_phase1(a, params->accumulate == 0, S.n_tiles, t.block, phase1_smem(S), s), "phase-1 launch");
+
+    Phase2Args b{};
+    b.one = S;
+    b.total = npol + (out->fan ? (int64_t)out->fan_w * out->fan_h : 0);
+    b.noised = noised;
+    b.rowmax = (const uint32_t*)ctx->rowmax.p;
+    b.normalise = params->normalise;
+    b.polar = out->polar;
+    b.fan = out->fan;
+    CU(launch_phase2(b, grid2_for(ctx, b.total), 256, s), "phase-2 launch");
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* sensor, const float* d_polar,
+                                           int32_t fan_w, int32_t fan_h, float* d_fan, void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    sonar_status st = check_sensor(ctx, sensor);
+    if (st) return st;
+    if (!d_polar || !d_fan) return fail(ctx, SONAR_ERR_ARG, "NULL polar or fan");
+    if (fan_w < 1 || fan_h < 1) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    Tune t;
+    t.cols = 1;
+    const SensorDev S = make_sensor(*sensor, 0, 0, t, fan_w, fan_h);
+    CU(launch_fan(S, d_polar, d_fan, (cudaStream_t)stream), "fan launch");
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                                              const sonar_params* params, const float* d_theta, int32_t n_mat,
+                                              uint64_t seed, uint64_t frame, const float* d_grad_polar,
+                                              const float* d_noised, const sonar_hit* d_hits, float* d_dtheta,
+                                              void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    sonar_status st;
+    if ((st = check_scene(ctx, scene_id)) || (st = check_sensor(ctx, sensor)) || (st = check_params(ctx, params)) ||
+        (st = check_nmat(ctx, scene_id, n_mat)))
+        return st;
+    if (!d_theta || !d_grad_polar || !d_noised || !d_dtheta)
+        return fail(ctx, SONAR_ERR_ARG, "NULL theta, grad, noised or dtheta");
+    if (d_hits && !aligned16(d_hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const Tune t = tune_for(ctx, *sensor);
+    const SensorDev S = make_sensor(*sensor, seed, frame, t, 0, 0);
+    const int groups = params->normalise == 1 ? S.nr : 1;
+    CU(grow(ctx->rowinfo, sizeof(RowInfo) * groups, s), "scratch allocation");
+    const int nq = n_mat + 2;
+    CU(grow(ctx->partials, sizeof(double) * (size_t)S.n_tiles * nq, s), "scratch allocation");
+    CU(grow(ctx->counters, sizeof(int32_t) * 4, s), "scratch allocation");
+    CU(cudaMemsetAsync(ctx->counters.p, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+    if (params->normalise != 0)
+        CU(launch_adj_rows(nullptr, S, 1, groups, params->normalise, d_noised, d_grad_polar,
+                           (RowInfo*)ctx->rowinfo.p, s),
+           "adjoint row launch");
+    AdjArgs a{};
+    a.done_counter = (int32_t*)ctx->counters.p + 1;
+    a.n_units = S.n_tiles;
+    a.n_mat = n_mat;
+    a.one = S;
+    a.one_scene = scene_dev(ctx->scenes[scene_id]);
+    a.theta = d_theta;
+    a.params = *params;
+    a.grad = d_grad_polar;
+    a.hits = d_hits;
+    a.rowinfo = (const RowInfo*)ctx->rowinfo.p;
+    a.partials = (double*)ctx->partials.p;
+    a.dtheta = d_dtheta;
+    a.err = ctx->d_err;
+    const size_t smem = sizeof(double) * (t.block / 32) * n_mat;
+    CU(launch_adjoint(a, d_hits == nullptr, S.n_tiles, t.block, smem, s), "adjoint launch");
+    return SONAR_OK;
+}
+
+// ===========================================================================
+// batches
+// ===========================================================================
+
+struct sonar_batch {
+    sonar_ctx* ctx = nullptr;
+    std::vector<sonar_batch_item> items;
+    std::vector<SensorDev> hs;        // host copy of the descriptors
+    std::vector<Unit> units;
+    std::vector<int64_t> prefix;      // phase-2 element prefix
+    int64_t total_rows = 0, total_polar = 0, total2 = 0;
+    int block = 128;
+    size_t smem1 = 0;
+    SensorDev* d_sens = nullptr;
+    Unit* d_units = nullptr;
+    SceneDev* d_scenes = nullptr;
+    int64_t* d_prefix = nullptr;
+    uint32_t* d_rowmax = nullptr;
+    float* d_noised = nullptr;
+    RowInfo* d_rowinfo = nullptr;
+    double* d_partials = nullptr;
+    int32_t* d_counters = nullptr;    // [0] phase-1 work, [1] adjoint work, [2] adjoint done
+    int n_mat_cap = 0;
+    size_t n_scene_table = 0;         // entries in d_scenes
+    // host staging for updates (pinned, double-buffered)
+    SensorDev* h_stage[2] = {nullptr, nullptr};
+    SceneDev* h_stage_sc[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    int stage_next = 0;
+    // graphs
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t fwd = nullptr, bwd = nullptr;
+    std::vector<unsigned char> fwd_key, bwd_key;
+    int graphs = 0;
+};
+
+namespace {
+
+void batch_free_device(sonar_batch* b) {
+    for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_scenes, (void*)b->d_prefix,
+                    (void*)b->d_rowmax, (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials,
+                    (void*)b->d_counters})
+        if (p) cudaFree(p);
+    b->d_sens = nullptr; b->d_units = nullptr; b->d_scenes = nullptr; b->d_prefix = nullptr;
+    b->d_rowmax = nullptr; b->d_noised = nullptr; b->d_rowinfo = nullptr; b->d_partials = nullptr;
+    b->d_counters = nullptr;
+    if (b->fwd) cudaGraphExecDestroy(b->fwd);
+    if (b->bwd) cudaGraphExecDestroy(b->bwd);
+    b->fwd = b->bwd = nullptr;
+    b->fwd_key.clear();
+    b->bwd_key.clear();
+}
+
+std::vector<SceneDev> scene_table(const sonar_ctx* ctx) {
+    std::vector<SceneDev> t(ctx->scenes.size());
+    for (size_t k = 0; k < t.size(); ++k) t[k] = scene_dev(ctx->scenes[k]);
+    return t;
+}
+
+sonar_status check_items(sonar_ctx* ctx, const sonar_batch_item* items, int32_t n) {
+    if (!items || n < 1) return fail(ctx, SONAR_ERR_ARG, "batch needs at least one item");
+    for (int k = 0; k < n; ++k) {
+        sonar_status st;
+        if ((st = check_scene(ctx, items[k].scene_id)) || (st = check_sensor(ctx, &items[k].sensor))) {
+            ctx->last_error = "item " + std::to_string(k) + ": " + ctx->last_error;
+            return st;
+        }
+        if (items[k].fan_w < 0 || items[k].fan_h < 0 || (items[k].fan_w > 0) != (items[k].fan_h > 0))
+            return fail(ctx, SONAR_ERR_ARG, "item " + std::to_string(k) + ": bad fan size");
+        if (items[k].polar_offset < 0 || items[k].hits_offset < 0 || items[k].fan_offset < 0)
+            return fail(ctx, SONAR_ERR_ARG, "item " + std::to_string(k) + ": negative offset");
+    }
+    return SONAR_OK;
+}
+
+// (Re)builds descriptors, work units and device buffers from b->items.
+sonar_status batch_plan(sonar_batch* b) {
+    sonar_ctx* ctx = b->ctx;
+    batch_free_device(b);
+    const int n = (int)b->items.size();
+    b->hs.assign(n, SensorDev{});
+    b->units.clear();
+    b->prefix.assign(n + 1, 0);
+    b->smem1 = 0;
+    int64_t rows = 0, polar_end = 0;
+    std::map<int, int64_t> block_votes;
+    for (int k = 0; k < n; ++k) {
+        const sonar_batch_item& it = b->items[k];
+        const Tune t = tune_for(ctx, it.sensor);
+        SensorDev S = make_sensor(it.sensor, it.seed, it.frame, t, it.fan_w, it.fan_h);
+        S.scene = it.scene_id;
+        S.polar_off = it.polar_offset;
+        S.hits_off = it.hits_offset;
+        S.fan_off = it.fan_offset;
+        S.rowmax_off = rows;
+        rows += S.nr;    // room for mode 1; mode 2 uses the first slot of each sensor
+        polar_end = std::max<int64_t>(polar_end, it.polar_offset + (int64_t)S.nr * S.naz);
+        b->hs[k] = S;
+        b->prefix[k + 1] = b->prefix[k] + (int64_t)S.nr * S.naz + (int64_t)S.fan_w * S.fan_h;
+        block_votes[t.block] += (int64_t)S.nb * S.ne;
+        for (int tile = 0; tile < S.n_tiles; ++tile) {
+            Unit u;
+            u.sensor = k;
+            u.c0 = tile * S.cols;
+            u.c1 = std::min(u.c0 + S.cols, S.naz);
+            const int64_t i0 = first_beam_of_col(u.c0, S.nb, S.naz), i1 = first_beam_of_col(u.c1, S.nb, S.naz);
+            u.rays = (int32_t)((i1 - i0) * S.ne);
+            b->units.push_back(u);
+        }
+        b->smem1 = std::max(b->smem1, (size_t)S.nr * S.cols * sizeof(float));
+    }
+    // largest units first: the persistent blocks then finish close together
+    std::stable_sort(b->units.begin(), b->units.end(), [&](const Unit& x, const Unit& y) {
+        return (int64_t)x.rays * 4 + b->hs[x.sensor].nr * (x.c1 - x.c0) / 64 >
+               (int64_t)y.rays * 4 + b->hs[y.sensor].nr * (y.c1 - y.c0) / 64;
+    });
+    b->block = 128;
+    int64_t best = -1;
+    for (auto& kv : block_votes)
+        if (kv.second > best) { best = kv.second; b->block = kv.first; }
+    b->total_rows = rows;
+    b->total_polar = polar_end;
+    b->total2 = b->prefix[n];
+    const size_t nu = b->units.size();
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, std::max(bytes, (size_t)16));
+    };
+    alloc((void**)&b->d_sens, sizeof(SensorDev) * n);
+    alloc((void**)&b->d_units, sizeof(Unit) * nu);
+    alloc((void**)&b->d_scenes, sizeof(SceneDev) * std::max<size_t>(1, ctx->scenes.size()));
+    b->n_scene_table = ctx->scenes.size();
+    alloc((void**)&b->d_prefix, sizeof(int64_t) * (n + 1));
+    alloc((void**)&b->d_rowmax, sizeof(uint32_t) * rows);
+    alloc((void**)&b->d_rowinfo, sizeof(RowInfo) * rows);
+    alloc((void**)&b->d_counters, sizeof(int32_t) * 4);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch allocation");
+    const std::vector<SceneDev> table = scene_table(ctx);
+    e = cudaMemcpy(b->d_sens, b->hs.data(), sizeof(SensorDev) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_units, b->units.data(), sizeof(Unit) * nu, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !table.empty())
+        e = cudaMemcpy(b->d_scenes, table.data(), sizeof(SceneDev) * table.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_prefix, b->prefix.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    return SONAR_OK;
+}
+
+int persistent_grid(const sonar_batch* b, int det) {
+    const int per_sm = phase1_blocks_per_sm(det, b->block, b->smem1);
+    const int64_t g = std::min<int64_t>((int64_t)b->units.size(), (int64_t)b->ctx->sm_count * per_sm);
+    return (int)std::max<int64_t>(1, g);
+}
+
+template <class T>
+void append_bytes(std::vector<unsigned char>& v, const T& x) {
+    const unsigned char* p = (const unsigned char*)&x;
+    v.insert(v.end(), p, p + sizeof(T));
+}
+
+sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
+                                    const sonar_batch_outputs* out, cudaStream_t s) {
+    sonar_ctx* ctx = b->ctx;
+    const int det = p->accumulate == 0;
+    CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+    CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
+    Phase1Args a{};
+    a.sensors = b->d_sens;
+    a.units = b->d_units;
+    a.scenes = b->d_scenes;
+    a.work_counter = b->d_counters;
+    a.n_units = (int32_t)b->units.size();
+    a.n_mat = n_mat;
+    a.theta = d_theta;
+    a.params = *p;
+    a.noised = out->noised ? out->noised : b->d_noised;
+    a.binned = out->binned;
+    a.hits = out->hits;
+    a.rowmax = b->d_rowmax;
+    a.err = ctx->d_err;
+    CU(launch_phase1(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch phase-1 launch");
+    Phase2Args c{};
+    c.sensors = b->d_sens;
+    c.prefix = b->d_prefix;
+    c.n_sensors = (int32_t)b->items.size();
+    c.total = b->total2;
+    c.noised = a.noised;
+    c.rowmax = b->d_rowmax;
+    c.normalise = p->normalise;
+    c.polar = out->polar;
+    c.fan = out->fan;   // NULL: fan pixels are skipped
+    CU(launch_phase2(c, grid2_for(ctx, c.total), 256, s), "batch phase-2 launch");
+    return SONAR_OK;
+}
+
+}  // namespace
+
+extern "C" sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_item* items, int32_t n,
+                                           sonar_batch_t* out) {
+    if (!ctx || !out) return fail(ctx, SONAR_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    sonar_status st = check_items(ctx, items, n);
+    if (st) return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    sonar_batch* b = new sonar_batch();
+    b->ctx = ctx;
+    b->items.assign(items, items + n);
+    st = batch_plan(b);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && st == SONAR_OK; ++k) {
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_stage[k], sizeof(SensorDev) * n);
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void**)&b->h_stage_sc[k], sizeof(SceneDev) * std::max<size_t>(1, 64));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming);
+    }
+    if (st == SONAR_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (st == SONAR_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "batch staging");
+    if (st != SONAR_OK) {
+        sonar_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_item* items, int32_t n, void* stream) {
+    if (!b) return SONAR_ERR_ARG;
+    sonar_ctx* ctx = b->ctx;
+    sonar_status st = check_items(ctx, items, n);
+    if (st) return st;
+    if (n != (int32_t)b->items.size()) return fail(ctx, SONAR_ERR_ARG, "item count differs from the plan");
+    for (int k = 0; k < n; ++k) {
+        const sonar_batch_item& x = items[k];
+        const sonar_batch_item& y = b->items[k];
+        if (x.sensor.n_beams != y.sensor.n_beams || x.sensor.n_elev != y.sensor.n_elev ||
+            x.sensor.n_range_bins != y.sensor.n_range_bins || x.sensor.n_az_bins != y.sensor.n_az_bins ||
+            x.fan_w != y.fan_w || x.fan_h != y.fan_h || x.polar_offset != y.polar_offset ||
+            x.hits_offset != y.hits_offset || x.fan_offset != y.fan_offset)
+            return fail(ctx, SONAR_ERR_ARG, "item " + std::to_string(k) + ": shape or offsets differ from the plan");
+    }
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    bool new_scene = false;
+    for (int k = 0; k < n; ++k) new_scene |= (size_t)items[k].scene_id >= b->n_scene_table;
+    if (new_scene) {
+        // a scene uploaded after planning: rebuild the scene table (synchronous)
+        CU(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronisation");
+        const std::vector<SceneDev> table = scene_table(ctx);
+        SceneDev* d = nullptr;
+        CU(cudaMalloc(&d, sizeof(SceneDev) * table.size()), "scene table");
+        CU(cudaMemcpy(d, table.data(), sizeof(SceneDev) * table.size(), cudaMemcpyHostToDevice), "scene table");
+        cudaFree(b->d_scenes);
+        b->d_scenes = d;
+        b->n_scene_table = table.size();
+        if (b->fwd) cudaGraphExecDestroy(b->fwd);
+        if (b->bwd) cudaGraphExecDestroy(b->bwd);
+        b->fwd = b->bwd = nullptr;
+    }
+    const int slot = b->stage_next;
+    b->stage_next ^= 1;
+    CU(cudaEventSynchronize(b->stage_ev[slot]), "staging wait");
+    for (int k = 0; k < n; ++k) {
+        SensorDev S = b->hs[k];
+        const sonar_batch_item& it = items[k];
+        const SensorDev fresh = make_sensor(it.sensor, it.seed, it.frame, Tune{S.cols, S.mapping, b->block},
+                                            it.fan_w, it.fan_h);
+        memcpy(S.pos, fresh.pos, sizeof S.pos);
+        memcpy(S.rot, fresh.rot, sizeof S.rot);
+        S.hfov = fresh.hfov; S.vfov = fresh.vfov; S.rmin = fresh.rmin; S.rmax = fresh.rmax;
+        S.inv_dr = fresh.inv_dr; S.fan_scale = fresh.fan_scale;
+        S.seed_lo = fresh.seed_lo; S.seed_hi = fresh.seed_hi; S.frame_lo = fresh.frame_lo; S.frame_hi = fresh.frame_hi;
+        S.scene = it.scene_id;
+        b->hs[k] = S;
+        b->h_stage[slot][k] = S;
+        b->items[k] = it;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(b->d_sens, b->h_stage[slot], sizeof(SensorDev) * n, cudaMemcpyHostToDevice, s),
+       "descriptor upload");
+    CU(cudaEventRecord(b->stage_ev[slot], s), "cudaEventRecord");
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* p, const float* d_theta,
+                                           int32_t n_mat, const sonar_batch_outputs* out, void* stream) {
+    if (!b) return SONAR_ERR_ARG;
+    sonar_ctx* ctx = b->ctx;
+    sonar_status st = check_params(ctx, p);
+    if (st) return st;
+    if (!d_theta || !out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "NULL theta or outputs");
+    if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
+    for (const sonar_batch_item& it : b->items)
+        if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!out->noised && !b->d_noised)
+        CU(cudaMalloc(&b->d_noised, sizeof(float) * std::max<int64_t>(1, b->total_polar)), "batch scratch");
+    std::vector<unsigned char> key;
+    append_bytes(key, *p);
+    append_bytes(key, d_theta);
+    append_bytes(key, n_mat);
+    append_bytes(key, *out);
+    if (!b->fwd || key != b->fwd_key) {
+        if (b->fwd) cudaGraphExecDestroy(b->fwd);
+        b->fwd = nullptr;
+        CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+        st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
+        CU(e, "graph capture");
+        const cudaError_t e2 = cudaGraphInstantiate(&b->fwd, g, 0);
+        cudaGraphDestroy(g);
+        CU(e2, "graph instantiation");
+        b->fwd_key = key;
+        ++b->graphs;
+    }
+    CU(cudaGraphLaunch(b->fwd, s), "graph launch");
+    return SONAR_OK;
+}
+
+namespace {
+
+sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
+                                     const float* grad, const float* noised, const sonar_hit* hits, float* dtheta,
+                                     cudaStream_t s) {
+    sonar_ctx* ctx = b->ctx;
+    CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+    if (p->normalise != 0)
+        CU(launch_adj_rows(b->d_sens, SensorDev{}, (int)b->items.size(),
+                           p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
+                           grad, b->d_rowinfo, s),
+           "batch adjoint rows");
+    AdjArgs a{};
+    a.sensors = b->d_sens;
+    a.units = b->d_units;
+    a.scenes = b->d_scenes;
+    a.work_counter = b->d_counters + 1;
+    a.done_counter = b->d_counters + 2;
+    a.n_units = (int32_t)b->units.size();
+    a.n_mat = n_mat;
+    a.theta = d_theta;
+    a.params = *p;
+    a.grad = grad;
+    a.hits = hits;
+    a.rowinfo = b->d_rowinfo;
+    a.partials = b->d_partials;
+    a.dtheta = dtheta;
+    a.err = ctx->d_err;
+    const size_t smem = sizeof(double) * (b->block / 32) * n_mat;
+    const int per_sm = adjoint_blocks_per_sm(hits == nullptr, b->block, smem);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->units.size(),
+                                                                    (int64_t)ctx->sm_count * per_sm));
+    CU(launch_adjoint(a, hits == nullptr, grid, b->block, smem, s), "batch adjoint launch");
+    return SONAR_OK;
+}
+
+}  // namespace
+
+extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar_params* p, const float* d_theta,
+                                                    int32_t n_mat, const float* d_grad, const float* d_noised,
+                                                    const sonar_hit* d_hits, float* d_dtheta, void* stream) {
+    if (!b) return SONAR_ERR_ARG;
+    sonar_ctx* ctx = b->ctx;
+    sonar_status st = check_params(ctx, p);
+    if (st) return st;
+    if (!d_theta || !d_grad || !d_noised || !d_dtheta) return fail(ctx, SONAR_ERR_ARG, "NULL argument");
+    if (d_hits && !aligned16(d_hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
+    for (const sonar_batch_item& it : b->items)
+        if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (n_mat > b->n_mat_cap) {
+        if (b->d_partials) cudaFree(b->d_partials);
+        b->d_partials = nullptr;
+        CU(cudaMalloc(&b->d_partials, sizeof(double) * b->units.size() * (n_mat + 2)), "batch scratch");
+        b->n_mat_cap = n_mat;
+        if (b->bwd) cudaGraphExecDestroy(b->bwd);
+        b->bwd = nullptr;
+    }
+    std::vector<unsigned char> key;
+    append_bytes(key, *p);
+    append_bytes(key, d_theta);
+    append_bytes(key, n_mat);
+    append_bytes(key, d_grad);
+    append_bytes(key, d_noised);
+    append_bytes(key, d_hits);
+    append_bytes(key, d_dtheta);
+    if (!b->bwd || key != b->bwd_key) {
+        if (b->bwd) cudaGraphExecDestroy(b->bwd);
+        b->bwd = nullptr;
+        CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+        st = batch_backward_launches(b, p, d_theta, n_mat, d_grad, d_noised, d_hits, d_dtheta, b->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
+        CU(e, "graph capture");
+        const cudaError_t e2 = cudaGraphInstantiate(&b->bwd, g, 0);
+        cudaGraphDestroy(g);
+        CU(e2, "graph instantiation");
+        b->bwd_key = key;
+        ++b->graphs;
+    }
+    CU(cudaGraphLaunch(b->bwd, (cudaStream_t)stream), "graph launch");
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_batch_info(sonar_batch_t b, int64_t out[5]) {
+    if (!b || !out) return SONAR_ERR_ARG;
+    int64_t rays = 0;
+    for (const SensorDev& S : b->hs) rays += (int64_t)S.nb * S.ne;
+    out[0] = (int64_t)b->units.size();
+    out[1] = rays;
+    out[2] = persistent_grid(b, 1);
+    out[3] = b->block;
+    out[4] = b->graphs;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_batch_destroy(sonar_batch_t b) {
+    if (!b) return SONAR_OK;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    batch_free_device(b);
+    for (int k = 0; k < 2; ++k) {
+        if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+        if (b->h_stage_sc[k]) cudaFreeHost(b->h_stage_sc[k]);
+        if (b->stage_ev[k]) cudaEventDestroy(b->stage_ev[k]);
+    }
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return SONAR_OK;
+}
+
+// ===========================================================================
+// autotuner
+// ===========================================================================
+
+namespace {
+
+// Times the batch's phase-1 + phase-2 launches (no graph) over `reps` runs.
+float time_batch(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
+                 const sonar_batch_outputs* out, cudaStream_t s, int reps) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    batch_forward_launches(b, p, d_theta, n_mat, out, s);   // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) batch_forward_launches(b, p, d_theta, n_mat, out, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
+}
+
+}  // namespace
+
+extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, const float* d_theta, int32_t n_mat,
+                                       const sonar_batch_outputs* out, void* stream) {
+    if (!b) return SONAR_ERR_ARG;
+    sonar_ctx* ctx = b->ctx;
+    sonar_status st = check_params(ctx, p);
+    if (st) return st;
+    if (!d_theta || !out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "NULL theta or outputs");
+    for (const sonar_batch_item& it : b->items)
+        if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!out->noised && !b->d_noised)
+        CU(cudaMalloc(&b->d_noised, sizeof(float) * std::max<int64_t>(1, b->total_polar)), "batch scratch");
+    std::vector<ShapeKey> shapes;
+    for (const sonar_batch_item& it : b->items) {
+        const ShapeKey k{it.sensor.n_beams, it.sensor.n_elev, it.sensor.n_range_bins, it.sensor.n_az_bins};
+        if (std::find(shapes.begin(), shapes.end(), k) == shapes.end()) shapes.push_back(k);
+    }
+    const std::vector<sonar_batch_item> all = b->items;
+    // 1. per shape: columns per unit and lane mapping, timed on that shape's items alone
+    for (const ShapeKey& k : shapes) {
+        std::vector<sonar_batch_item> sub;
+        for (const sonar_batch_item& it : all)
+            if (ShapeKey{it.sensor.n_beams, it.sensor.n_elev, it.sensor.n_range_bins, it.sensor.n_az_bins} == k)
+                sub.push_back(it);
+        b->items = sub;
+        Tune best;
+        float best_ms = 1e30f;
+        for (int block : {64, 128, 256}) {
+            for (int cols : {1, 2, 4, 8, 16, 32}) {
+                if (cols > k[3] || (size_t)cols * k[2] * 4 > kMaxDynSmem / 2) continue;
+                for (int mapping : {0, 1}) {
+                    if (p->accumulate == 0 && mapping == 1) continue;   // keep the canonical fold order
+                    ctx->tune[k] = Tune{cols, mapping, block};
+                    if ((st = batch_plan(b)) != SONAR_OK) goto restore;
+                    const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
+                    if (cudaGetLastError() != cudaSuccess) continue;
+                    if (ms < best_ms) { best_ms = ms; best = Tune{cols, mapping, block}; }
+                }
+            }
+        }
+        ctx->tune[k] = best;
+    }
+restore:
+    b->items = all;
+    {
+        const sonar_status st2 = batch_plan(b);
+        if (st == SONAR_OK) st = st2;
+    }
+    CU(cudaStreamSynchronize(s), "autotune synchronisation");
+    return st;
+}
+
+extern "C" sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count) {
+    if (!ctx || !count) return SONAR_ERR_ARG;
+    int k = 0;
+    for (auto& kv : ctx->tune) {
+        if (rows && k < cap) {
+            int32_t* r = rows + 8 * k;
+            r[0] = kv.first[0]; r[1] = kv.first[1]; r[2] = kv.first[2]; r[3] = kv.first[3];
+            r[4] = kv.second.cols; r[5] = kv.second.mapping; r[6] = kv.second.block; r[7] = 0;
+        }
+        ++k;
+    }
+    *count = k;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int32_t count) {
+    if (!ctx || (!rows && count > 0) || count < 0) return fail(ctx, SONAR_ERR_ARG, "bad tune rows");
+    for (int k = 0; k < count; ++k) {
+        const int32_t* r = rows + 8 * k;
+        if (r[0] < 1 || r[1] < 1 || r[2] < 1 || r[3] < 1 || r[4] < 1 || r[5] < 0 || r[5] > 1 || r[6] < 32 ||
+            r[6] > 512 || (r[6] & 31))
+            return fail(ctx, SONAR_ERR_ARG, "bad tune row " + std::to_string(k));
+        ctx->tune[ShapeKey{r[0], r[1], r[2], r[3]}] = Tune{r[4], r[5], r[6]};
+    }
+    return SONAR_OK;
+}
+
+// ===========================================================================
+// counters
+// ===========================================================================
+
+extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                                          const sonar_params* params, void* stream, int64_t out[6]) {
+    if (!ctx || !out) return fail(ctx, SONAR_ERR_ARG, "NULL argument");
+    sonar_status st;
+    if ((st = check_scene(ctx, scene_id)) || (st = check_sensor(ctx, sensor)) || (st = check_params(ctx, params)))
+        return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const SceneStore& sc = ctx->scenes[scene_id];
+    const int64_t node_words = sc.n_pairs / 32 + 1, tri_words = sc.n_tris / 32 + 1;
+    unsigned long long* cnt = nullptr;
+    uint32_t *nb = nullptr, *tb = nullptr;
+    CU(cudaMalloc(&cnt, sizeof(unsigned long long) * 8), "stats allocation");
+    cudaError_t e = cudaMalloc(&nb, sizeof(uint32_t) * node_words);
+    if (e == cudaSuccess) e = cudaMalloc(&tb, sizeof(uint32_t) * tri_words);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nb, 0, sizeof(uint32_t) * node_words, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tb, 0, sizeof(uint32_t) * tri_words, s);
+    TraceCounters tc{cnt, cnt + 1, cnt + 2, nb, tb};
+    Tune t;
+    t.cols = 1;
+    const SensorDev S = make_sensor(*sensor, 0, 0, t, 0, 0);
+    if (e == cudaSuccess) e = launch_stats(S, scene_dev(sc), *params, tc, ctx->d_err, s);
+    if (e == cudaSuccess) e = launch_popcount(nb, node_words, cnt + 3, s);
+    if (e == cudaSuccess) e = launch_popcount(tb, tri_words, cnt + 4, s);
+    unsigned long long h[8] = {};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(cnt);
+    cudaFree(nb);
+    cudaFree(tb);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trace statistics");
+    out[0] = (int64_t)h[0];
+    out[1] = (int64_t)h[1];
+    out[2] = (int64_t)h[3];
+    out[3] = (int64_t)h[4];
+    out[4] = (int64_t)S.nb * S.ne;
+    out[5] = (int64_t)h[2];
+    return SONAR_OK;
+}

@@ -1,0 +1,51 @@
+// Host-side internal declarations shared by the libsonar translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sonar_internal.cuh"
+
+namespace sonar {
+
+// A built scene: packed hierarchy and triangles (owned by the context).
+struct SceneStore {
+    float4* nodes = nullptr;
+    float4* tris = nullptr;
+    int32_t* mat_orig = nullptr;
+    int32_t root = kEmpty;
+    int64_t n_tris = 0, n_pairs = 0;
+    int32_t height = 0;
+    int32_t max_mat = -1;
+    size_t bytes = 0;
+};
+
+sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, const int32_t* mat,
+                         int64_t nt, cudaStream_t st, SceneStore* out, std::string* msg);
+void free_scene(SceneStore* s);
+
+inline SceneDev scene_dev(const SceneStore& s) {
+    return SceneDev{s.nodes, s.tris, s.mat_orig, s.root, (int32_t)s.n_tris};
+}
+
+// Kernel launchers (render.cu).
+void set_kernel_attributes();
+cudaError_t launch_phase1(const Phase1Args& a, int det, int grid, int block, size_t smem, cudaStream_t st);
+int phase1_blocks_per_sm(int det, int block, size_t smem);
+constexpr size_t kMaxDynSmem = 200 * 1024;
+cudaError_t launch_phase2(const Phase2Args& a, int grid, int block, cudaStream_t st);
+cudaError_t launch_fan(const SensorDev& s, const float* polar, float* fan, cudaStream_t st);
+cudaError_t launch_adj_rows(const SensorDev* sensors, const SensorDev& one, int n_sensors,
+                            int64_t total_groups, int normalise, const float* noised,
+                            const float* grad, RowInfo* info, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, bool recompute, int grid, int block, size_t smem,
+                           cudaStream_t st);
+int adjoint_blocks_per_sm(bool recompute, int block, size_t smem);
+cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
+                         const TraceCounters& tc, uint32_t* err, cudaStream_t st);
+cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out,
+                            cudaStream_t st);
+
+}  // namespace sonar

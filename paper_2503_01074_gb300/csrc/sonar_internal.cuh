@@ -1,0 +1,198 @@
+// Internal device-side definitions of libsonar (GB300, sm_103a).
+//
+// Data layout in HBM
+//   node pairs  float4[4] per internal node p of the LBVH (64 B, 64-B aligned):
+//               [0] (lo0.x, lo0.y, lo0.z, handle0)  [1] (hi0.x, hi0.y, hi0.z, 0)
+//               [2] (lo1.x, lo1.y, lo1.z, handle1)  [3] (hi1.x, hi1.y, hi1.z, 0)
+//               i.e. the two 32-byte child records of p, each loaded as two float4.
+//   handles     int32: >= 0 an internal node pair index; < 0 a leaf
+//               ~((first << 3) | (count - 1)), a run of 1..8 triangles in leaf order.
+//   triangles   float4[3] per triangle in leaf order (48 B):
+//               (v0, material id bits), (v1, caller's index bits), (v2, 0).
+//   polar       [n_range_bins][n_az_bins] f32 per sensor (row = range bin).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sonar.h"
+
+namespace sonar {
+
+constexpr int kLeafMax = 4;          // triangles per collapsed leaf
+constexpr int kStackMax = 64;        // traversal stack entries (tree height is checked at build)
+constexpr int32_t kEmpty = (int32_t)0x80000000;
+constexpr int kMaxMat = 1024;
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+
+__host__ __device__ inline int32_t leaf_handle(int32_t first, int32_t count) {
+    return ~((first << 3) | (count - 1));
+}
+
+// The scene as the kernels see it.
+struct SceneDev {
+    const float4* nodes;      // [n_pairs * 4]
+    const float4* tris;       // [n_tris * 3]
+    const int32_t* mat_orig;  // [n_tris] material of the caller's triangle index
+    int32_t root;             // root handle (kEmpty if the scene has no triangles)
+    int32_t n_tris;
+};
+
+// One sensor of a render, with everything the kernels derive from it.
+struct SensorDev {
+    float pos[3];
+    float rot[9];
+    int32_t nb, ne, nr, naz;
+    float hfov, vfov, rmin, rmax;
+    float inv_dr;        // n_range_bins / (r_max - r_min)
+    float fan_scale;     // fan pixels per metre
+    int32_t fan_w, fan_h;
+    uint32_t seed_lo, seed_hi, frame_lo, frame_hi;
+    int32_t scene;       // index into the scene table
+    int32_t cols;        // azimuth columns per work unit
+    int32_t mapping;     // 0: lanes run along elevation, 1: lanes run along beams
+    int32_t n_tiles;     // work units of this sensor = ceil(naz / cols)
+    int64_t polar_off, hits_off, fan_off, rowmax_off;
+};
+
+// A work unit: the azimuth columns [c0, c1) of one sensor, i.e. every ray
+// of the beams that fall into those columns.
+struct Unit {
+    int32_t sensor;
+    int32_t c0, c1;
+    int32_t rays;
+};
+
+// First beam whose azimuth bin floor((2i+1) naz / (2 nb)) is >= c.
+__host__ __device__ inline int32_t first_beam_of_col(int64_t c, int64_t nb, int64_t naz) {
+    // (2i + 1) naz >= 2 nb c  <=>  i >= (2 nb c - naz) / (2 naz)
+    const int64_t num = 2 * nb * c - naz;
+    if (num <= 0) return 0;
+    const int64_t den = 2 * naz;
+    const int64_t i = (num + den - 1) / den;
+    return (int32_t)(i < nb ? i : nb);
+}
+
+// ---- order-preserving float <-> uint32 encoding (for atomicMax on floats) ----
+__device__ __forceinline__ uint32_t ord_enc(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord_dec(uint32_t e) {
+    return __uint_as_float((e & 0x80000000u) ? (e & 0x7FFFFFFFu) : ~e);
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----
+// Round: multiply words 0 and 2 by the two round multipliers (full 64-bit
+// products); the new words are (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2),
+// hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)); the key advances by the Weyl increments
+// between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// -2 ln u for u = (x + 1) / 2^32, accurate for u near 0 and near 1.
+__device__ __forceinline__ float neg2log_u(uint32_t x) {
+    if (x < 0x80000000u) {
+        return -2.0f * logf(fmaf((float)x, 0x1p-32f, 0x1p-32f));
+    }
+    // u = 1 - (2^32 - 1 - x) / 2^32: log1p keeps the small offset exact
+    return -2.0f * log1pf(-(float)(0xFFFFFFFFu - x) * 0x1p-32f);
+}
+
+// Per-bin noise draws: counter (bin, frame lo, 0, frame hi), key = seed.
+// Word 0 -> Rayleigh(sigma_sa) by inversion; words 1, 2 -> the cosine branch
+// of Box-Muller for N(0, sigma_sm); word 3 unused.
+__device__ __forceinline__ void bin_noise(uint32_t bin, const SensorDev& s, float sigma_sa,
+                                          float sigma_sm, float& w_sa, float& w_sm) {
+    const U4 x = philox10(U4{bin, s.frame_lo, 0u, s.frame_hi}, s.seed_lo, s.seed_hi);
+    w_sa = sigma_sa * sqrtf(neg2log_u(x.x));
+    const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);
+    w_sm = sigma_sm * sqrtf(neg2log_u(x.y)) * cospif(2.0f * u2);
+}
+
+__device__ __forceinline__ float w_sm_of(uint32_t bin, const SensorDev& s, float sigma_sm) {
+    const U4 x = philox10(U4{bin, s.frame_lo, 0u, s.frame_hi}, s.seed_lo, s.seed_hi);
+    const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);
+    return sigma_sm * sqrtf(neg2log_u(x.y)) * cospif(2.0f * u2);
+}
+
+// ---- kernel argument blocks ----
+
+struct TraceCounters {
+    unsigned long long* visits;     // node-pair visits
+    unsigned long long* tests;      // triangle tests
+    unsigned long long* exact;      // tests resolved in FP64
+    uint32_t* node_bits;            // touched node pairs (bitmap)
+    uint32_t* tri_bits;             // touched triangles (bitmap)
+};
+
+struct Phase1Args {
+    const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
+    const Unit* units;          // batch: device work list; single: nullptr
+    const SceneDev* scenes;     // batch: device table; single: nullptr (use `one_scene`)
+    int32_t* work_counter;      // persistent work list counter (nullptr: unit = blockIdx.x)
+    int32_t n_units;
+    int32_t n_mat;
+    SensorDev one;
+    SceneDev one_scene;
+    const float* theta;         // (alpha, gain, mu[...])
+    sonar_params params;
+    float* noised;
+    float* binned;
+    sonar_hit* hits;
+    uint32_t* rowmax;           // ordered-encoded maxima per range row (or per image)
+    uint32_t* err;
+};
+
+struct Phase2Args {
+    const SensorDev* sensors;   // batch: device array; single: nullptr
+    const int64_t* prefix;      // batch: [n_sensors + 1] element prefix; single: nullptr
+    int32_t n_sensors;
+    int64_t total;
+    SensorDev one;
+    const float* noised;
+    const uint32_t* rowmax;
+    int32_t normalise;
+    float* polar;
+    float* fan;
+};
+
+struct RowInfo {
+    float m;        // group maximum of I~ (normalise mode 1: per row; mode 2: whole image)
+    float c;        // sum_k G_k I~_k / m^2
+    int32_t arg;    // bin index of the maximum (lowest on ties) within the sensor image
+    int32_t valid;  // m > 0
+};
+
+struct AdjArgs {
+    const SensorDev* sensors;
+    const Unit* units;
+    const SceneDev* scenes;
+    int32_t* work_counter;
+    int32_t* done_counter;
+    int32_t n_units;
+    int32_t n_mat;
+    SensorDev one;
+    SceneDev one_scene;
+    const float* theta;
+    sonar_params params;
+    const float* grad;          // dL/dN, packed like the polar output
+    const sonar_hit* hits;      // nullptr: re-cast the rays
+    const RowInfo* rowinfo;     // per sensor: at rowmax_off
+    double* partials;           // [n_units][2 + n_mat]
+    float* dtheta;
+    uint32_t* err;
+};
+
+}  // namespace sonar
