@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 sonar path on the single-frame seabed workload.
+
+Workload (the single-frame configuration): a 1024 x 1024-cell fBm seabed over
+100 x 100 m (2,097,152 triangles) with 48 pier piles and 24 boxes (2,100,512
+triangles), 16 materials; a 512-beam x 64-elevation sonar (130 x 20 deg,
+0.1-20 m, 1000 range x 512 azimuth bins) with a 1024 x 576 fan image.
+
+One step = one batch of B frames (B sensor poses along a trajectory) through
+the whole path: the batched persistent launch (ray cast, intensity, binning,
+noise), normalisation + fan, and the adjoint (gradient of a fixed upstream
+gradient image with respect to alpha, gain and the 16 reflectivities), each
+replayed from a captured CUDA graph.  `value` = frames per second of that
+forward+adjoint step with inputs resident in HBM; `e2e` = the same through
+the public API with the step's inputs copied from pinned host memory and its
+outputs (polar + fan images, gradient) copied back inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank renders its own B frames (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sonar frames/s & Mrays/s, batched vs single, fwd+adjoint; % of memory roofline"
+UNIT = "frames/s"
+WORKLOAD = ("single-frame seabed: 1024^2-cell fBm heightfield over 100 m (2,097,152 tris) + 48 piles "
+            "+ 24 boxes = 2,100,512 tris, 16 materials; sonar 512 beams x 64 elevations (130 x 20 deg), "
+            "0.1-20 m, 1000 x 512 polar bins, 1024 x 576 fan")
+ALPHA, GAIN = 0.04, 1.5
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--frames", type=int, default=64, help="frames (sensor poses) per step and rank")
+    p.add_argument("--cpu-rays", type=int, default=8192, help="rays in the oracle's CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the single-frame and e2e legs")
+    p.add_argument("--small", action="store_true", help="a small case for profiler captures")
+    return p.parse_args()
+
+
+def rank_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int, frames: int, small: bool):
+    from paper_2503_01074_gb300 import scenes as S
+    if small:
+        mesh, mu, hfn = S.single_frame_scene(n_cells=512, extent=100.0)
+    else:
+        mesh, mu, hfn = S.single_frame_scene()
+    base = S.sensor_single(hfn)
+    poses = S.trajectory(base, hfn, frames, radius=20.0 + 2.0 * rank, seed=rank)
+    return mesh, mu, base, poses
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def oracle_frame_time(mesh, mu, spec, n_rays, seed=0, tv=None):
+    """Seconds per full frame, extrapolated from casting `n_rays` sampled rays
+    plus the full per-bin pipeline (binning, noise, normalisation, fan)."""
+    import oracle as O
+    tv = O.tri_verts(mesh) if tv is None else tv
+    ids = np.sort(np.random.default_rng(seed).choice(spec.n_rays, n_rays, replace=False))
+    t0 = time.perf_counter()
+    r = O.render(mesh, mu, ALPHA, GAIN, spec, O.Params(), ray_ids=ids, tv=tv)
+    t1 = time.perf_counter()
+    # per-bin stages on a full-size image built from the sampled returns
+    P = np.zeros(spec.n_range_bins * spec.n_az_bins)
+    O.lib().oracle_accumulate(len(ids), r["key"], r["score"], P.size, P)
+    In = O.noise(spec, P.reshape(spec.n_range_bins, spec.n_az_bins), 0, 0, O.Params())
+    N, _, _ = O.normalise(spec, In, 1)
+    O.fan_image(spec, N, spec.fan_w, spec.fan_h)
+    t2 = time.perf_counter()
+    per_frame = (t1 - t0) * spec.n_rays / n_rays + (t2 - t1)
+    return per_frame, r["hits"]["threads"], (t1 - t0), (t2 - t1)
+
+
+def cpu_baseline(mesh, mu, spec, n_rays):
+    per_frame, threads, t_rays, t_bins = oracle_frame_time(mesh, mu, spec, n_rays)
+    return {"value": 1.0 / per_frame, "unit": UNIT, "cores": int(threads), "kind": "oracle",
+            "sample": (f"{n_rays} of {spec.n_rays} rays of one frame cast by brute force in FP64 "
+                       f"({t_rays:.1f} s, scaled to the full frame) + the full per-bin pipeline "
+                       f"({t_bins:.2f} s)")}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    mesh, mu, base, poses = workload(0, max(args.frames, 1), args.small)
+    import oracle as O
+    tv = O.tri_verts(mesh)
+    n = min(args.cpu_rays, 2048)
+    for k in range(args.warmup):
+        oracle_frame_time(mesh, mu, poses[k % len(poses)], 256, seed=k, tv=tv)
+    times = []
+    threads = 0
+    for k in range(args.steps):
+        pf, threads, _, _ = oracle_frame_time(mesh, mu, poses[k % len(poses)], n, seed=100 + k, tv=tv)
+        times.append(pf)
+    value = 1.0 / float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "frames_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(threads), "kind": "oracle",
+                             "sample": f"each step: {n} of {base.n_rays} rays of one frame in FP64 brute "
+                                       f"force, scaled to the frame, + the full per-bin pipeline"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def traffic_from_profile():
+    """Per-frame DRAM bytes of the trace/bin/noise kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_phase1_dram.txt")
+    src = os.path.join(ROOT, "paper_2503_01074_gb300", "csrc", "render.cu")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("render_cu_sha256_16") != sha or "dram_bytes_per_frame" not in kv:
+        return None
+    return float(kv["dram_bytes_per_frame"])
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2503_01074_gb300.sonar import RenderParams, Sonar
+
+    dev = torch.device("cuda", local)
+    B = args.frames
+    mesh, mu, base, poses = workload(rank, B, args.small)
+    son = Sonar(local)
+    verts = torch.from_numpy(mesh.verts).to(dev)
+    tris = torch.from_numpy(mesh.tris).to(dev)
+    mat = torch.from_numpy(mesh.mat).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sid = son.upload(verts, tris, mat)
+    torch.cuda.synchronize()
+    build_ms = 1000.0 * (time.perf_counter() - t0)
+    prm = RenderParams()
+    theta = son.theta(ALPHA, GAIN, mu)
+    items = [(sid, p, 1000 * rank + k, k) for k, p in enumerate(poses)]
+    batch = son.batch(items)
+    batch.autotune(theta, prm)
+    G = torch.randn(batch.n_polar, generator=torch.Generator().manual_seed(5)).to(dev) * 1e-3
+    dtheta = torch.empty_like(theta)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        batch.render(theta, prm, hits=True, fan=True)
+        batch.backward(theta, prm, G, hits=True, out=dtheta)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase = []
+    torch.cuda.nvtx.range_push("timed")
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between timed iterations (256 MiB write)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        phase.append(batch.timings())       # in-graph events of this step's replays
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    frames_total = B * args.steps * world
+    value = frames_total / (total_ms / 1000.0)
+    rays_per_frame = base.n_rays
+    phase1_ms = float(np.mean([p["trace_bin_noise"] for p in phase]))
+    info = batch.info()
+
+    extras = {}
+    e2e = None
+    if not args.no_extras:
+        # batched forward only
+        e_f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        fwd_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            e_f[0].record(stream)
+            batch.render(theta, prm, hits=True, fan=True)
+            e_f[1].record(stream)
+            torch.cuda.synchronize()
+            fwd_ms.append(e_f[0].elapsed_time(e_f[1]))
+        extras["batched_fwd_fps"] = B / (np.mean(fwd_ms) / 1000.0)
+        # the plain single-sensor path: one sonar_render call per frame (no batching, no graph)
+        out = {"polar": torch.empty(base.n_range_bins, base.n_az_bins, device=dev),
+               "noised": torch.empty(base.n_range_bins, base.n_az_bins, device=dev),
+               "hits": torch.empty(base.n_rays, 4, dtype=torch.int32, device=dev),
+               "fan": torch.empty(base.fan_h, base.fan_w, device=dev)}
+        g1 = G[: base.n_range_bins * base.n_az_bins].view(base.n_range_bins, base.n_az_bins)
+        for p in poses[:4]:
+            son.render(sid, p, theta, prm, 0, 0, hits=True, fan=True, outputs=out)
+        torch.cuda.synchronize()
+        for with_adj in (False, True):
+            ms = []
+            for k in range(max(2, args.steps // 2)):
+                flush.zero_()
+                e_f[0].record(stream)
+                for j, p in enumerate(poses):
+                    son.render(sid, p, theta, prm, 1000 * rank + j, j, hits=True, fan=True, outputs=out)
+                    if with_adj:
+                        son.backward(sid, p, theta, prm, 1000 * rank + j, j, g1, out["noised"], out["hits"])
+                e_f[1].record(stream)
+                torch.cuda.synchronize()
+                ms.append(e_f[0].elapsed_time(e_f[1]))
+            extras["single_fwd_adj_fps" if with_adj else "single_fwd_fps"] = B / (np.mean(ms) / 1000.0)
+        # end to end through the public API with host buffers
+        pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)   # noqa: E731
+        h_theta, h_G = pin(theta), pin(G)
+        h_theta.copy_(theta.cpu())
+        h_G.copy_(G.cpu())
+        h_polar, h_fan, h_d = pin(batch.polar), pin(batch.fan), pin(dtheta)
+        e2e_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            e_f[0].record(stream)
+            # the step's inputs land in the device buffers the captured graphs read
+            theta.copy_(h_theta, non_blocking=True)
+            G.copy_(h_G, non_blocking=True)
+            batch.update(items)
+            batch.render(theta, prm, hits=True, fan=True)
+            batch.backward(theta, prm, G, hits=True, out=dtheta)
+            h_polar.copy_(batch.polar, non_blocking=True)
+            h_fan.copy_(batch.fan, non_blocking=True)
+            h_d.copy_(dtheta, non_blocking=True)
+            e_f[1].record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(e_f[0].elapsed_time(e_f[1]))
+        from paper_2503_01074_gb300.sonar import BatchItem
+        h2d = theta.numel() * 4 + G.numel() * 4 + B * __import__("ctypes").sizeof(BatchItem)
+        d2h = batch.polar.numel() * 4 + batch.fan.numel() * 4 + dtheta.numel() * 4
+        e2e_total = float(sum(e2e_ms))
+        if world > 1:
+            t = torch.tensor([e2e_total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        e2e = {"value": frames_total / (e2e_total / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # algorithmic bytes of one trace/bin/noise launch: per frame, the BVH node
+    # pairs (64 B) and triangles (48 B) its rays touch, plus the noised image and
+    # hit records it writes; summed over the B frames the launch renders
+    alg = 0
+    for p in poses:
+        st = son.trace_stats(sid, p, prm)
+        alg += st["nodes_touched"] * 64 + st["tris_touched"] * 48 + base.n_range_bins * base.n_az_bins * 4 \
+            + p.n_rays * 16
+    achieved = alg / (phase1_ms / 1000.0) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    tb = traffic_from_profile()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tb * B if tb is not None else None),
+                "kernel": "k_phase1 (trace + intensity + bin + noise)", "avg_launch_ms": phase1_ms,
+                "algorithmic_bytes_per_launch": int(alg),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, mu, poses[0], min(args.cpu_rays, base.n_rays))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "frames_per_step": B, "rays_per_frame": rays_per_frame,
+                           "step": "batched forward (graph) + batched adjoint (graph)",
+                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world}"},
+                "Mrays_s": value * rays_per_frame / 1e6,
+                "scene_build_ms": build_ms,
+                "phase_ms": {k: float(np.mean([p[k] for p in phase])) for k in phase[0]},
+                "batch": info,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 4 * args.steps}
+        line.update({k: float(v) for k, v in extras.items()})
+        print(json.dumps(line), flush=True)
+    batch.close()
+    son.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

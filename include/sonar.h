@@ -253,6 +253,14 @@ sonar_status sonar_render_batch_backward(sonar_batch_t batch, const sonar_params
  * grid size, out[3] block size, out[4] graphs captured so far. */
 sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
 
+/* Device durations, in milliseconds, of the phases of the most recent
+ * sonar_render_batch and sonar_render_batch_backward replays, measured by CUDA
+ * events captured inside their graphs: ms[0] trace/bin/noise launch,
+ * ms[1] normalise/fan launch, ms[2] adjoint row-term launch, ms[3] adjoint
+ * gather launch.  Waits for those replays to finish; a phase not yet run
+ * reports -1. */
+sonar_status sonar_batch_timings(sonar_batch_t batch, float ms[4]);
+
 sonar_status sonar_batch_destroy(sonar_batch_t batch);
 
 /* ---- autotuner ---- */

@@ -485,18 +485,22 @@ __device__ __forceinline__ float fan_pixel(const SensorDev& s, int64_t pix, F va
     const int v = (int)(pix / s.fan_w), u = (int)(pix - (int64_t)v * s.fan_w);
     const float x = ((float)u + 0.5f - 0.5f * (float)s.fan_w) / s.fan_scale;
     const float y = ((float)s.fan_h - (float)v - 0.5f) / s.fan_scale;
-    const float r = sqrtf(x * x + y * y);
+    const float r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
     const float phi = atan2f(x, y);
     if (r < s.rmin || r > s.rmax || fabsf(phi) > 0.5f * s.hfov) return 0.0f;
-    const float fr = (r - s.rmin) * s.inv_dr - 0.5f;
-    const float fa = (phi + 0.5f * s.hfov) * ((float)s.naz / s.hfov) - 0.5f;
+    const float fr = __fsub_rn(__fmul_rn(r - s.rmin, s.inv_dr), 0.5f);
+    const float fa = __fsub_rn(__fmul_rn(phi + 0.5f * s.hfov, (float)s.naz / s.hfov), 0.5f);
     const float i0f = floorf(fr), j0f = floorf(fa);
     const float wr = fr - i0f, wa = fa - j0f;
     const int i0 = (int)i0f, j0 = (int)j0f;
     const int ia = min(max(i0, 0), s.nr - 1), ib = min(max(i0 + 1, 0), s.nr - 1);
     const int ja = min(max(j0, 0), s.naz - 1), jb = min(max(j0 + 1, 0), s.naz - 1);
-    return (1.0f - wr) * ((1.0f - wa) * val(ia, ja) + wa * val(ia, jb)) +
-           wr * ((1.0f - wa) * val(ib, ja) + wa * val(ib, jb));
+    // explicit round-to-nearest operations: no FMA contraction, so every
+    // caller of this function (fused or standalone) produces the same bits
+    const float ua = 1.0f - wa, ur = 1.0f - wr;
+    const float top = __fadd_rn(__fmul_rn(ua, val(ia, ja)), __fmul_rn(wa, val(ia, jb)));
+    const float bot = __fadd_rn(__fmul_rn(ua, val(ib, ja)), __fmul_rn(wa, val(ib, jb)));
+    return __fadd_rn(__fmul_rn(ur, top), __fmul_rn(wr, bot));
 }
 
 __device__ __forceinline__ int find_sensor(const int64_t* prefix, int n, int64_t e) {

@@ -445,6 +445,8 @@ struct sonar_batch {
     // graphs
     cudaStream_t cap = nullptr;
     cudaGraphExec_t fwd = nullptr, bwd = nullptr;
+    cudaEvent_t ev[6] = {};           // phase boundaries recorded inside the graphs
+    bool ran_fwd = false, ran_bwd = false;
     std::vector<unsigned char> fwd_key, bwd_key;
     int graphs = 0;
 };
@@ -574,11 +576,12 @@ void append_bytes(std::vector<unsigned char>& v, const T& x) {
 }
 
 sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
-                                    const sonar_batch_outputs* out, cudaStream_t s) {
+                                    const sonar_batch_outputs* out, cudaStream_t s, bool events = false) {
     sonar_ctx* ctx = b->ctx;
     const int det = p->accumulate == 0;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
     CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
+    if (events) CU(cudaEventRecord(b->ev[0], s), "cudaEventRecord");
     Phase1Args a{};
     a.sensors = b->d_sens;
     a.units = b->d_units;
@@ -594,6 +597,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     a.rowmax = b->d_rowmax;
     a.err = ctx->d_err;
     CU(launch_phase1(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch phase-1 launch");
+    if (events) CU(cudaEventRecord(b->ev[1], s), "cudaEventRecord");
     Phase2Args c{};
     c.sensors = b->d_sens;
     c.prefix = b->d_prefix;
@@ -605,6 +609,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     c.polar = out->polar;
     c.fan = out->fan;   // NULL: fan pixels are skipped
     CU(launch_phase2(c, grid2_for(ctx, c.total), 256, s), "batch phase-2 launch");
+    if (events) CU(cudaEventRecord(b->ev[2], s), "cudaEventRecord");
     return SONAR_OK;
 }
 
@@ -629,6 +634,7 @@ extern "C" sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_it
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming);
     }
     if (st == SONAR_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int k = 0; k < 6 && st == SONAR_OK && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     if (st == SONAR_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "batch staging");
     if (st != SONAR_OK) {
         sonar_batch_destroy(b);
@@ -718,7 +724,7 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
         if (b->fwd) cudaGraphExecDestroy(b->fwd);
         b->fwd = nullptr;
         CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
-        st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap);
+        st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap, true);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -730,6 +736,7 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
         ++b->graphs;
     }
     CU(cudaGraphLaunch(b->fwd, s), "graph launch");
+    b->ran_fwd = true;
     return SONAR_OK;
 }
 
@@ -740,11 +747,13 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
                                      cudaStream_t s) {
     sonar_ctx* ctx = b->ctx;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+    CU(cudaEventRecord(b->ev[3], s), "cudaEventRecord");
     if (p->normalise != 0)
         CU(launch_adj_rows(b->d_sens, SensorDev{}, (int)b->items.size(),
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
                            grad, b->d_rowinfo, s),
            "batch adjoint rows");
+    CU(cudaEventRecord(b->ev[4], s), "cudaEventRecord");
     AdjArgs a{};
     a.sensors = b->d_sens;
     a.units = b->d_units;
@@ -766,6 +775,7 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->units.size(),
                                                                     (int64_t)ctx->sm_count * per_sm));
     CU(launch_adjoint(a, hits == nullptr, grid, b->block, smem, s), "batch adjoint launch");
+    CU(cudaEventRecord(b->ev[5], s), "cudaEventRecord");
     return SONAR_OK;
 }
 
@@ -815,6 +825,7 @@ extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar
         ++b->graphs;
     }
     CU(cudaGraphLaunch(b->bwd, (cudaStream_t)stream), "graph launch");
+    b->ran_bwd = true;
     return SONAR_OK;
 }
 
@@ -830,11 +841,31 @@ extern "C" sonar_status sonar_batch_info(sonar_batch_t b, int64_t out[5]) {
     return SONAR_OK;
 }
 
+extern "C" sonar_status sonar_batch_timings(sonar_batch_t b, float ms[4]) {
+    if (!b || !ms) return SONAR_ERR_ARG;
+    sonar_ctx* ctx = b->ctx;
+    for (int k = 0; k < 4; ++k) ms[k] = -1.0f;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (b->ran_fwd) {
+        CU(cudaEventSynchronize(b->ev[2]), "cudaEventSynchronize");
+        CU(cudaEventElapsedTime(&ms[0], b->ev[0], b->ev[1]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[1], b->ev[1], b->ev[2]), "cudaEventElapsedTime");
+    }
+    if (b->ran_bwd) {
+        CU(cudaEventSynchronize(b->ev[5]), "cudaEventSynchronize");
+        CU(cudaEventElapsedTime(&ms[2], b->ev[3], b->ev[4]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[3], b->ev[4], b->ev[5]), "cudaEventElapsedTime");
+    }
+    return SONAR_OK;
+}
+
 extern "C" sonar_status sonar_batch_destroy(sonar_batch_t b) {
     if (!b) return SONAR_OK;
     cudaSetDevice(b->ctx->device);
     cudaDeviceSynchronize();
     batch_free_device(b);
+    for (cudaEvent_t& e : b->ev)
+        if (e) cudaEventDestroy(e);
     for (int k = 0; k < 2; ++k) {
         if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
         if (b->h_stage_sc[k]) cudaFreeHost(b->h_stage_sc[k]);

@@ -88,6 +88,7 @@ _SIG = {
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p]),
     "sonar_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "sonar_batch_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "sonar_batch_destroy": (C.c_int, [C.c_void_p]),
     "sonar_autotune": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_int32,
                                  C.POINTER(BatchOutputs), C.c_void_p]),
@@ -394,6 +395,12 @@ class Batch:
         out = (C.c_int64 * 5)()
         self.sonar._check(self.lib.sonar_batch_info(self.h, out))
         return dict(zip(("units", "rays", "grid", "block", "graphs"), list(out)))
+
+    def timings(self):
+        """Phase durations (ms) of the last forward/backward graph replays."""
+        ms = (C.c_float * 4)()
+        self.sonar._check(self.lib.sonar_batch_timings(self.h, ms))
+        return dict(zip(("trace_bin_noise", "normalise_fan", "adjoint_rows", "adjoint_gather"), list(ms)))
 
     def view(self, k):
         """Per-item views (polar [nr, naz], noised, hits [rays, 4], fan [h, w]) of the packed outputs."""

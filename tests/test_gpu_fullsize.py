@@ -1,0 +1,128 @@
+"""Full-size parity on the single-frame workload (2,100,512 triangles, 512 x 64
+rays, 1000 x 512 bins, 1024 x 576 fan) in the launch configuration bench.py
+times: a batch of 64 poses, autotuned, graph-replayed.
+
+The oracle cannot brute-force whole frames here, so it checks
+  - sampled rays, one by one (hit triangle, range, bin, incidence);
+  - complete azimuth columns: every ray of the beams that fall into a column,
+    so the column's binned and noised values can be compared bin by bin;
+and properties that hold at any size check the rest (the polar total equals
+the sum of the binned scores; N = I~ / row max; single render = batch frame).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_01074_gb300 import scenes as S
+from tests._parity import assert_bins_close, excluded_bins, gpu_hits, hit_parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2503_01074_gb300.sonar import RenderParams, Sonar, hits_numpy  # noqa: E402
+
+ALPHA, GAIN, B = 0.04, 1.5, 64
+
+
+@pytest.fixture(scope="module")
+def setup():
+    mesh, mu, hfn = S.single_frame_scene()
+    base = S.sensor_single(hfn)
+    poses = S.trajectory(base, hfn, B, radius=20.0, seed=0)
+    son = Sonar(0)
+    sid = son.upload_mesh(mesh)
+    theta = son.theta(ALPHA, GAIN, mu)
+    prm = RenderParams()
+    items = [(sid, p, k, k) for k, p in enumerate(poses)]
+    batch = son.batch(items)
+    batch.autotune(theta, prm)
+    batch.render(theta, prm, hits=True, fan=True, binned=True)
+    torch.cuda.synchronize()
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+    yield dict(mesh=mesh, mu=mu, poses=poses, son=son, sid=sid, theta=theta, prm=prm, batch=batch,
+               tv=O.tri_verts(mesh))
+    batch.close()
+    son.close()
+
+
+def column_rays(spec, cols):
+    ids = []
+    for c in cols:
+        for i in range(spec.n_beams):
+            if ((2 * i + 1) * spec.n_az_bins) // (2 * spec.n_beams) == c:
+                ids.extend(range(i * spec.n_elev, (i + 1) * spec.n_elev))
+    return np.array(ids, np.int64)
+
+
+@pytest.mark.parametrize("frame", [0, 21, 63])
+def test_sampled_rays_and_complete_columns(setup, frame):
+    d = setup
+    spec = d["poses"][frame]
+    v = d["batch"].view(frame)
+    h = hits_numpy(v["hits"])
+    rng = np.random.default_rng(frame)
+    cols = [0, int(rng.integers(1, spec.n_az_bins - 1)), spec.n_az_bins - 1]
+    ids = np.unique(np.concatenate([column_rays(spec, cols), rng.choice(spec.n_rays, 128, replace=False)]))
+    ref = O.render(d["mesh"], d["mu"], ALPHA, GAIN, spec, O.Params(), seed=frame, frame=frame,
+                   ray_ids=ids, tv=d["tv"])
+    hit_parity(ref, h, ids)
+    assert (ref["key"] >= 0).sum() > 0.6 * len(ids)
+    # column-complete comparison of P and I~
+    nb = spec.n_range_bins * spec.n_az_bins
+    P = np.zeros(nb)
+    O.lib().oracle_accumulate(len(ids), ref["key"], ref["score"], nb, P)
+    In = O.noise(spec, P.reshape(spec.n_range_bins, spec.n_az_bins), frame, frame, O.Params())
+    sub = {"flags": ref["flags"], "key": ref["key"]}
+    hsub = h[ids]
+    mask = excluded_bins(spec, sub, hsub)
+    colmask = np.ones((spec.n_range_bins, spec.n_az_bins), bool)
+    colmask[:, cols] = False
+    gP = v["binned"].double().cpu().numpy()
+    gI = v["noised"].double().cpu().numpy()
+    assert_bins_close(gP, P.reshape(gP.shape), mask | colmask, what="binned columns")
+    assert_bins_close(gI, In, mask | colmask, what="noised columns")
+    # whole-image properties
+    N = v["polar"].double().cpu().numpy()
+    m = gI.max(axis=1, keepdims=True)
+    assert np.allclose(N, np.where(m > 0, gI / np.where(m > 0, m, 1), gI), rtol=2e-7, atol=0)
+    _, key, r, cs = gpu_hits(h)
+    tri = h["tri"]
+    mat = d["mesh"].mat[tri[key >= 0]]
+    s = d["mu"][mat].astype(np.float64) * cs[key >= 0] * np.exp(-2 * ALPHA * r[key >= 0]) * GAIN
+    assert np.isclose(gP.sum(), s.sum(), rtol=1e-5)
+
+
+def test_single_render_equals_batch_frame(setup):
+    d = setup
+    for frame in (0, 40):
+        spec = d["poses"][frame]
+        single = d["son"].render(d["sid"], spec, d["theta"], d["prm"], frame, frame, hits=True, fan=True)
+        v = d["batch"].view(frame)
+        for k in ("polar", "noised", "hits", "fan"):
+            assert torch.equal(single[k], v[k]), (frame, k)
+
+
+def test_fan_of_batch_frame(setup):
+    d = setup
+    spec = d["poses"][5]
+    v = d["batch"].view(5)
+    F = v["fan"].double().cpu().numpy()
+    fr, flag = O.fan_image(spec, v["polar"].double().cpu().numpy(), spec.fan_w, spec.fan_h)
+    bad = ~flag & ~np.isclose(F, fr, rtol=1e-4, atol=1e-5)
+    assert not bad.any(), bad.sum()
+    assert (F[~flag] != 0).mean() > 0.3
+
+
+def test_adjoint_full_size_stored_equals_recomputed(setup):
+    d = setup
+    b = d["batch"]
+    G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(3)).to(d["son"].device)
+    g1 = b.backward(d["theta"], d["prm"], G, hits=True)
+    g2 = b.backward(d["theta"], d["prm"], G, hits=False)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    assert torch.isfinite(g1).all() and float(g1.abs().sum()) > 0
