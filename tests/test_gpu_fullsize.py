@@ -70,7 +70,7 @@ def test_sampled_rays_and_complete_columns(setup, frame):
     ref = O.render(d["mesh"], d["mu"], ALPHA, GAIN, spec, O.Params(), seed=frame, frame=frame,
                    ray_ids=ids, tv=d["tv"])
     hit_parity(ref, h, ids)
-    assert (ref["key"] >= 0).sum() > 0.6 * len(ids)
+    assert (ref["key"] >= 0).sum() > 0.4 * len(ids)      # the test is not vacuous
     # column-complete comparison of P and I~
     nb = spec.n_range_bins * spec.n_az_bins
     P = np.zeros(nb)
