@@ -581,7 +581,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     const int det = p->accumulate == 0;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
     CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
-    if (events) CU(cudaEventRecord(b->ev[0], s), "cudaEventRecord");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
     Phase1Args a{};
     a.sensors = b->d_sens;
     a.units = b->d_units;
@@ -597,7 +597,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     a.rowmax = b->d_rowmax;
     a.err = ctx->d_err;
     CU(launch_phase1(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch phase-1 launch");
-    if (events) CU(cudaEventRecord(b->ev[1], s), "cudaEventRecord");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal), "cudaEventRecord");
     Phase2Args c{};
     c.sensors = b->d_sens;
     c.prefix = b->d_prefix;
@@ -609,7 +609,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     c.polar = out->polar;
     c.fan = out->fan;   // NULL: fan pixels are skipped
     CU(launch_phase2(c, grid2_for(ctx, c.total), 256, s), "batch phase-2 launch");
-    if (events) CU(cudaEventRecord(b->ev[2], s), "cudaEventRecord");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[2], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
 }
 
@@ -747,13 +747,13 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
                                      cudaStream_t s) {
     sonar_ctx* ctx = b->ctx;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
-    CU(cudaEventRecord(b->ev[3], s), "cudaEventRecord");
+    CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
     if (p->normalise != 0)
         CU(launch_adj_rows(b->d_sens, SensorDev{}, (int)b->items.size(),
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
                            grad, b->d_rowinfo, s),
            "batch adjoint rows");
-    CU(cudaEventRecord(b->ev[4], s), "cudaEventRecord");
+    CU(cudaEventRecordWithFlags(b->ev[4], s, cudaEventRecordExternal), "cudaEventRecord");
     AdjArgs a{};
     a.sensors = b->d_sens;
     a.units = b->d_units;
@@ -775,7 +775,7 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->units.size(),
                                                                     (int64_t)ctx->sm_count * per_sm));
     CU(launch_adjoint(a, hits == nullptr, grid, b->block, smem, s), "batch adjoint launch");
-    CU(cudaEventRecord(b->ev[5], s), "cudaEventRecord");
+    CU(cudaEventRecordWithFlags(b->ev[5], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
 }
 
