@@ -168,6 +168,36 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
                           uint64_t seed, uint64_t frame, const sonar_outputs* out,
                           void* stream);
 
+/* Maximum scratch, in 4-byte words, that sonar_render_noalloc can use: the
+ * row maxima (n_range_bins words, or 1 for normalise = 2) plus, when
+ * out->noised is NULL, the noised image (n_range_bins * n_az_bins words,
+ * placed at a 256-byte boundary). */
+#define SONAR_NOALLOC_SCRATCH_WORDS (1u << 20)
+
+/* sonar_render for callers that must not allocate device memory: a render
+ * loop with a fixed memory budget whose device memory is all owned by its
+ * own pool, or real-time code where an allocation could block or
+ * synchronise the device.  This call makes no allocation of any kind: its
+ * scratch is a fixed array of SONAR_NOALLOC_SCRATCH_WORDS words (4 MiB)
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  The caller still provides every input and
+ * output, as for sonar_render, and gets the same results.
+ *   - A frame needing more scratch than the array holds is rejected with
+ *     SONAR_ERR_ARG before anything is enqueued (pass out->noised to need
+ *     only the row maxima).
+ *   - The first call on a device looks up the array's device address (which
+ *     may load the library's device code) and caches it; make that first call
+ *     before any stream capture on that device.
+ *   - All calls on a device share the one array, and it keeps the last
+ *     call's contents (each call clears what it needs cleared): calls whose
+ *     work can overlap on the GPU (different streams, or different contexts
+ *     on the same device) race on it and must be serialised by the caller.
+ * The paper has no counterpart of this entry point. */
+sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                                  const sonar_params* params, const float* d_theta, int32_t n_mat,
+                                  uint64_t seed, uint64_t frame, const sonar_outputs* out,
+                                  void* stream);
+
 /* Resamples any polar image d_polar [n_range_bins][n_az_bins] into a fan
  * image d_fan [fan_h][fan_w]: square pixels, sensor at the bottom centre,
  * scale = min(fan_w / (2 r_max sin(hfov/2)), fan_h / r_max) pixels per metre;

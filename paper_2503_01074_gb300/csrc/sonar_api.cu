@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1024,5 +1025,97 @@ extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, con
     out[3] = (int64_t)h[4];
     out[4] = (int64_t)S.nb * S.ne;
     out[5] = (int64_t)h[2];
+    return SONAR_OK;
+}
+
+// ===========================================================================
+// rendering without device allocation
+// ===========================================================================
+
+namespace {
+
+// The scratch of sonar_render_noalloc: a fixed array in the library's device
+// image, resident on every device that loads the library until the process
+// exits.  Host code cannot use the symbol as a pointer; each device's address
+// comes from cudaGetSymbolAddress.
+static __device__ __align__(256) float g_noalloc_scratch[SONAR_NOALLOC_SCRATCH_WORDS];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[256] = {};
+
+// Device address of the scratch array on `device` (current), looked up once.
+cudaError_t noalloc_scratch(int device, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
+                                             const sonar_params* params, const float* d_theta, int32_t n_mat,
+                                             uint64_t seed, uint64_t frame, const sonar_outputs* out,
+                                             void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    sonar_status st;
+    if ((st = check_scene(ctx, scene_id)) || (st = check_sensor(ctx, sensor)) || (st = check_params(ctx, params)) ||
+        (st = check_nmat(ctx, scene_id, n_mat)))
+        return st;
+    if (!d_theta) return fail(ctx, SONAR_ERR_ARG, "d_theta is NULL");
+    if (!out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "outputs or outputs->polar is NULL");
+    if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
+    if (out->fan && (out->fan_w < 1 || out->fan_h < 1)) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
+    // scratch layout: row maxima at word 0, the noised image (if the caller
+    // passes none) from the next 256-byte boundary
+    const int64_t groups = params->normalise == 1 ? sensor->n_range_bins : 1;
+    const int64_t noised_at = (groups + 63) / 64 * 64;
+    const int64_t npol = (int64_t)sensor->n_range_bins * sensor->n_az_bins;
+    const int64_t need = out->noised ? groups : noised_at + npol;
+    if (need > (int64_t)SONAR_NOALLOC_SCRATCH_WORDS)
+        return fail(ctx, SONAR_ERR_ARG, "sonar_render_noalloc: frame needs " + std::to_string(need) +
+                                            " scratch words, the fixed scratch holds " +
+                                            std::to_string(SONAR_NOALLOC_SCRATCH_WORDS) +
+                                            (out->noised ? "" : " (pass outputs->noised to need fewer)"));
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    void* base = nullptr;
+    CU(noalloc_scratch(ctx->device, &base), "cudaGetSymbolAddress of the fixed scratch");
+    uint32_t* rowmax = (uint32_t*)base;
+    float* noised = out->noised ? out->noised : (float*)base + noised_at;
+    const Tune t = tune_for(ctx, *sensor);
+    const SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
+    // the row maxima must start at zero (the smallest encoded value); the
+    // array still holds the previous call's values
+    CU(cudaMemsetAsync(rowmax, 0, sizeof(uint32_t) * groups, s), "cudaMemsetAsync");
+    Phase1Args a{};
+    a.n_units = S.n_tiles;
+    a.n_mat = n_mat;
+    a.one = S;
+    a.one_scene = scene_dev(ctx->scenes[scene_id]);
+    a.theta = d_theta;
+    a.params = *params;
+    a.noised = noised;
+    a.binned = out->binned;
+    a.hits = out->hits;
+    a.rowmax = rowmax;
+    a.err = ctx->d_err;
+    CU(launch_phase1(a, params->accumulate == 0, S.n_tiles, t.block, (size_t)S.nr * S.cols * sizeof(float), s),
+       "phase-1 launch");
+    Phase2Args b{};
+    b.one = S;
+    b.total = npol + (out->fan ? (int64_t)out->fan_w * out->fan_h : 0);
+    b.noised = noised;
+    b.rowmax = rowmax;
+    b.normalise = params->normalise;
+    b.polar = out->polar;
+    b.fan = out->fan;
+    CU(launch_phase2(b, grid2_for(ctx, b.total), 256, s), "phase-2 launch");
     return SONAR_OK;
 }

@@ -74,6 +74,9 @@ _SIG = {
     "sonar_render": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Sensor), C.POINTER(Params),
                                C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64,
                                C.POINTER(Outputs), C.c_void_p]),
+    "sonar_render_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Sensor), C.POINTER(Params),
+                                       C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64,
+                                       C.POINTER(Outputs), C.c_void_p]),
     "sonar_fan_resample": (C.c_int, [C.c_void_p, C.POINTER(Sensor), C.c_void_p, C.c_int32,
                                      C.c_int32, C.c_void_p, C.c_void_p]),
     "sonar_render_backward": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Sensor), C.POINTER(Params),
