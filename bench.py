@@ -383,7 +383,7 @@ def run_ours(args):
                 "phase_ms": {k: float(np.mean([p[k] for p in phase])) for k in phase[0]},
                 "batch": info,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 4 * args.steps}
+                "gpu_launches": 6 * args.steps}
         line.update({k: float(v) for k, v in extras.items()})
         print(json.dumps(line), flush=True)
     batch.close()

@@ -168,10 +168,9 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
                           uint64_t seed, uint64_t frame, const sonar_outputs* out,
                           void* stream);
 
-/* Maximum scratch, in 4-byte words, that sonar_render_noalloc can use: the
- * row maxima (n_range_bins words, or 1 for normalise = 2) plus, when
- * out->noised is NULL, the noised image (n_range_bins * n_az_bins words,
- * placed at a 256-byte boundary). */
+/* Maximum scratch, in 4-byte words, that sonar_render_noalloc can use: one
+ * word for the image maximum plus, when out->noised is NULL, the noised
+ * image (n_range_bins * n_az_bins words from word 64). */
 #define SONAR_NOALLOC_SCRATCH_WORDS (1u << 20)
 
 /* sonar_render for callers that must not allocate device memory: a render
@@ -183,8 +182,8 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
  * until the process exits.  The caller still provides every input and
  * output, as for sonar_render, and gets the same results.
  *   - A frame needing more scratch than the array holds is rejected with
- *     SONAR_ERR_ARG before anything is enqueued (pass out->noised to need
- *     only the row maxima).
+ *     SONAR_ERR_ARG before anything is enqueued (with out->noised given, one
+ *     word suffices).
  *   - The first call on a device looks up the array's device address (which
  *     may load the library's device code) and caches it; make that first call
  *     before any stream capture on that device.
@@ -260,8 +259,8 @@ sonar_status sonar_batch_update(sonar_batch_t batch, const sonar_batch_item* ite
                                 int32_t n_items, void* stream);
 
 /* Renders every item of the batch: one persistent launch traces, bins and
- * adds noise for all work units (dynamic work list), a second normalises and
- * resamples every fan.  The first call for a given (params, theta, outputs)
+ * adds noise for all work units (dynamic work list); a second normalises
+ * every range row and a third resamples every fan.  The first call for a given (params, theta, outputs)
  * captures the launches in a CUDA graph; later calls with the same arguments
  * replay it.  Results per item equal sonar_render's for the same item and
  * tile shape (bitwise, in deterministic accumulation). */
@@ -285,9 +284,9 @@ sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
 
 /* Device durations, in milliseconds, of the phases of the most recent
  * sonar_render_batch and sonar_render_batch_backward replays, measured by CUDA
- * events captured inside their graphs: ms[0] trace/bin/noise launch,
- * ms[1] normalise/fan launch, ms[2] adjoint row-term launch, ms[3] adjoint
- * gather launch.  Waits for those replays to finish; a phase not yet run
+ * events captured inside their graphs: ms[0] the trace/bin/noise launch,
+ * ms[1] the normalisation and fan launches, ms[2] the adjoint row-term
+ * launch, ms[3] the adjoint gather and final-reduction launches.  Waits for those replays to finish; a phase not yet run
  * reports -1. */
 sonar_status sonar_batch_timings(sonar_batch_t batch, float ms[4]);
 

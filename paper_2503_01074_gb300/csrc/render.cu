@@ -4,13 +4,15 @@
 //                     ray generation -> closest hit (LBVH walk, Moller-Trumbore)
 //                     -> intensity (Eq. 2, two-way) -> polar binning into a
 //                     shared-memory column block -> Eq. 3-6 noise per bin ->
-//                     I~ to HBM + per-row maxima (ordered-int atomicMax).
-//                     Because a unit owns its columns, every polar bin is written
-//                     exactly once: no global atomics, no memset of the image.
-// phase 2 (k_phase2)  range-wise normalisation of every bin and the fan resample
-//                     of every pixel (bilinear over normalised bin centres).
+//                     I~ to HBM.  Because a unit owns its columns, every polar
+//                     bin is written exactly once: no global atomics, no memset
+//                     of the image.
+// k_norm_rows         range-wise normalisation: one warp per range row takes the
+//                     row maximum of I~ and writes N = I~ / max.
+// k_fan_tiles         fan resample of the normalised image, tiles of pixels.
 // adjoint             per-group (row) Jacobian terms, then a per-ray gather of
-//                     dL/dP into (dalpha, dgain, dmu), deterministic reduction.
+//                     dL/dP into (dalpha, dgain, dmu) over ray chunks, and a
+//                     fixed-order final reduction (deterministic).
 //
 // Ray casting precision: the walk and the triangle tests run in FP32.  A test
 // whose barycentric or distance outcome lies inside a certified FP32 error
@@ -446,13 +448,9 @@ __global__ void __launch_bounds__(512) k_phase1(Phase1Args a) {
             acc[k] = In;
         }
         __syncthreads();
-        if (a.params.normalise == 1) {
-            for (int row = tid; row < S.nr; row += nt) {
-                float m = acc[row * cw];
-                for (int c = 1; c < cw; ++c) m = fmaxf(m, acc[row * cw + c]);
-                atomicMax(a.rowmax + S.rowmax_off + row, ord_enc(m));
-            }
-        } else if (a.params.normalise == 2) {
+        if (a.params.normalise == 2) {
+            // one maximum per unit for the whole-image normalisation; range-row
+            // maxima are taken by the normalisation kernel from I~ itself
             float m = -CUDART_INF_F;
             for (int k = tid; k < nbin; k += nt) m = fmaxf(m, acc[k]);
             for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
@@ -468,16 +466,46 @@ __global__ void __launch_bounds__(512) k_phase1(Phase1Args a) {
 }
 
 // ---------------------------------------------------------------------------
-// phase 2: normalisation + fan
+// phase 2a: range-wise normalisation, one warp per (sensor, range row)
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float group_max(const uint32_t* rowmax, const SensorDev& s, int mode, int row) {
-    return ord_dec(rowmax[s.rowmax_off + (mode == 1 ? row : 0)]);
-}
 
 __device__ __forceinline__ float norm_value(float In, float m, int mode) {
     return (mode != 0 && m > 0.0f) ? In / m : In;
 }
+
+// Sensor whose rows [rowmax_off, rowmax_off + nr) contain row g.
+__device__ __forceinline__ int sensor_of_row(const SensorDev* sensors, int n, int64_t g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sensors[mid].rowmax_off <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= a.total_rows) return;
+    const SensorDev& s = a.sensors ? a.sensors[sensor_of_row(a.sensors, a.n_sensors, g)] : a.one;
+    const int row = (int)(g - s.rowmax_off);
+    const int naz = s.naz;
+    const float* In = a.noised + s.polar_off + (int64_t)row * naz;
+    float* out = a.polar + s.polar_off + (int64_t)row * naz;
+    float m = 0.0f;
+    if (a.normalise == 1) {
+        m = -CUDART_INF_F;
+        for (int j = lane; j < naz; j += 32) m = fmaxf(m, In[j]);
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    } else if (a.normalise == 2) {
+        m = ord_dec(a.gmax[s.rowmax_off]);
+    }
+    for (int j = lane; j < naz; j += 32) out[j] = norm_value(In[j], m, a.normalise);
+}
+
+// ---------------------------------------------------------------------------
+// phase 2b: fan resample of the normalised image
+// ---------------------------------------------------------------------------
 
 // Fan pixel value; `val(row, col)` returns the normalised polar value.
 template <class F>
@@ -495,59 +523,41 @@ __device__ __forceinline__ float fan_pixel(const SensorDev& s, int64_t pix, F va
     const int i0 = (int)i0f, j0 = (int)j0f;
     const int ia = min(max(i0, 0), s.nr - 1), ib = min(max(i0 + 1, 0), s.nr - 1);
     const int ja = min(max(j0, 0), s.naz - 1), jb = min(max(j0 + 1, 0), s.naz - 1);
-    // explicit round-to-nearest operations: no FMA contraction, so every
-    // caller of this function (fused or standalone) produces the same bits
     const float ua = 1.0f - wa, ur = 1.0f - wr;
     const float top = __fadd_rn(__fmul_rn(ua, val(ia, ja)), __fmul_rn(wa, val(ia, jb)));
     const float bot = __fadd_rn(__fmul_rn(ua, val(ib, ja)), __fmul_rn(wa, val(ib, jb)));
     return __fadd_rn(__fmul_rn(ur, top), __fmul_rn(wr, bot));
 }
 
-__device__ __forceinline__ int find_sensor(const int64_t* prefix, int n, int64_t e) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__global__ void __launch_bounds__(256) k_phase2(Phase2Args a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.total; e += stride) {
-        const SensorDev* sp;
-        int64_t local;
-        if (a.sensors) {
-            const int si = find_sensor(a.prefix, a.n_sensors, e);
-            sp = a.sensors + si;
-            local = e - a.prefix[si];
+__global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
+    __shared__ SensorDev S;
+    __shared__ int64_t s_base;
+    if (threadIdx.x == 0) {
+        int si = 0;
+        if (a.block_prefix) {
+            int lo = 0, hi = a.n_sensors - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.block_prefix[mid] <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
+            }
+            si = lo;
+            S = a.sensors[si];
+            s_base = (int64_t)(blockIdx.x - a.block_prefix[si]) * kFanTile;
         } else {
-            sp = &a.one;
-            local = e;
-        }
-        const SensorDev& s = *sp;
-        const int64_t npol = (int64_t)s.nr * s.naz;
-        if (local < npol) {
-            const int row = (int)(local / s.naz);
-            const float m = group_max(a.rowmax, s, a.normalise, row);
-            a.polar[s.polar_off + local] = norm_value(a.noised[s.polar_off + local], m, a.normalise);
-        } else if (a.fan) {
-            const int64_t pix = local - npol;
-            const float* In = a.noised + s.polar_off;
-            const uint32_t* rm = a.rowmax;
-            const int mode = a.normalise;
-            a.fan[s.fan_off + pix] = fan_pixel(s, pix, [&](int row, int col) {
-                return norm_value(In[(int64_t)row * s.naz + col], group_max(rm, s, mode, row), mode);
-            });
+            S = a.one;
+            s_base = (int64_t)blockIdx.x * kFanTile;
         }
     }
-}
-
-__global__ void __launch_bounds__(256) k_fan(SensorDev s, const float* polar, float* fan) {
-    const int64_t n = (int64_t)s.fan_w * s.fan_h;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
-        fan[p] = fan_pixel(s, p, [&](int row, int col) { return polar[(int64_t)row * s.naz + col]; });
+    __syncthreads();
+    const int64_t n = (int64_t)S.fan_w * S.fan_h;
+    const float* P = a.polar + S.polar_off;
+    float* F = a.fan + S.fan_off;
+    const int naz = S.naz;
+#pragma unroll 1
+    for (int k = 0; k < kFanTile / 256; ++k) {
+        const int64_t pix = s_base + k * 256 + threadIdx.x;
+        if (pix < n) F[pix] = fan_pixel(S, pix, [&](int row, int col) { return P[(int64_t)row * naz + col]; });
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -566,27 +576,19 @@ __global__ void k_adj_rows(const SensorDev* sensors, SensorDev one, int n_sensor
     if (mode == 1) {
         const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (g >= total) return;
-        int si = 0;
-        if (sensors) {
-            int lo = 0, hi = n_sensors - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sensors[mid].rowmax_off <= g) lo = mid; else hi = mid - 1;
-            }
-            si = lo;
-        }
-        const SensorDev& s = sensors ? sensors[si] : one;
+        const SensorDev& s = sensors ? sensors[sensor_of_row(sensors, n_sensors, g)] : one;
         const int row = (int)(g - s.rowmax_off);
         const float* In = noised + s.polar_off + (int64_t)row * s.naz;
         const float* G = grad + s.polar_off + (int64_t)row * s.naz;
         float m = -CUDART_INF_F;
         int am = 0x7FFFFFFF;
-        double dot = 0.0;
+        float dl = 0.0f;                      // per-lane partial of sum G I~ (few terms)
         for (int j = lane; j < s.naz; j += 32) {
             const float x = In[j];
             if (x > m) { m = x; am = j; }
-            dot += (double)G[j] * (double)x;
+            dl = fmaf(G[j], x, dl);
         }
+        double dot = dl;
         for (int o = 16; o; o >>= 1) {
             const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o);
             const int a2 = __shfl_xor_sync(0xFFFFFFFFu, am, o);
@@ -640,32 +642,17 @@ __global__ void k_adj_rows(const SensorDev* sensors, SensorDev one, int n_sensor
     }
 }
 
-__device__ __forceinline__ void load_unit_adj(const AdjArgs& a, int u, SensorDev* S, SceneDev* SC, Unit* U) {
-    if (a.units) {
-        *U = a.units[u];
-        *S = a.sensors[U->sensor];
-        *SC = a.scenes[S->scene];
-    } else {
-        *S = a.one;
-        *SC = a.one_scene;
-        U->sensor = 0;
-        U->c0 = u * a.one.cols;
-        U->c1 = min(U->c0 + a.one.cols, a.one.naz);
-        U->rays = 0;
-    }
-}
-
-// Per-ray gather of dL/dP and accumulation of dtheta.  Units are the forward's
-// column tiles; each unit's sums go to its own row of `partials` (per-warp
-// material slabs in lane order, per-thread alpha/gain, fixed-order block
-// reductions), and the last block to finish adds the rows in unit order.
+// Per-ray gather of dL/dP and accumulation of dtheta over a unit of rays.
+// Deterministic: each unit's sums go to its own row of `partials` (material
+// sums per warp in lane order, warp slabs added in warp order, alpha/gain per
+// thread then in a fixed tree); k_adj_final adds the rows in a fixed order.
 template <bool RECOMPUTE>
 __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
     extern __shared__ double slab[];   // [n_warps][n_mat]
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
-    __shared__ Unit U;
-    __shared__ int s_unit, s_last;
+    __shared__ AdjUnit U;
+    __shared__ int s_unit;
     __shared__ double s_ag[2][32];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -683,24 +670,29 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
             u = blockIdx.x;
         }
         if (u >= a.n_units) break;
-        if (tid == 0) load_unit_adj(a, u, &S, &SC, &U);
+        if (tid == 0) {
+            if (a.units) {
+                U = a.units[u];
+                S = a.sensors[U.sensor];
+                SC = a.scenes[S.scene];
+            } else {
+                S = a.one;
+                SC = a.one_scene;
+                U.sensor = 0;
+                U.r0 = u * a.chunk;
+                U.r1 = min(U.r0 + a.chunk, a.one.nb * a.one.ne);
+            }
+        }
         for (int k = tid; k < nw * nm; k += nt) slab[k] = 0.0;
         __syncthreads();
-        const int i0 = first_beam_of_col(U.c0, S.nb, S.naz), i1 = first_beam_of_col(U.c1, S.nb, S.naz);
-        const int nbeam = i1 - i0;
-        const int R = nbeam * S.ne;
-        const int mapping = S.mapping;
-        double acc_a = 0.0, acc_g = 0.0;
-        for (int base = 0; base < R; base += nt) {
+        float acc_a = 0.0f, acc_g = 0.0f;
+        for (int base = U.r0; base < U.r1; base += nt) {
             const int r = base + tid;
             bool valid = false;
             int mat = 0;
-            double v_mu = 0.0;
-            if (r < R) {
-                int bi, ej;
-                if (mapping == 0) { bi = r / S.ne; ej = r - bi * S.ne; }
-                else { ej = r / nbeam; bi = r - ej * nbeam; }
-                const int i = i0 + bi, j = ej;
+            float v_mu = 0.0f;
+            if (r < U.r1) {
+                const int i = r / S.ne, j = r - (r / S.ne) * S.ne;
                 uint32_t key, orig;
                 float rr, cf;
                 if (RECOMPUTE) {
@@ -714,7 +706,7 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
                     rr = c.t;
                     cf = c.cosf;
                 } else {
-                    const uint4 h = *reinterpret_cast<const uint4*>(a.hits + S.hits_off + (int64_t)i * S.ne + j);
+                    const uint4 h = *reinterpret_cast<const uint4*>(a.hits + S.hits_off + r);
                     key = h.x;
                     orig = h.y;
                     rr = __uint_as_float(h.z);
@@ -734,26 +726,28 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
                         mat = SC.mat_orig[orig];
                         mat = mat < nm ? mat : nm - 1;
                         const float mu = __ldg(a.theta + 2 + mat);
-                        const float att = expf(-2.0f * alpha * rr);
-                        const double ca = (double)gP * (double)(cf * att);
+                        const float ca = gP * cf * expf(-2.0f * alpha * rr);
                         v_mu = ca * gain;
-                        acc_a += ca * gain * mu * (-2.0 * rr);
-                        acc_g += ca * mu;
+                        acc_a = fmaf(ca * gain * mu, -2.0f * rr, acc_a);
+                        acc_g = fmaf(ca, mu, acc_g);
                         valid = true;
                     }
                 }
             }
-            // material slab of this warp, lanes in order
-            for (int l = 0; l < 32; ++l) {
-                if (lane == l && valid) slab[warp * nm + mat] += v_mu;
-                __syncwarp();
+            // material sums of this warp: one leader per material, lanes in order
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, valid ? mat : -1);
+            if (valid) {
+                float sum = 0.0f;
+                for (uint32_t m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v_mu, __ffs(m) - 1);
+                if (lane == __ffs(peers) - 1) slab[warp * nm + mat] += (double)sum;
             }
         }
+        double da = acc_a, dg = acc_g;
         for (int o = 16; o; o >>= 1) {
-            acc_a += __shfl_down_sync(0xFFFFFFFFu, acc_a, o);
-            acc_g += __shfl_down_sync(0xFFFFFFFFu, acc_g, o);
+            da += __shfl_down_sync(0xFFFFFFFFu, da, o);
+            dg += __shfl_down_sync(0xFFFFFFFFu, dg, o);
         }
-        if (lane == 0) { s_ag[0][warp] = acc_a; s_ag[1][warp] = acc_g; }
+        if (lane == 0) { s_ag[0][warp] = da; s_ag[1][warp] = dg; }
         __syncthreads();
         double* out = a.partials + (int64_t)u * nq;
         for (int m = tid; m < nm; m += nt) {
@@ -769,18 +763,22 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
         }
         __syncthreads();
     }
-    __threadfence();
+}
+
+// dtheta[q] = sum over units of partials[u][q]: a fixed strided split over the
+// threads, then a fixed tree.
+__global__ void __launch_bounds__(256) k_adj_final(const double* partials, int n_units, int nq, float* dtheta) {
+    __shared__ double red[256];
+    const int q = blockIdx.x;
+    double v = 0.0;
+    for (int u = threadIdx.x; u < n_units; u += 256) v += partials[(int64_t)u * nq + q];
+    red[threadIdx.x] = v;
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(a.done_counter, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        for (int q = tid; q < nq; q += nt) {
-            double v = 0.0;
-            for (int u = 0; u < a.n_units; ++u) v += __ldcg(a.partials + (int64_t)u * nq + q);
-            a.dtheta[q] = (float)v;
-        }
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) dtheta[q] = (float)red[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -829,15 +827,14 @@ int phase1_blocks_per_sm(int det, int block, size_t smem) {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_phase2(const Phase2Args& a, int grid, int block, cudaStream_t st) {
-    k_phase2<<<grid, block, 0, st>>>(a);
+cudaError_t launch_norm(const NormArgs& a, cudaStream_t st) {
+    const int64_t threads = a.total_rows * 32;
+    k_norm_rows<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fan(const SensorDev& s, const float* polar, float* fan, cudaStream_t st) {
-    const int64_t n = (int64_t)s.fan_w * s.fan_h;
-    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_fan<<<grid > 0 ? grid : 1, 256, 0, st>>>(s, polar, fan);
+cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st) {
+    if (blocks > 0) k_fan_tiles<<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -856,9 +853,12 @@ cudaError_t launch_adj_rows(const SensorDev* sensors, const SensorDev& one, int 
 }
 
 cudaError_t launch_adjoint(const AdjArgs& a, bool recompute, int grid, int block, size_t smem,
-                           cudaStream_t st) {
+                           float* dtheta, cudaStream_t st) {
     if (recompute) k_adjoint<true><<<grid, block, smem, st>>>(a);
     else k_adjoint<false><<<grid, block, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adj_final<<<a.n_mat + 2, 256, 0, st>>>(a.partials, a.n_units, a.n_mat + 2, dtheta);
     return cudaGetLastError();
 }
 

@@ -173,11 +173,6 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     return d;
 }
 
-int grid2_for(const sonar_ctx* ctx, int64_t total) {
-    const int64_t g = (total + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)ctx->sm_count * 8));
-}
-
 }  // namespace
 
 // ===========================================================================
@@ -298,6 +293,36 @@ namespace {
 
 size_t phase1_smem(const SensorDev& s) { return (size_t)s.nr * s.cols * sizeof(float); }
 
+// Normalisation and fan of one sensor (polar_off = fan_off = rowmax_off = 0).
+sonar_status single_post(sonar_ctx* ctx, const SensorDev& S, int normalise, const float* noised,
+                         const uint32_t* gmax, float* polar, float* fan, cudaStream_t s) {
+    NormArgs n{};
+    n.one = S;
+    n.total_rows = S.nr;
+    n.noised = noised;
+    n.gmax = gmax;
+    n.normalise = normalise;
+    n.polar = polar;
+    CU(launch_norm(n, s), "normalisation launch");
+    if (fan) {
+        FanArgs f{};
+        f.one = S;
+        f.polar = polar;
+        f.fan = fan;
+        const int64_t px = (int64_t)S.fan_w * S.fan_h;
+        CU(launch_fan_tiles(f, (int)((px + kFanTile - 1) / kFanTile), s), "fan launch");
+    }
+    return SONAR_OK;
+}
+
+// Rays per adjoint work unit: about four units per SM over the whole render,
+// a multiple of the block size.
+int adj_chunk(int64_t rays, int sm_count, int block) {
+    int64_t c = rays / (4 * (int64_t)sm_count);
+    c = (c + block - 1) / block * block;
+    return (int)std::max<int64_t>(block, std::min<int64_t>(c, 64ll * block));
+}
+
 }  // namespace
 
 extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
@@ -323,9 +348,8 @@ extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const so
         CU(grow(ctx->noised, sizeof(float) * npol, s), "scratch allocation");
         noised = (float*)ctx->noised.p;
     }
-    const int groups = params->normalise == 1 ? S.nr : 1;
-    CU(grow(ctx->rowmax, sizeof(uint32_t) * groups, s), "scratch allocation");
-    CU(cudaMemsetAsync(ctx->rowmax.p, 0, sizeof(uint32_t) * groups, s), "cudaMemsetAsync");
+    CU(grow(ctx->rowmax, sizeof(uint32_t), s), "scratch allocation");
+    if (params->normalise == 2) CU(cudaMemsetAsync(ctx->rowmax.p, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
 
     Phase1Args a{};
     a.n_units = S.n_tiles;
@@ -340,17 +364,8 @@ extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const so
     a.rowmax = (uint32_t*)ctx->rowmax.p;
     a.err = ctx->d_err;
     CU(launch_phase1(a, params->accumulate == 0, S.n_tiles, t.block, phase1_smem(S), s), "phase-1 launch");
-
-    Phase2Args b{};
-    b.one = S;
-    b.total = npol + (out->fan ? (int64_t)out->fan_w * out->fan_h : 0);
-    b.noised = noised;
-    b.rowmax = (const uint32_t*)ctx->rowmax.p;
-    b.normalise = params->normalise;
-    b.polar = out->polar;
-    b.fan = out->fan;
-    CU(launch_phase2(b, grid2_for(ctx, b.total), 256, s), "phase-2 launch");
-    return SONAR_OK;
+    (void)npol;
+    return single_post(ctx, S, params->normalise, noised, (const uint32_t*)ctx->rowmax.p, out->polar, out->fan, s);
 }
 
 extern "C" sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* sensor, const float* d_polar,
@@ -364,7 +379,12 @@ extern "C" sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* 
     Tune t;
     t.cols = 1;
     const SensorDev S = make_sensor(*sensor, 0, 0, t, fan_w, fan_h);
-    CU(launch_fan(S, d_polar, d_fan, (cudaStream_t)stream), "fan launch");
+    FanArgs f{};
+    f.one = S;
+    f.polar = d_polar;
+    f.fan = d_fan;
+    const int64_t px = (int64_t)fan_w * fan_h;
+    CU(launch_fan_tiles(f, (int)((px + kFanTile - 1) / kFanTile), (cudaStream_t)stream), "fan launch");
     return SONAR_OK;
 }
 
@@ -388,16 +408,17 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     const int groups = params->normalise == 1 ? S.nr : 1;
     CU(grow(ctx->rowinfo, sizeof(RowInfo) * groups, s), "scratch allocation");
     const int nq = n_mat + 2;
-    CU(grow(ctx->partials, sizeof(double) * (size_t)S.n_tiles * nq, s), "scratch allocation");
-    CU(grow(ctx->counters, sizeof(int32_t) * 4, s), "scratch allocation");
-    CU(cudaMemsetAsync(ctx->counters.p, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+    const int64_t rays = (int64_t)S.nb * S.ne;
+    const int chunk = adj_chunk(rays, ctx->sm_count, t.block);
+    const int n_units = (int)((rays + chunk - 1) / chunk);
+    CU(grow(ctx->partials, sizeof(double) * (size_t)n_units * nq, s), "scratch allocation");
     if (params->normalise != 0)
         CU(launch_adj_rows(nullptr, S, 1, groups, params->normalise, d_noised, d_grad_polar,
                            (RowInfo*)ctx->rowinfo.p, s),
            "adjoint row launch");
     AdjArgs a{};
-    a.done_counter = (int32_t*)ctx->counters.p + 1;
-    a.n_units = S.n_tiles;
+    a.n_units = n_units;
+    a.chunk = chunk;
     a.n_mat = n_mat;
     a.one = S;
     a.one_scene = scene_dev(ctx->scenes[scene_id]);
@@ -407,10 +428,9 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     a.hits = d_hits;
     a.rowinfo = (const RowInfo*)ctx->rowinfo.p;
     a.partials = (double*)ctx->partials.p;
-    a.dtheta = d_dtheta;
     a.err = ctx->d_err;
     const size_t smem = sizeof(double) * (t.block / 32) * n_mat;
-    CU(launch_adjoint(a, d_hits == nullptr, S.n_tiles, t.block, smem, s), "adjoint launch");
+    CU(launch_adjoint(a, d_hits == nullptr, n_units, t.block, smem, d_dtheta, s), "adjoint launch");
     return SONAR_OK;
 }
 
@@ -422,20 +442,23 @@ struct sonar_batch {
     sonar_ctx* ctx = nullptr;
     std::vector<sonar_batch_item> items;
     std::vector<SensorDev> hs;        // host copy of the descriptors
-    std::vector<Unit> units;
-    std::vector<int64_t> prefix;      // phase-2 element prefix
-    int64_t total_rows = 0, total_polar = 0, total2 = 0;
+    std::vector<Unit> units;          // forward work list (column tiles)
+    std::vector<AdjUnit> adj_units;   // adjoint work list (ray chunks)
+    std::vector<int32_t> fan_prefix;  // fan blocks per sensor, prefix
+    int64_t total_rows = 0, total_polar = 0;
     int block = 128;
+    int adj_chunk = 0;
     size_t smem1 = 0;
     SensorDev* d_sens = nullptr;
     Unit* d_units = nullptr;
+    AdjUnit* d_adj_units = nullptr;
     SceneDev* d_scenes = nullptr;
-    int64_t* d_prefix = nullptr;
+    int32_t* d_fan_prefix = nullptr;
     uint32_t* d_rowmax = nullptr;
     float* d_noised = nullptr;
     RowInfo* d_rowinfo = nullptr;
     double* d_partials = nullptr;
-    int32_t* d_counters = nullptr;    // [0] phase-1 work, [1] adjoint work, [2] adjoint done
+    int32_t* d_counters = nullptr;    // [0] phase-1 work, [1] adjoint work
     int n_mat_cap = 0;
     size_t n_scene_table = 0;         // entries in d_scenes
     // host staging for updates (pinned, double-buffered)
@@ -455,11 +478,13 @@ struct sonar_batch {
 namespace {
 
 void batch_free_device(sonar_batch* b) {
-    for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_scenes, (void*)b->d_prefix,
-                    (void*)b->d_rowmax, (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials,
-                    (void*)b->d_counters})
+    for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_adj_units, (void*)b->d_scenes,
+                    (void*)b->d_fan_prefix, (void*)b->d_rowmax, (void*)b->d_noised, (void*)b->d_rowinfo,
+                    (void*)b->d_partials, (void*)b->d_counters})
         if (p) cudaFree(p);
-    b->d_sens = nullptr; b->d_units = nullptr; b->d_scenes = nullptr; b->d_prefix = nullptr;
+    b->n_mat_cap = 0;
+    b->d_sens = nullptr; b->d_units = nullptr; b->d_adj_units = nullptr; b->d_scenes = nullptr;
+    b->d_fan_prefix = nullptr;
     b->d_rowmax = nullptr; b->d_noised = nullptr; b->d_rowinfo = nullptr; b->d_partials = nullptr;
     b->d_counters = nullptr;
     if (b->fwd) cudaGraphExecDestroy(b->fwd);
@@ -498,7 +523,8 @@ sonar_status batch_plan(sonar_batch* b) {
     const int n = (int)b->items.size();
     b->hs.assign(n, SensorDev{});
     b->units.clear();
-    b->prefix.assign(n + 1, 0);
+    b->adj_units.clear();
+    b->fan_prefix.assign(n + 1, 0);
     b->smem1 = 0;
     int64_t rows = 0, polar_end = 0;
     std::map<int, int64_t> block_votes;
@@ -514,7 +540,8 @@ sonar_status batch_plan(sonar_batch* b) {
         rows += S.nr;    // room for mode 1; mode 2 uses the first slot of each sensor
         polar_end = std::max<int64_t>(polar_end, it.polar_offset + (int64_t)S.nr * S.naz);
         b->hs[k] = S;
-        b->prefix[k + 1] = b->prefix[k] + (int64_t)S.nr * S.naz + (int64_t)S.fan_w * S.fan_h;
+        b->fan_prefix[k + 1] =
+            b->fan_prefix[k] + (int32_t)(((int64_t)S.fan_w * S.fan_h + kFanTile - 1) / kFanTile);
         block_votes[t.block] += (int64_t)S.nb * S.ne;
         for (int tile = 0; tile < S.n_tiles; ++tile) {
             Unit u;
@@ -538,8 +565,15 @@ sonar_status batch_plan(sonar_batch* b) {
         if (kv.second > best) { best = kv.second; b->block = kv.first; }
     b->total_rows = rows;
     b->total_polar = polar_end;
-    b->total2 = b->prefix[n];
-    const size_t nu = b->units.size();
+    int64_t all_rays = 0;
+    for (const SensorDev& S : b->hs) all_rays += (int64_t)S.nb * S.ne;
+    b->adj_chunk = adj_chunk(all_rays, ctx->sm_count, b->block);
+    for (int k = 0; k < n; ++k) {
+        const int64_t r = (int64_t)b->hs[k].nb * b->hs[k].ne;
+        for (int64_t r0 = 0; r0 < r; r0 += b->adj_chunk)
+            b->adj_units.push_back(AdjUnit{k, (int32_t)r0, (int32_t)std::min<int64_t>(r, r0 + b->adj_chunk), 0});
+    }
+    const size_t nu = b->units.size(), na = b->adj_units.size();
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, std::max(bytes, (size_t)16));
@@ -548,7 +582,8 @@ sonar_status batch_plan(sonar_batch* b) {
     alloc((void**)&b->d_units, sizeof(Unit) * nu);
     alloc((void**)&b->d_scenes, sizeof(SceneDev) * std::max<size_t>(1, ctx->scenes.size()));
     b->n_scene_table = ctx->scenes.size();
-    alloc((void**)&b->d_prefix, sizeof(int64_t) * (n + 1));
+    alloc((void**)&b->d_adj_units, sizeof(AdjUnit) * na);
+    alloc((void**)&b->d_fan_prefix, sizeof(int32_t) * (n + 1));
     alloc((void**)&b->d_rowmax, sizeof(uint32_t) * rows);
     alloc((void**)&b->d_rowinfo, sizeof(RowInfo) * rows);
     alloc((void**)&b->d_counters, sizeof(int32_t) * 4);
@@ -559,7 +594,9 @@ sonar_status batch_plan(sonar_batch* b) {
     if (e == cudaSuccess && !table.empty())
         e = cudaMemcpy(b->d_scenes, table.data(), sizeof(SceneDev) * table.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_prefix, b->prefix.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_adj_units, b->adj_units.data(), sizeof(AdjUnit) * na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_fan_prefix, b->fan_prefix.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
     return SONAR_OK;
 }
@@ -581,7 +618,8 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     sonar_ctx* ctx = b->ctx;
     const int det = p->accumulate == 0;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
-    CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
+    if (p->normalise == 2)
+        CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
     if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
     Phase1Args a{};
     a.sensors = b->d_sens;
@@ -599,17 +637,24 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     a.err = ctx->d_err;
     CU(launch_phase1(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch phase-1 launch");
     if (events) CU(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal), "cudaEventRecord");
-    Phase2Args c{};
+    NormArgs c{};
     c.sensors = b->d_sens;
-    c.prefix = b->d_prefix;
     c.n_sensors = (int32_t)b->items.size();
-    c.total = b->total2;
+    c.total_rows = b->total_rows;
     c.noised = a.noised;
-    c.rowmax = b->d_rowmax;
+    c.gmax = b->d_rowmax;
     c.normalise = p->normalise;
     c.polar = out->polar;
-    c.fan = out->fan;   // NULL: fan pixels are skipped
-    CU(launch_phase2(c, grid2_for(ctx, c.total), 256, s), "batch phase-2 launch");
+    CU(launch_norm(c, s), "batch normalisation launch");
+    if (out->fan) {
+        FanArgs f{};
+        f.sensors = b->d_sens;
+        f.block_prefix = b->d_fan_prefix;
+        f.n_sensors = (int32_t)b->items.size();
+        f.polar = out->polar;
+        f.fan = out->fan;
+        CU(launch_fan_tiles(f, b->fan_prefix.back(), s), "batch fan launch");
+    }
     if (events) CU(cudaEventRecordWithFlags(b->ev[2], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
 }
@@ -757,11 +802,11 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     CU(cudaEventRecordWithFlags(b->ev[4], s, cudaEventRecordExternal), "cudaEventRecord");
     AdjArgs a{};
     a.sensors = b->d_sens;
-    a.units = b->d_units;
+    a.units = b->d_adj_units;
     a.scenes = b->d_scenes;
     a.work_counter = b->d_counters + 1;
-    a.done_counter = b->d_counters + 2;
-    a.n_units = (int32_t)b->units.size();
+    a.n_units = (int32_t)b->adj_units.size();
+    a.chunk = b->adj_chunk;
     a.n_mat = n_mat;
     a.theta = d_theta;
     a.params = *p;
@@ -769,13 +814,12 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     a.hits = hits;
     a.rowinfo = b->d_rowinfo;
     a.partials = b->d_partials;
-    a.dtheta = dtheta;
     a.err = ctx->d_err;
     const size_t smem = sizeof(double) * (b->block / 32) * n_mat;
     const int per_sm = adjoint_blocks_per_sm(hits == nullptr, b->block, smem);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->units.size(),
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->adj_units.size(),
                                                                     (int64_t)ctx->sm_count * per_sm));
-    CU(launch_adjoint(a, hits == nullptr, grid, b->block, smem, s), "batch adjoint launch");
+    CU(launch_adjoint(a, hits == nullptr, grid, b->block, smem, dtheta, s), "batch adjoint launch");
     CU(cudaEventRecordWithFlags(b->ev[5], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
 }
@@ -797,7 +841,7 @@ extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar
     if (n_mat > b->n_mat_cap) {
         if (b->d_partials) cudaFree(b->d_partials);
         b->d_partials = nullptr;
-        CU(cudaMalloc(&b->d_partials, sizeof(double) * b->units.size() * (n_mat + 2)), "batch scratch");
+        CU(cudaMalloc(&b->d_partials, sizeof(double) * b->adj_units.size() * (n_mat + 2)), "batch scratch");
         b->n_mat_cap = n_mat;
         if (b->bwd) cudaGraphExecDestroy(b->bwd);
         b->bwd = nullptr;
@@ -1072,12 +1116,11 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     if (!out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "outputs or outputs->polar is NULL");
     if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
     if (out->fan && (out->fan_w < 1 || out->fan_h < 1)) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
-    // scratch layout: row maxima at word 0, the noised image (if the caller
-    // passes none) from the next 256-byte boundary
-    const int64_t groups = params->normalise == 1 ? sensor->n_range_bins : 1;
-    const int64_t noised_at = (groups + 63) / 64 * 64;
+    // scratch layout: the image maximum (normalise = 2) at word 0, the noised
+    // image (if the caller passes none) from the next 256-byte boundary
+    const int64_t noised_at = 64;
     const int64_t npol = (int64_t)sensor->n_range_bins * sensor->n_az_bins;
-    const int64_t need = out->noised ? groups : noised_at + npol;
+    const int64_t need = out->noised ? 1 : noised_at + npol;
     if (need > (int64_t)SONAR_NOALLOC_SCRATCH_WORDS)
         return fail(ctx, SONAR_ERR_ARG, "sonar_render_noalloc: frame needs " + std::to_string(need) +
                                             " scratch words, the fixed scratch holds " +
@@ -1091,9 +1134,9 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     float* noised = out->noised ? out->noised : (float*)base + noised_at;
     const Tune t = tune_for(ctx, *sensor);
     const SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
-    // the row maxima must start at zero (the smallest encoded value); the
-    // array still holds the previous call's values
-    CU(cudaMemsetAsync(rowmax, 0, sizeof(uint32_t) * groups, s), "cudaMemsetAsync");
+    // the maximum must start at zero (the smallest encoded value); the array
+    // still holds the previous call's values
+    if (params->normalise == 2) CU(cudaMemsetAsync(rowmax, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
     Phase1Args a{};
     a.n_units = S.n_tiles;
     a.n_mat = n_mat;
@@ -1108,14 +1151,5 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     a.err = ctx->d_err;
     CU(launch_phase1(a, params->accumulate == 0, S.n_tiles, t.block, (size_t)S.nr * S.cols * sizeof(float), s),
        "phase-1 launch");
-    Phase2Args b{};
-    b.one = S;
-    b.total = npol + (out->fan ? (int64_t)out->fan_w * out->fan_h : 0);
-    b.noised = noised;
-    b.rowmax = rowmax;
-    b.normalise = params->normalise;
-    b.polar = out->polar;
-    b.fan = out->fan;
-    CU(launch_phase2(b, grid2_for(ctx, b.total), 256, s), "phase-2 launch");
-    return SONAR_OK;
+    return single_post(ctx, S, params->normalise, noised, rowmax, out->polar, out->fan, s);
 }

@@ -35,13 +35,13 @@ void set_kernel_attributes();
 cudaError_t launch_phase1(const Phase1Args& a, int det, int grid, int block, size_t smem, cudaStream_t st);
 int phase1_blocks_per_sm(int det, int block, size_t smem);
 constexpr size_t kMaxDynSmem = 200 * 1024;
-cudaError_t launch_phase2(const Phase2Args& a, int grid, int block, cudaStream_t st);
-cudaError_t launch_fan(const SensorDev& s, const float* polar, float* fan, cudaStream_t st);
+cudaError_t launch_norm(const NormArgs& a, cudaStream_t st);
+cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_adj_rows(const SensorDev* sensors, const SensorDev& one, int n_sensors,
                             int64_t total_groups, int normalise, const float* noised,
                             const float* grad, RowInfo* info, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, bool recompute, int grid, int block, size_t smem,
-                           cudaStream_t st);
+                           float* dtheta, cudaStream_t st);
 int adjoint_blocks_per_sm(bool recompute, int block, size_t smem);
 cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
                          const TraceCounters& tc, uint32_t* err, cudaStream_t st);

@@ -155,17 +155,33 @@ struct Phase1Args {
     uint32_t* err;
 };
 
-struct Phase2Args {
-    const SensorDev* sensors;   // batch: device array; single: nullptr
-    const int64_t* prefix;      // batch: [n_sensors + 1] element prefix; single: nullptr
+// Normalisation: one warp per (sensor, range row).
+struct NormArgs {
+    const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
     int32_t n_sensors;
-    int64_t total;
+    int64_t total_rows;         // sum of n_range_bins over the sensors
     SensorDev one;
     const float* noised;
-    const uint32_t* rowmax;
+    const uint32_t* gmax;       // normalise = 2: ordered-encoded image maximum at rowmax_off
     int32_t normalise;
     float* polar;
+};
+
+constexpr int kFanTile = 1024;  // fan pixels per block
+
+// Fan resample: blocks of kFanTile pixels of one sensor, reading the normalised image.
+struct FanArgs {
+    const SensorDev* sensors;   // batch: device array; single: nullptr
+    const int32_t* block_prefix;  // batch: [n_sensors + 1] fan-block prefix; single: nullptr
+    int32_t n_sensors;
+    SensorDev one;
+    const float* polar;
     float* fan;
+};
+
+// A work unit of the adjoint: canonical rays [r0, r1) of one sensor.
+struct AdjUnit {
+    int32_t sensor, r0, r1, pad;
 };
 
 struct RowInfo {
@@ -177,12 +193,12 @@ struct RowInfo {
 
 struct AdjArgs {
     const SensorDev* sensors;
-    const Unit* units;
+    const AdjUnit* units;       // batch: device work list; single: nullptr (chunks of `chunk` rays)
     const SceneDev* scenes;
-    int32_t* work_counter;
-    int32_t* done_counter;
+    int32_t* work_counter;      // persistent work list counter (nullptr: unit = blockIdx.x)
     int32_t n_units;
     int32_t n_mat;
+    int32_t chunk;
     SensorDev one;
     SceneDev one_scene;
     const float* theta;
@@ -191,7 +207,6 @@ struct AdjArgs {
     const sonar_hit* hits;      // nullptr: re-cast the rays
     const RowInfo* rowinfo;     // per sensor: at rowmax_off
     double* partials;           // [n_units][2 + n_mat]
-    float* dtheta;
     uint32_t* err;
 };
 
