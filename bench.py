@@ -195,7 +195,7 @@ def run_reference(args):
 def traffic_from_profile():
     """Per-frame DRAM bytes of the trace/bin/noise kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_phase1_dram.txt")
+    path = os.path.join(ROOT, "profiles", "k_trace_dram.txt")
     src = os.path.join(ROOT, "paper_2503_01074_gb300", "csrc", "render.cu")
     if not os.path.exists(path):
         return None
@@ -273,7 +273,8 @@ def run_ours(args):
     frames_total = B * args.steps * world
     value = frames_total / (total_ms / 1000.0)
     rays_per_frame = base.n_rays
-    phase1_ms = float(np.mean([p["trace_bin_noise"] for p in phase]))
+    trace_ms = float(np.mean([p["trace"] for p in phase]))
+    bin_ms = float(np.mean([p["bin_noise"] for p in phase]))
     info = batch.info()
 
     extras = {}
@@ -345,15 +346,18 @@ def run_ours(args):
         e2e = {"value": frames_total / (e2e_total / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    # algorithmic bytes of one trace/bin/noise launch: per frame, the BVH node
-    # pairs (64 B) and triangles (48 B) its rays touch, plus the noised image and
-    # hit records it writes; summed over the B frames the launch renders
+    # algorithmic bytes of one ray-cast launch: per frame, the BVH node pairs
+    # (64 B) and triangles (48 B) its rays touch, plus the 16-byte hit record of
+    # every ray; summed over the B frames the launch renders
     alg = 0
+    visits = tests = exact = 0
     for p in poses:
         st = son.trace_stats(sid, p, prm)
-        alg += st["nodes_touched"] * 64 + st["tris_touched"] * 48 + base.n_range_bins * base.n_az_bins * 4 \
-            + p.n_rays * 16
-    achieved = alg / (phase1_ms / 1000.0) / 1e9
+        alg += st["nodes_touched"] * 64 + st["tris_touched"] * 48 + p.n_rays * 16
+        visits += st["visits"]
+        tests += st["tests"]
+        exact += st["exact_tests"]
+    achieved = alg / (trace_ms / 1000.0) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -363,9 +367,15 @@ def run_ours(args):
     tb = traffic_from_profile()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tb * B if tb is not None else None),
-                "kernel": "k_phase1 (trace + intensity + bin + noise)", "avg_launch_ms": phase1_ms,
-                "algorithmic_bytes_per_launch": int(alg),
+                "kernel": "k_trace (ray generation + LBVH walk + Moller-Trumbore + bin key)",
+                "avg_launch_ms": trace_ms, "algorithmic_bytes_per_launch": int(alg),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    # the binning kernel streams hit records in and I~ out: its own figure
+    bin_bytes = B * (base.n_rays * 16 + base.n_range_bins * base.n_az_bins * 4)
+    extras["bin_noise_GBps"] = bin_bytes / (bin_ms / 1000.0) / 1e9
+    extras["node_visits_per_ray"] = visits / (B * base.n_rays)
+    extras["tri_tests_per_ray"] = tests / (B * base.n_rays)
+    extras["fp64_tests_per_ray"] = exact / (B * base.n_rays)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -383,7 +393,7 @@ def run_ours(args):
                 "phase_ms": {k: float(np.mean([p[k] for p in phase])) for k in phase[0]},
                 "batch": info,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 6 * args.steps}
+                "gpu_launches": 7 * args.steps}
         line.update({k: float(v) for k, v in extras.items()})
         print(json.dumps(line), flush=True)
     batch.close()

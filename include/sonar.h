@@ -168,9 +168,10 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
                           uint64_t seed, uint64_t frame, const sonar_outputs* out,
                           void* stream);
 
-/* Maximum scratch, in 4-byte words, that sonar_render_noalloc can use: one
- * word for the image maximum plus, when out->noised is NULL, the noised
- * image (n_range_bins * n_az_bins words from word 64). */
+/* Maximum scratch, in 4-byte words, that sonar_render_noalloc can use: 64
+ * words, plus 4 words a ray for the hit records when out->hits is NULL, plus
+ * (rounded up to 64 words first) n_range_bins * n_az_bins words for the
+ * noised image when out->noised is NULL. */
 #define SONAR_NOALLOC_SCRATCH_WORDS (1u << 20)
 
 /* sonar_render for callers that must not allocate device memory: a render
@@ -182,8 +183,8 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
  * until the process exits.  The caller still provides every input and
  * output, as for sonar_render, and gets the same results.
  *   - A frame needing more scratch than the array holds is rejected with
- *     SONAR_ERR_ARG before anything is enqueued (with out->noised given, one
- *     word suffices).
+ *     SONAR_ERR_ARG before anything is enqueued (with out->hits and
+ *     out->noised given, 64 words suffice).
  *   - The first call on a device looks up the array's device address (which
  *     may load the library's device code) and caches it; make that first call
  *     before any stream capture on that device.
@@ -258,9 +259,10 @@ sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_item* items,
 sonar_status sonar_batch_update(sonar_batch_t batch, const sonar_batch_item* items,
                                 int32_t n_items, void* stream);
 
-/* Renders every item of the batch: one persistent launch traces, bins and
- * adds noise for all work units (dynamic work list); a second normalises
- * every range row and a third resamples every fan.  The first call for a given (params, theta, outputs)
+/* Renders every item of the batch: one launch casts every ray of every
+ * sensor, one persistent launch bins and adds noise for all column work units
+ * (dynamic work list), one normalises every range row and one resamples every
+ * fan.  The first call for a given (params, theta, outputs)
  * captures the launches in a CUDA graph; later calls with the same arguments
  * replay it.  Results per item equal sonar_render's for the same item and
  * tile shape (bitwise, in deterministic accumulation). */
@@ -284,18 +286,19 @@ sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
 
 /* Device durations, in milliseconds, of the phases of the most recent
  * sonar_render_batch and sonar_render_batch_backward replays, measured by CUDA
- * events captured inside their graphs: ms[0] the trace/bin/noise launch,
- * ms[1] the normalisation and fan launches, ms[2] the adjoint row-term
- * launch, ms[3] the adjoint gather and final-reduction launches.  Waits for those replays to finish; a phase not yet run
- * reports -1. */
-sonar_status sonar_batch_timings(sonar_batch_t batch, float ms[4]);
+ * events captured inside their graphs: ms[0] the ray-cast launch, ms[1] the
+ * binning/noise launch, ms[2] the normalisation and fan launches, ms[3] the
+ * adjoint row-term launch, ms[4] the adjoint gather and final-reduction
+ * launches.  Waits for those replays to finish; a phase not yet run reports
+ * -1. */
+sonar_status sonar_batch_timings(sonar_batch_t batch, float ms[5]);
 
 sonar_status sonar_batch_destroy(sonar_batch_t batch);
 
 /* ---- autotuner ---- */
 
-/* Times candidate tile shapes (columns per work unit, ray-to-lane mapping,
- * block size) on the batch's own sensors and records the fastest per sensor
+/* Times candidate tile shapes (beams x elevations per ray-cast warp, columns
+ * per binning work unit, binning block size) on the batch's own sensors and records the fastest per sensor
  * shape (n_beams, n_elev, n_range_bins, n_az_bins) in the context's tuning
  * cache; later sonar_batch_create and sonar_render calls use it.  Runs
  * renders on `stream` and synchronises it.  Outputs of `out` are
@@ -305,7 +308,8 @@ sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
                             const sonar_batch_outputs* out, void* stream);
 
 /* Tuning cache entries: writes up to `cap` rows of 8 int32
- * (n_beams, n_elev, n_range_bins, n_az_bins, cols, mapping, block, reserved)
+ * (n_beams, n_elev, n_range_bins, n_az_bins, cols, tb, block, reserved), tb =
+ * beams per ray-cast warp (a power of two <= 32; elevations = 32 / tb)
  * and returns the number of entries in *count. */
 sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count);
 

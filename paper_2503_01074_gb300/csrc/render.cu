@@ -1,12 +1,14 @@
 // Sonar rendering kernels (OceanSim, arXiv 2503.01074, Sec. III-A-2).
 //
-// phase 1 (k_phase1)  one work unit = whole azimuth columns of one sensor:
-//                     ray generation -> closest hit (LBVH walk, Moller-Trumbore)
-//                     -> intensity (Eq. 2, two-way) -> polar binning into a
-//                     shared-memory column block -> Eq. 3-6 noise per bin ->
-//                     I~ to HBM.  Because a unit owns its columns, every polar
-//                     bin is written exactly once: no global atomics, no memset
-//                     of the image.
+// k_trace             one ray per thread, warps on compact beam x elevation
+//                     patches: ray generation -> closest hit (LBVH walk,
+//                     Moller-Trumbore) -> range/azimuth bin -> 16-byte hit record.
+// k_bin               one work unit = whole azimuth columns of one sensor: the
+//                     units' hit records -> intensity (Eq. 2, two-way) -> polar
+//                     binning into a shared-memory column block -> Eq. 3-6 noise
+//                     per bin -> I~ to HBM.  A unit owns its columns, so every
+//                     polar bin is written exactly once: no global atomics, no
+//                     memset of the image.
 // k_norm_rows         range-wise normalisation: one warp per range row takes the
 //                     row maximum of I~ and writes N = I~ / max.
 // k_fan_tiles         fan resample of the normalised image, tiles of pixels.
@@ -134,10 +136,19 @@ __device__ bool mt64(const double o[3], const double d[3], float4 a, float4 b, f
 // closest hit: LBVH walk with a short stack
 // ---------------------------------------------------------------------------
 
-struct Exact {
-    double o[3], d[3];
-    bool ready;
-};
+// The FP64 decision for one triangle: builds the exact ray of (i, j) and runs
+// mt64.  Out of line so that the FP32 walk keeps no FP64 state in registers;
+// it runs only for tests FP32 cannot decide.
+__device__ __noinline__ bool exact_hit(const SensorDev& s, int i, int j, float4 a, float4 b, float4 c,
+                                       double* t) {
+    double d[3];
+    ray_dir64(s, i, j, d);
+    const double o[3] = {s.pos[0], s.pos[1], s.pos[2]};
+    double tt;
+    if (!mt64(o, d, a, b, c, tt)) return false;
+    *t = tt;
+    return true;
+}
 
 template <bool STATS>
 __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int rj, float3 o,
@@ -157,8 +168,6 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
     float best_t = tlimit;
     bool best_exact = false;
     double best_t64 = 0.0;
-    Exact ex;
-    ex.ready = false;
     uint64_t visits = 0, tests = 0, exact_n = 0;
 
     for (;;) {
@@ -224,13 +233,8 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
             bool exact = false;
             double t64 = 0.0;
             if (r == 2) {
-                if (!ex.ready) {
-                    ex.o[0] = s.pos[0]; ex.o[1] = s.pos[1]; ex.o[2] = s.pos[2];
-                    ray_dir64(s, ri, rj, ex.d);
-                    ex.ready = true;
-                }
                 if (STATS) ++exact_n;
-                if (!mt64(ex.o, ex.d, a, b, c, t64)) continue;
+                if (!exact_hit(s, ri, rj, a, b, c, &t64)) continue;
                 t = (float)t64;
                 exact = true;
             }
@@ -241,21 +245,16 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
                 take = true;
             } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
                 // near tie: decide on the exact distances, then on the caller's index
-                if (!ex.ready) {
-                    ex.o[0] = s.pos[0]; ex.o[1] = s.pos[1]; ex.o[2] = s.pos[2];
-                    ray_dir64(s, ri, rj, ex.d);
-                    ex.ready = true;
-                }
                 if (!exact) {
                     if (STATS) ++exact_n;
-                    if (!mt64(ex.o, ex.d, a, b, c, t64)) continue;
+                    if (!exact_hit(s, ri, rj, a, b, c, &t64)) continue;
                     exact = true;
                 }
                 if (!best_exact) {
                     const float4* bp = sc.tris + 3 * (int64_t)best;
                     double bt;
                     if (STATS) ++exact_n;
-                    best_t64 = mt64(ex.o, ex.d, __ldg(bp), __ldg(bp + 1), __ldg(bp + 2), bt) ? bt : CUDART_INF;
+                    best_t64 = exact_hit(s, ri, rj, __ldg(bp), __ldg(bp + 1), __ldg(bp + 2), &bt) ? bt : CUDART_INF;
                     best_exact = true;
                 }
                 take = t64 < best_t64 || (t64 == best_t64 && id < best_id);
@@ -324,15 +323,73 @@ __device__ __forceinline__ int range_bin(const SensorDev& s, float r) {
     return br < s.nr - 1 ? br : s.nr - 1;
 }
 
+// Azimuth bin of beam i: floor((2i + 1) naz / (2 nb)), in 32-bit integers when
+// the product fits (it does whenever nb * naz < 2^30).
 __device__ __forceinline__ int az_bin(const SensorDev& s, int i) {
+    if ((int64_t)s.nb * s.naz < (1ll << 30)) return (int)(((2u * i + 1u) * (uint32_t)s.naz) / (2u * (uint32_t)s.nb));
     return (int)(((2ll * i + 1) * s.naz) / (2ll * s.nb));
 }
 
+// Exact uint -> float for v < 2^23 without a conversion instruction.
+__device__ __forceinline__ float small_u2f(uint32_t v) {
+    return __uint_as_float(0x4B000000u | v) - 8388608.0f;
+}
+
 // ---------------------------------------------------------------------------
-// phase 1: trace + bin + noise, one work unit per block iteration
+// trace: one ray per thread, hit record out
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void load_unit(const Phase1Args& a, int u, SensorDev* S, SceneDev* SC, Unit* U) {
+// Each block covers a tile of 4 * tb beams x (32 / tb) elevations of one
+// sensor; lane l of warp w traces beam i0 + w * tb + l % tb, elevation
+// j0 + l / tb, so that a warp's rays sample a compact patch of the field of
+// view.  Records go to their canonical index i * n_elev + j.
+__global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
+    __shared__ SensorDev S;
+    __shared__ SceneDev SC;
+    __shared__ int s_tile;
+    if (threadIdx.x == 0) {
+        int si = 0, tile = blockIdx.x;
+        if (a.sensors) {
+            int lo = 0, hi = a.n_sensors - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.tile_prefix[mid] <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
+            }
+            si = lo;
+            tile = blockIdx.x - a.tile_prefix[si];
+            S = a.sensors[si];
+            SC = a.scenes[S.scene];
+        } else {
+            S = a.one;
+            SC = a.one_scene;
+        }
+        s_tile = tile;
+    }
+    __syncthreads();
+    const int tb = S.tb, te = 32 / S.tb;
+    const int bb = 4 * tb;
+    const int tiles_b = (S.nb + bb - 1) / bb;
+    const int tile = s_tile;
+    const int ty = tile / tiles_b, tx = tile - ty * tiles_b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = tx * bb + warp * tb + (lane % tb);
+    const int j = ty * te + lane / tb;
+    if (i >= S.nb || j >= S.ne) return;
+    const Cast c = cast_ray<false>(S, SC, i, j, a.params, a.err, nullptr);
+    uint32_t key = kNoKey;
+    if (c.orig != 0xFFFFFFFFu) {
+        const int br = range_bin(S, c.t);
+        if (br >= 0) key = (uint32_t)(br * S.naz + az_bin(S, i));
+    }
+    *reinterpret_cast<uint4*>(a.hits + S.hits_off + (int64_t)i * S.ne + j) =
+        make_uint4(key, c.orig, __float_as_uint(c.t), __float_as_uint(c.cosf));
+}
+
+// ---------------------------------------------------------------------------
+// bin + noise: one work unit = whole azimuth columns of one sensor
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void load_unit(const BinArgs& a, int u, SensorDev* S, SceneDev* SC, Unit* U) {
     if (a.units) {
         *U = a.units[u];
         *S = a.sensors[U->sensor];
@@ -347,8 +404,13 @@ __device__ __forceinline__ void load_unit(const Phase1Args& a, int u, SensorDev*
     }
 }
 
+// The unit's rays are the contiguous hit records of its beams.  Their scores
+// s = mu[m] cos exp(-2 alpha r) gain are summed into a shared-memory column
+// block (DET: in canonical ray order, warps taking turns and each group of
+// equal bins folded by its leader in lane order; otherwise warp-aggregated
+// shared-memory atomics); then Eq. 3-6 noise per bin and I~ to HBM.
 template <int DET>
-__global__ void __launch_bounds__(512) k_phase1(Phase1Args a) {
+__global__ void __launch_bounds__(512) k_bin(BinArgs a) {
     extern __shared__ float acc[];
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
@@ -373,42 +435,29 @@ __global__ void __launch_bounds__(512) k_phase1(Phase1Args a) {
         __syncthreads();
         const int cw = U.c1 - U.c0;
         const int i0 = first_beam_of_col(U.c0, S.nb, S.naz), i1 = first_beam_of_col(U.c1, S.nb, S.naz);
-        const int nbeam = i1 - i0;
-        const int R = nbeam * S.ne;
+        const int64_t r0 = (int64_t)i0 * S.ne, r1 = (int64_t)i1 * S.ne;
         const int nbin = S.nr * cw;
         for (int k = tid; k < nbin; k += nt) acc[k] = 0.0f;
         __syncthreads();
-        for (int base = 0; base < R; base += nt) {
-            const int r = base + tid;
+        const sonar_hit* H = a.hits + S.hits_off;
+        for (int64_t base = r0; base < r1; base += nt) {
+            const int64_t r = base + tid;
             uint32_t lkey = kNoKey;
             float score = 0.0f;
-            if (r < R) {
-                int bi, ej;
-                if (S.mapping == 0) { bi = r / S.ne; ej = r - bi * S.ne; }
-                else { ej = r / nbeam; bi = r - ej * nbeam; }
-                const int i = i0 + bi, j = ej;
-                const Cast c = cast_ray<false>(S, SC, i, j, a.params, a.err, nullptr);
-                uint32_t gkey = kNoKey;
-                if (c.orig != 0xFFFFFFFFu) {
-                    const int br = range_bin(S, c.t);
-                    if (br >= 0) {
-                        const int ba = az_bin(S, i);
-                        gkey = (uint32_t)(br * S.naz + ba);
-                        lkey = (uint32_t)(br * cw + (ba - U.c0));
-                        const int m = c.mat < a.n_mat ? c.mat : a.n_mat - 1;
-                        score = __ldg(a.theta + 2 + m) * c.cosf * expf(-2.0f * alpha * c.t) * gain;
-                    }
-                }
-                if (a.hits) {
-                    uint4 rec = make_uint4(gkey, c.orig, __float_as_uint(c.t), __float_as_uint(c.cosf));
-                    *reinterpret_cast<uint4*>(a.hits + S.hits_off + (int64_t)i * S.ne + j) = rec;
+            if (r < r1) {
+                const uint4 h = __ldg(reinterpret_cast<const uint4*>(H + r));
+                if (h.x != kNoKey) {
+                    const uint32_t br = h.x / (uint32_t)S.naz, ba = h.x - br * (uint32_t)S.naz;
+                    lkey = br * (uint32_t)cw + (ba - (uint32_t)U.c0);
+                    int m = SC.mat_orig[h.y];
+                    m = m < a.n_mat ? m : a.n_mat - 1;
+                    score = __ldg(a.theta + 2 + m) * __uint_as_float(h.w) *
+                            expf(-2.0f * alpha * __uint_as_float(h.z)) * gain;
                 }
             }
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, lkey);
             const int leader = __ffs(peers) - 1;
             if (DET) {
-                // sequential fold in ray order: warps take turns, lanes of a
-                // group are added by their leader in lane order
                 for (int w = 0; w < nw; ++w) {
                     if (warp == w && lkey != kNoKey) {
                         float v = lane == leader ? acc[lkey] : 0.0f;
@@ -429,23 +478,28 @@ __global__ void __launch_bounds__(512) k_phase1(Phase1Args a) {
             }
         }
         __syncthreads();
-        // Eq. 3-6 per bin, I~ to HBM, kept in shared memory for the maxima
+        // Eq. 3-6 per bin; (row, col) advance incrementally: no division and no
+        // integer-to-float conversion instruction in this loop
         const float dr = (S.rmax - S.rmin) / (float)S.nr, da = S.hfov / (float)S.naz;
         const float inv_rmax2 = 1.0f / (S.rmax * S.rmax);
         const float inv_sphi = 1.0f / a.params.sigma_phi;
+        const int drow = nt / cw, dcol = nt - drow * cw;
+        int row = tid / cw, col = tid - row * cw;
         for (int k = tid; k < nbin; k += nt) {
-            const int row = k / cw, col = U.c0 + (k - row * cw);
-            const uint32_t b = (uint32_t)(row * S.naz + col);
+            const uint32_t b = (uint32_t)(row * S.naz + U.c0 + col);
             const float P = acc[k];
             float w_sa, w_sm;
             bin_noise(b, S, a.params.sigma_sa, a.params.sigma_sm, w_sa, w_sm);
-            const float rc = fmaf((float)row + 0.5f, dr, S.rmin);
-            const float pc = fmaf((float)col + 0.5f, da, -0.5f * S.hfov);
+            const float rc = fmaf(small_u2f(row) + 0.5f, dr, S.rmin);
+            const float pc = fmaf(small_u2f(U.c0 + col) + 0.5f, da, -0.5f * S.hfov);
             const float additive = rc * rc * inv_rmax2 * (1.0f + 0.5f * expf(-pc * pc * inv_sphi) * w_sa);
             const float In = P * (0.5f + w_sm) + additive;
             a.noised[S.polar_off + b] = In;
             if (a.binned) a.binned[S.polar_off + b] = P;
             acc[k] = In;
+            row += drow;
+            col += dcol;
+            if (col >= cw) { col -= cw; ++row; }
         }
         __syncthreads();
         if (a.params.normalise == 2) {
@@ -808,21 +862,26 @@ __global__ void k_popcount(const uint32_t* bits, int64_t words, unsigned long lo
 // ---------------------------------------------------------------------------
 
 void set_kernel_attributes() {
-    cudaFuncSetAttribute(k_phase1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_phase1<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_bin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
-cudaError_t launch_phase1(const Phase1Args& a, int det, int grid, int block, size_t smem, cudaStream_t st) {
-    if (det) k_phase1<1><<<grid, block, smem, st>>>(a);
-    else k_phase1<0><<<grid, block, smem, st>>>(a);
+cudaError_t launch_trace(const TraceArgs& a, int blocks, cudaStream_t st) {
+    if (blocks > 0) k_trace<<<blocks, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-int phase1_blocks_per_sm(int det, int block, size_t smem) {
+cudaError_t launch_bin(const BinArgs& a, int det, int grid, int block, size_t smem, cudaStream_t st) {
+    if (det) k_bin<1><<<grid, block, smem, st>>>(a);
+    else k_bin<0><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int bin_blocks_per_sm(int det, int block, size_t smem) {
     int n = 0;
-    const void* f = det ? (const void*)k_phase1<1> : (const void*)k_phase1<0>;
+    const void* f = det ? (const void*)k_bin<1> : (const void*)k_bin<0>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

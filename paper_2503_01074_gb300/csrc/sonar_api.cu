@@ -21,9 +21,9 @@ using namespace sonar;
 namespace {
 
 struct Tune {
-    int cols = 0;     // azimuth columns per work unit (0: derive)
-    int mapping = 0;  // 0: lanes along elevation, 1: lanes along beams
-    int block = 128;
+    int cols = 0;     // binning: azimuth columns per work unit (0: derive)
+    int tb = 0;       // tracing: beams per warp tile, elevations = 32 / tb (0: derive)
+    int block = 128;  // binning: threads per block
 };
 
 using ShapeKey = std::array<int, 4>;   // n_beams, n_elev, n_range_bins, n_az_bins
@@ -43,7 +43,7 @@ struct sonar_ctx {
     std::vector<bool> alive;
     std::string last_error;
     uint32_t* d_err = nullptr;
-    Scratch rowmax, noised, rowinfo, partials, counters;
+    Scratch rowmax, noised, rowinfo, partials, counters, hits;
     std::map<ShapeKey, Tune> tune;
 };
 
@@ -139,6 +139,8 @@ Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
     const int max_cols_smem = std::max(1, (int)(kMaxDynSmem / 4 / 2) / s.n_range_bins);
     t.cols = std::max(1, std::min({t.cols, s.n_az_bins, max_cols_smem}));
     if (t.block < 32 || t.block > 512 || (t.block & 31)) t.block = 128;
+    if (t.tb <= 0) t.tb = 8;
+    if (t.tb > 32 || (t.tb & (t.tb - 1))) t.tb = 8;
     return t;
 }
 
@@ -168,8 +170,10 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     d.frame_lo = (uint32_t)frame;
     d.frame_hi = (uint32_t)(frame >> 32);
     d.cols = t.cols;
-    d.mapping = t.mapping;
     d.n_tiles = (s.n_az_bins + t.cols - 1) / t.cols;
+    d.tb = t.tb;
+    const int64_t bb = 4 * t.tb, be = 32 / t.tb;
+    d.trace_blocks = (int32_t)(((s.n_beams + bb - 1) / bb) * ((s.n_elev + be - 1) / be));
     return d;
 }
 
@@ -208,7 +212,7 @@ extern "C" sonar_status sonar_destroy(sonar_ctx_t ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto& s : ctx->scenes) free_scene(&s);
-    for (Scratch* s : {&ctx->rowmax, &ctx->noised, &ctx->rowinfo, &ctx->partials, &ctx->counters})
+    for (Scratch* s : {&ctx->rowmax, &ctx->noised, &ctx->rowinfo, &ctx->partials, &ctx->counters, &ctx->hits})
         if (s->p) cudaFreeAsync(s->p, 0);
     cudaDeviceSynchronize();
     cudaFree(ctx->d_err);
@@ -291,7 +295,35 @@ extern "C" sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t id, int64_t ou
 
 namespace {
 
-size_t phase1_smem(const SensorDev& s) { return (size_t)s.nr * s.cols * sizeof(float); }
+size_t bin_smem(const SensorDev& s) { return (size_t)s.nr * s.cols * sizeof(float); }
+
+// Trace, bin and noise of one sensor (polar_off = hits_off = rowmax_off = 0).
+sonar_status single_forward(sonar_ctx* ctx, const SensorDev& S, const SceneDev& sc, const sonar_params* p,
+                            const float* d_theta, int32_t n_mat, sonar_hit* hits, float* noised, float* binned,
+                            uint32_t* gmax, int block, cudaStream_t s) {
+    if (p->normalise == 2) CU(cudaMemsetAsync(gmax, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
+    TraceArgs t{};
+    t.one = S;
+    t.one_scene = sc;
+    t.params = *p;
+    t.hits = hits;
+    t.err = ctx->d_err;
+    CU(launch_trace(t, S.trace_blocks, s), "trace launch");
+    BinArgs a{};
+    a.n_units = S.n_tiles;
+    a.n_mat = n_mat;
+    a.one = S;
+    a.one_scene = sc;
+    a.theta = d_theta;
+    a.params = *p;
+    a.hits = hits;
+    a.noised = noised;
+    a.binned = binned;
+    a.rowmax = gmax;
+    a.err = ctx->d_err;
+    CU(launch_bin(a, p->accumulate == 0, S.n_tiles, block, bin_smem(S), s), "binning launch");
+    return SONAR_OK;
+}
 
 // Normalisation and fan of one sensor (polar_off = fan_off = rowmax_off = 0).
 sonar_status single_post(sonar_ctx* ctx, const SensorDev& S, int normalise, const float* noised,
@@ -349,21 +381,14 @@ extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const so
         noised = (float*)ctx->noised.p;
     }
     CU(grow(ctx->rowmax, sizeof(uint32_t), s), "scratch allocation");
-    if (params->normalise == 2) CU(cudaMemsetAsync(ctx->rowmax.p, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
-
-    Phase1Args a{};
-    a.n_units = S.n_tiles;
-    a.n_mat = n_mat;
-    a.one = S;
-    a.one_scene = scene_dev(ctx->scenes[scene_id]);
-    a.theta = d_theta;
-    a.params = *params;
-    a.noised = noised;
-    a.binned = out->binned;
-    a.hits = out->hits;
-    a.rowmax = (uint32_t*)ctx->rowmax.p;
-    a.err = ctx->d_err;
-    CU(launch_phase1(a, params->accumulate == 0, S.n_tiles, t.block, phase1_smem(S), s), "phase-1 launch");
+    sonar_hit* hits = out->hits;
+    if (!hits) {
+        CU(grow(ctx->hits, sizeof(sonar_hit) * (size_t)S.nb * S.ne, s), "scratch allocation");
+        hits = (sonar_hit*)ctx->hits.p;
+    }
+    sonar_status st2 = single_forward(ctx, S, scene_dev(ctx->scenes[scene_id]), params, d_theta, n_mat, hits, noised,
+                                      out->binned, (uint32_t*)ctx->rowmax.p, t.block, s);
+    if (st2 != SONAR_OK) return st2;
     (void)npol;
     return single_post(ctx, S, params->normalise, noised, (const uint32_t*)ctx->rowmax.p, out->polar, out->fan, s);
 }
@@ -445,6 +470,8 @@ struct sonar_batch {
     std::vector<Unit> units;          // forward work list (column tiles)
     std::vector<AdjUnit> adj_units;   // adjoint work list (ray chunks)
     std::vector<int32_t> fan_prefix;  // fan blocks per sensor, prefix
+    std::vector<int32_t> trace_prefix;  // trace blocks per sensor, prefix
+    int64_t total_rays = 0;
     int64_t total_rows = 0, total_polar = 0;
     int block = 128;
     int adj_chunk = 0;
@@ -454,6 +481,8 @@ struct sonar_batch {
     AdjUnit* d_adj_units = nullptr;
     SceneDev* d_scenes = nullptr;
     int32_t* d_fan_prefix = nullptr;
+    int32_t* d_trace_prefix = nullptr;
+    sonar_hit* d_hits = nullptr;      // hit records when the caller asks for none
     uint32_t* d_rowmax = nullptr;
     float* d_noised = nullptr;
     RowInfo* d_rowinfo = nullptr;
@@ -469,7 +498,7 @@ struct sonar_batch {
     // graphs
     cudaStream_t cap = nullptr;
     cudaGraphExec_t fwd = nullptr, bwd = nullptr;
-    cudaEvent_t ev[6] = {};           // phase boundaries recorded inside the graphs
+    cudaEvent_t ev[7] = {};           // phase boundaries recorded inside the graphs
     bool ran_fwd = false, ran_bwd = false;
     std::vector<unsigned char> fwd_key, bwd_key;
     int graphs = 0;
@@ -479,9 +508,11 @@ namespace {
 
 void batch_free_device(sonar_batch* b) {
     for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_adj_units, (void*)b->d_scenes,
-                    (void*)b->d_fan_prefix, (void*)b->d_rowmax, (void*)b->d_noised, (void*)b->d_rowinfo,
-                    (void*)b->d_partials, (void*)b->d_counters})
+                    (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_hits, (void*)b->d_rowmax,
+                    (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters})
         if (p) cudaFree(p);
+    b->d_trace_prefix = nullptr;
+    b->d_hits = nullptr;
     b->n_mat_cap = 0;
     b->d_sens = nullptr; b->d_units = nullptr; b->d_adj_units = nullptr; b->d_scenes = nullptr;
     b->d_fan_prefix = nullptr;
@@ -525,6 +556,7 @@ sonar_status batch_plan(sonar_batch* b) {
     b->units.clear();
     b->adj_units.clear();
     b->fan_prefix.assign(n + 1, 0);
+    b->trace_prefix.assign(n + 1, 0);
     b->smem1 = 0;
     int64_t rows = 0, polar_end = 0;
     std::map<int, int64_t> block_votes;
@@ -542,6 +574,7 @@ sonar_status batch_plan(sonar_batch* b) {
         b->hs[k] = S;
         b->fan_prefix[k + 1] =
             b->fan_prefix[k] + (int32_t)(((int64_t)S.fan_w * S.fan_h + kFanTile - 1) / kFanTile);
+        b->trace_prefix[k + 1] = b->trace_prefix[k] + S.trace_blocks;
         block_votes[t.block] += (int64_t)S.nb * S.ne;
         for (int tile = 0; tile < S.n_tiles; ++tile) {
             Unit u;
@@ -567,6 +600,7 @@ sonar_status batch_plan(sonar_batch* b) {
     b->total_polar = polar_end;
     int64_t all_rays = 0;
     for (const SensorDev& S : b->hs) all_rays += (int64_t)S.nb * S.ne;
+    b->total_rays = all_rays;
     b->adj_chunk = adj_chunk(all_rays, ctx->sm_count, b->block);
     for (int k = 0; k < n; ++k) {
         const int64_t r = (int64_t)b->hs[k].nb * b->hs[k].ne;
@@ -584,6 +618,7 @@ sonar_status batch_plan(sonar_batch* b) {
     b->n_scene_table = ctx->scenes.size();
     alloc((void**)&b->d_adj_units, sizeof(AdjUnit) * na);
     alloc((void**)&b->d_fan_prefix, sizeof(int32_t) * (n + 1));
+    alloc((void**)&b->d_trace_prefix, sizeof(int32_t) * (n + 1));
     alloc((void**)&b->d_rowmax, sizeof(uint32_t) * rows);
     alloc((void**)&b->d_rowinfo, sizeof(RowInfo) * rows);
     alloc((void**)&b->d_counters, sizeof(int32_t) * 4);
@@ -597,12 +632,14 @@ sonar_status batch_plan(sonar_batch* b) {
         e = cudaMemcpy(b->d_adj_units, b->adj_units.data(), sizeof(AdjUnit) * na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_fan_prefix, b->fan_prefix.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_trace_prefix, b->trace_prefix.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
     return SONAR_OK;
 }
 
 int persistent_grid(const sonar_batch* b, int det) {
-    const int per_sm = phase1_blocks_per_sm(det, b->block, b->smem1);
+    const int per_sm = bin_blocks_per_sm(det, b->block, b->smem1);
     const int64_t g = std::min<int64_t>((int64_t)b->units.size(), (int64_t)b->ctx->sm_count * per_sm);
     return (int)std::max<int64_t>(1, g);
 }
@@ -620,8 +657,21 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
     if (p->normalise == 2)
         CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
+    if (!out->hits && !b->d_hits)
+        CU(cudaMalloc(&b->d_hits, sizeof(sonar_hit) * std::max<int64_t>(1, b->total_rays)), "batch scratch");
+    sonar_hit* hits = out->hits ? out->hits : b->d_hits;
     if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
-    Phase1Args a{};
+    TraceArgs t{};
+    t.sensors = b->d_sens;
+    t.scenes = b->d_scenes;
+    t.tile_prefix = b->d_trace_prefix;
+    t.n_sensors = (int32_t)b->items.size();
+    t.params = *p;
+    t.hits = hits;
+    t.err = ctx->d_err;
+    CU(launch_trace(t, b->trace_prefix.back(), s), "batch trace launch");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[6], s, cudaEventRecordExternal), "cudaEventRecord");
+    BinArgs a{};
     a.sensors = b->d_sens;
     a.units = b->d_units;
     a.scenes = b->d_scenes;
@@ -632,10 +682,10 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     a.params = *p;
     a.noised = out->noised ? out->noised : b->d_noised;
     a.binned = out->binned;
-    a.hits = out->hits;
+    a.hits = hits;
     a.rowmax = b->d_rowmax;
     a.err = ctx->d_err;
-    CU(launch_phase1(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch phase-1 launch");
+    CU(launch_bin(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch binning launch");
     if (events) CU(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal), "cudaEventRecord");
     NormArgs c{};
     c.sensors = b->d_sens;
@@ -680,7 +730,7 @@ extern "C" sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_it
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming);
     }
     if (st == SONAR_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    for (int k = 0; k < 6 && st == SONAR_OK && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
+    for (int k = 0; k < 7 && st == SONAR_OK && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     if (st == SONAR_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "batch staging");
     if (st != SONAR_OK) {
         sonar_batch_destroy(b);
@@ -728,7 +778,7 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
     for (int k = 0; k < n; ++k) {
         SensorDev S = b->hs[k];
         const sonar_batch_item& it = items[k];
-        const SensorDev fresh = make_sensor(it.sensor, it.seed, it.frame, Tune{S.cols, S.mapping, b->block},
+        const SensorDev fresh = make_sensor(it.sensor, it.seed, it.frame, Tune{S.cols, S.tb, b->block},
                                             it.fan_w, it.fan_h);
         memcpy(S.pos, fresh.pos, sizeof S.pos);
         memcpy(S.rot, fresh.rot, sizeof S.rot);
@@ -886,20 +936,21 @@ extern "C" sonar_status sonar_batch_info(sonar_batch_t b, int64_t out[5]) {
     return SONAR_OK;
 }
 
-extern "C" sonar_status sonar_batch_timings(sonar_batch_t b, float ms[4]) {
+extern "C" sonar_status sonar_batch_timings(sonar_batch_t b, float ms[5]) {
     if (!b || !ms) return SONAR_ERR_ARG;
     sonar_ctx* ctx = b->ctx;
-    for (int k = 0; k < 4; ++k) ms[k] = -1.0f;
+    for (int k = 0; k < 5; ++k) ms[k] = -1.0f;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
     if (b->ran_fwd) {
         CU(cudaEventSynchronize(b->ev[2]), "cudaEventSynchronize");
-        CU(cudaEventElapsedTime(&ms[0], b->ev[0], b->ev[1]), "cudaEventElapsedTime");
-        CU(cudaEventElapsedTime(&ms[1], b->ev[1], b->ev[2]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[0], b->ev[0], b->ev[6]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[1], b->ev[6], b->ev[1]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[2], b->ev[1], b->ev[2]), "cudaEventElapsedTime");
     }
     if (b->ran_bwd) {
         CU(cudaEventSynchronize(b->ev[5]), "cudaEventSynchronize");
-        CU(cudaEventElapsedTime(&ms[2], b->ev[3], b->ev[4]), "cudaEventElapsedTime");
-        CU(cudaEventElapsedTime(&ms[3], b->ev[4], b->ev[5]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[3], b->ev[3], b->ev[4]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&ms[4], b->ev[4], b->ev[5]), "cudaEventElapsedTime");
     }
     return SONAR_OK;
 }
@@ -966,7 +1017,7 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
         if (std::find(shapes.begin(), shapes.end(), k) == shapes.end()) shapes.push_back(k);
     }
     const std::vector<sonar_batch_item> all = b->items;
-    // 1. per shape: columns per unit and lane mapping, timed on that shape's items alone
+    // per shape, timed on that shape's items alone
     for (const ShapeKey& k : shapes) {
         std::vector<sonar_batch_item> sub;
         for (const sonar_batch_item& it : all)
@@ -974,18 +1025,27 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
                 sub.push_back(it);
         b->items = sub;
         Tune best;
+        best.block = 128;
         float best_ms = 1e30f;
+        // the trace warp tile (beams x elevations per warp) with default binning shapes
+        for (int tb : {1, 2, 4, 8, 16, 32}) {
+            ctx->tune[k] = Tune{0, tb, 128};
+            if ((st = batch_plan(b)) != SONAR_OK) goto restore;
+            const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
+            if (cudaGetLastError() != cudaSuccess) continue;
+            if (ms < best_ms) { best_ms = ms; best.tb = tb; }
+        }
+        // then columns per binning unit and the binning block size
+        best_ms = 1e30f;
+        const int tb = best.tb;
         for (int block : {64, 128, 256}) {
             for (int cols : {1, 2, 4, 8, 16, 32}) {
                 if (cols > k[3] || (size_t)cols * k[2] * 4 > kMaxDynSmem / 2) continue;
-                for (int mapping : {0, 1}) {
-                    if (p->accumulate == 0 && mapping == 1) continue;   // keep the canonical fold order
-                    ctx->tune[k] = Tune{cols, mapping, block};
-                    if ((st = batch_plan(b)) != SONAR_OK) goto restore;
-                    const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
-                    if (cudaGetLastError() != cudaSuccess) continue;
-                    if (ms < best_ms) { best_ms = ms; best = Tune{cols, mapping, block}; }
-                }
+                ctx->tune[k] = Tune{cols, tb, block};
+                if ((st = batch_plan(b)) != SONAR_OK) goto restore;
+                const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
+                if (cudaGetLastError() != cudaSuccess) continue;
+                if (ms < best_ms) { best_ms = ms; best = Tune{cols, tb, block}; }
             }
         }
         ctx->tune[k] = best;
@@ -1007,7 +1067,7 @@ extern "C" sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t c
         if (rows && k < cap) {
             int32_t* r = rows + 8 * k;
             r[0] = kv.first[0]; r[1] = kv.first[1]; r[2] = kv.first[2]; r[3] = kv.first[3];
-            r[4] = kv.second.cols; r[5] = kv.second.mapping; r[6] = kv.second.block; r[7] = 0;
+            r[4] = kv.second.cols; r[5] = kv.second.tb; r[6] = kv.second.block; r[7] = 0;
         }
         ++k;
     }
@@ -1019,8 +1079,8 @@ extern "C" sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int
     if (!ctx || (!rows && count > 0) || count < 0) return fail(ctx, SONAR_ERR_ARG, "bad tune rows");
     for (int k = 0; k < count; ++k) {
         const int32_t* r = rows + 8 * k;
-        if (r[0] < 1 || r[1] < 1 || r[2] < 1 || r[3] < 1 || r[4] < 1 || r[5] < 0 || r[5] > 1 || r[6] < 32 ||
-            r[6] > 512 || (r[6] & 31))
+        if (r[0] < 1 || r[1] < 1 || r[2] < 1 || r[3] < 1 || r[4] < 1 || r[5] < 1 || r[5] > 32 ||
+            (r[5] & (r[5] - 1)) || r[6] < 32 || r[6] > 512 || (r[6] & 31))
             return fail(ctx, SONAR_ERR_ARG, "bad tune row " + std::to_string(k));
         ctx->tune[ShapeKey{r[0], r[1], r[2], r[3]}] = Tune{r[4], r[5], r[6]};
     }
@@ -1116,40 +1176,31 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     if (!out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "outputs or outputs->polar is NULL");
     if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
     if (out->fan && (out->fan_w < 1 || out->fan_h < 1)) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
-    // scratch layout: the image maximum (normalise = 2) at word 0, the noised
-    // image (if the caller passes none) from the next 256-byte boundary
-    const int64_t noised_at = 64;
+    // scratch layout (words): the image maximum at 0; from 64 the hit records
+    // (4 words a ray) unless the caller passes them; then, at a 256-byte
+    // boundary, the noised image unless the caller passes it
     const int64_t npol = (int64_t)sensor->n_range_bins * sensor->n_az_bins;
-    const int64_t need = out->noised ? 1 : noised_at + npol;
+    const int64_t hit_words = out->hits ? 0 : 4 * (int64_t)sensor->n_beams * sensor->n_elev;
+    const int64_t noised_at = 64 + (hit_words + 63) / 64 * 64;
+    const int64_t need = out->noised ? noised_at : noised_at + npol;
     if (need > (int64_t)SONAR_NOALLOC_SCRATCH_WORDS)
         return fail(ctx, SONAR_ERR_ARG, "sonar_render_noalloc: frame needs " + std::to_string(need) +
                                             " scratch words, the fixed scratch holds " +
                                             std::to_string(SONAR_NOALLOC_SCRATCH_WORDS) +
-                                            (out->noised ? "" : " (pass outputs->noised to need fewer)"));
+                                            " (pass outputs->hits and outputs->noised to need fewer)");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
     void* base = nullptr;
     CU(noalloc_scratch(ctx->device, &base), "cudaGetSymbolAddress of the fixed scratch");
     uint32_t* rowmax = (uint32_t*)base;
+    sonar_hit* hits = out->hits ? out->hits : (sonar_hit*)((float*)base + 64);
     float* noised = out->noised ? out->noised : (float*)base + noised_at;
     const Tune t = tune_for(ctx, *sensor);
     const SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
-    // the maximum must start at zero (the smallest encoded value); the array
-    // still holds the previous call's values
-    if (params->normalise == 2) CU(cudaMemsetAsync(rowmax, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
-    Phase1Args a{};
-    a.n_units = S.n_tiles;
-    a.n_mat = n_mat;
-    a.one = S;
-    a.one_scene = scene_dev(ctx->scenes[scene_id]);
-    a.theta = d_theta;
-    a.params = *params;
-    a.noised = noised;
-    a.binned = out->binned;
-    a.hits = out->hits;
-    a.rowmax = rowmax;
-    a.err = ctx->d_err;
-    CU(launch_phase1(a, params->accumulate == 0, S.n_tiles, t.block, (size_t)S.nr * S.cols * sizeof(float), s),
-       "phase-1 launch");
+    // single_forward clears the maximum (the array still holds the previous
+    // call's values); hit records and the noised image are fully overwritten
+    st = single_forward(ctx, S, scene_dev(ctx->scenes[scene_id]), params, d_theta, n_mat, hits, noised, out->binned,
+                        rowmax, t.block, s);
+    if (st != SONAR_OK) return st;
     return single_post(ctx, S, params->normalise, noised, rowmax, out->polar, out->fan, s);
 }

@@ -32,8 +32,9 @@ inline SceneDev scene_dev(const SceneStore& s) {
 
 // Kernel launchers (render.cu).
 void set_kernel_attributes();
-cudaError_t launch_phase1(const Phase1Args& a, int det, int grid, int block, size_t smem, cudaStream_t st);
-int phase1_blocks_per_sm(int det, int block, size_t smem);
+cudaError_t launch_trace(const TraceArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_bin(const BinArgs& a, int det, int grid, int block, size_t smem, cudaStream_t st);
+int bin_blocks_per_sm(int det, int block, size_t smem);
 constexpr size_t kMaxDynSmem = 200 * 1024;
 cudaError_t launch_norm(const NormArgs& a, cudaStream_t st);
 cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st);

@@ -49,9 +49,10 @@ struct SensorDev {
     int32_t fan_w, fan_h;
     uint32_t seed_lo, seed_hi, frame_lo, frame_hi;
     int32_t scene;       // index into the scene table
-    int32_t cols;        // azimuth columns per work unit
-    int32_t mapping;     // 0: lanes run along elevation, 1: lanes run along beams
-    int32_t n_tiles;     // work units of this sensor = ceil(naz / cols)
+    int32_t cols;        // binning: azimuth columns per work unit
+    int32_t n_tiles;     // binning work units of this sensor = ceil(naz / cols)
+    int32_t tb;          // trace: beams per warp tile (elevations = 32 / tb)
+    int32_t trace_blocks;  // trace: blocks of 4 warp tiles covering the sensor
     int64_t polar_off, hits_off, fan_off, rowmax_off;
 };
 
@@ -137,7 +138,21 @@ struct TraceCounters {
     uint32_t* tri_bits;             // touched triangles (bitmap)
 };
 
-struct Phase1Args {
+// Ray casting: blocks of 128 rays.
+struct TraceArgs {
+    const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
+    const SceneDev* scenes;     // batch: device table; single: nullptr (use `one_scene`)
+    const int32_t* tile_prefix; // batch: [n_sensors + 1] trace-block prefix
+    int32_t n_sensors;
+    SensorDev one;
+    SceneDev one_scene;
+    sonar_params params;
+    sonar_hit* hits;            // always written (the caller's buffer or scratch)
+    uint32_t* err;
+};
+
+// Binning and noise over column-tile work units.
+struct BinArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
     const Unit* units;          // batch: device work list; single: nullptr
     const SceneDev* scenes;     // batch: device table; single: nullptr (use `one_scene`)
@@ -148,10 +163,10 @@ struct Phase1Args {
     SceneDev one_scene;
     const float* theta;         // (alpha, gain, mu[...])
     sonar_params params;
+    const sonar_hit* hits;      // the trace kernel's records
     float* noised;
     float* binned;
-    sonar_hit* hits;
-    uint32_t* rowmax;           // ordered-encoded maxima per range row (or per image)
+    uint32_t* rowmax;           // normalise = 2: ordered-encoded image maximum per sensor
     uint32_t* err;
 };
 

@@ -401,9 +401,9 @@ class Batch:
 
     def timings(self):
         """Phase durations (ms) of the last forward/backward graph replays."""
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 5)()
         self.sonar._check(self.lib.sonar_batch_timings(self.h, ms))
-        return dict(zip(("trace_bin_noise", "normalise_fan", "adjoint_rows", "adjoint_gather"), list(ms)))
+        return dict(zip(("trace", "bin_noise", "normalise_fan", "adjoint_rows", "adjoint_gather"), list(ms)))
 
     def view(self, k):
         """Per-item views (polar [nr, naz], noised, hits [rays, 4], fan [h, w]) of the packed outputs."""
