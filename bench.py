@@ -391,7 +391,7 @@ def run_ours(args):
                 "Mrays_s": value * rays_per_frame / 1e6,
                 "scene_build_ms": build_ms,
                 "phase_ms": {k: float(np.mean([p[k] for p in phase])) for k in phase[0]},
-                "batch": info,
+                "batch": info, "tune": son.tune_get().tolist(),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 7 * args.steps}
         line.update({k: float(v) for k, v in extras.items()})

@@ -308,8 +308,9 @@ sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
                             const sonar_batch_outputs* out, void* stream);
 
 /* Tuning cache entries: writes up to `cap` rows of 8 int32
- * (n_beams, n_elev, n_range_bins, n_az_bins, cols, tb, block, reserved), tb =
- * beams per ray-cast warp (a power of two <= 32; elevations = 32 / tb)
+ * (n_beams, n_elev, n_range_bins, n_az_bins, cols, tb, block, occ), tb =
+ * beams per ray-cast warp (a power of two <= 32; elevations = 32 / tb), occ =
+ * 8 to cap the ray-cast registers for 8 blocks of 128 per SM, else 0
  * and returns the number of entries in *count. */
 sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count);
 

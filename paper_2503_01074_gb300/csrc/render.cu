@@ -343,7 +343,8 @@ __device__ __forceinline__ float small_u2f(uint32_t v) {
 // sensor; lane l of warp w traces beam i0 + w * tb + l % tb, elevation
 // j0 + l / tb, so that a warp's rays sample a compact patch of the field of
 // view.  Records go to their canonical index i * n_elev + j.
-__global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_trace(TraceArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
     __shared__ int s_tile;
@@ -868,8 +869,11 @@ void set_kernel_attributes() {
     cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
-cudaError_t launch_trace(const TraceArgs& a, int blocks, cudaStream_t st) {
-    if (blocks > 0) k_trace<<<blocks, 128, 0, st>>>(a);
+cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st) {
+    if (blocks > 0) {
+        if (occupancy >= 8) k_trace<8><<<blocks, 128, 0, st>>>(a);
+        else k_trace<1><<<blocks, 128, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

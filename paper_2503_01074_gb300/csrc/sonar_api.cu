@@ -24,6 +24,7 @@ struct Tune {
     int cols = 0;     // binning: azimuth columns per work unit (0: derive)
     int tb = 0;       // tracing: beams per warp tile, elevations = 32 / tb (0: derive)
     int block = 128;  // binning: threads per block
+    int occ = 0;      // tracing: 8 = cap registers for 8 blocks per SM, 0 = no cap
 };
 
 using ShapeKey = std::array<int, 4>;   // n_beams, n_elev, n_range_bins, n_az_bins
@@ -144,6 +145,15 @@ Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
     return t;
 }
 
+// A single frame alone on the GPU: the tuned shapes, but at least two binning
+// units per SM (the batch tunes may favour few, large units).
+Tune single_tune(const sonar_ctx* ctx, const sonar_sensor& s) {
+    Tune t = tune_for(ctx, s);
+    const int want = std::max(1, s.n_az_bins / (2 * ctx->sm_count));
+    if (t.cols > want) t.cols = want;
+    return t;
+}
+
 SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, const Tune& t, int fan_w,
                       int fan_h) {
     SensorDev d{};
@@ -172,6 +182,7 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     d.cols = t.cols;
     d.n_tiles = (s.n_az_bins + t.cols - 1) / t.cols;
     d.tb = t.tb;
+    d.occ = t.occ;
     const int64_t bb = 4 * t.tb, be = 32 / t.tb;
     d.trace_blocks = (int32_t)(((s.n_beams + bb - 1) / bb) * ((s.n_elev + be - 1) / be));
     return d;
@@ -308,7 +319,7 @@ sonar_status single_forward(sonar_ctx* ctx, const SensorDev& S, const SceneDev& 
     t.params = *p;
     t.hits = hits;
     t.err = ctx->d_err;
-    CU(launch_trace(t, S.trace_blocks, s), "trace launch");
+    CU(launch_trace(t, S.trace_blocks, S.occ, s), "trace launch");
     BinArgs a{};
     a.n_units = S.n_tiles;
     a.n_mat = n_mat;
@@ -372,7 +383,7 @@ extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const so
     if (out->fan && (out->fan_w < 1 || out->fan_h < 1)) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const Tune t = tune_for(ctx, *sensor);
+    const Tune t = single_tune(ctx, *sensor);
     SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
     const int64_t npol = (int64_t)S.nr * S.naz;
     float* noised = out->noised;
@@ -474,6 +485,7 @@ struct sonar_batch {
     int64_t total_rays = 0;
     int64_t total_rows = 0, total_polar = 0;
     int block = 128;
+    int trace_occ = 0;
     int adj_chunk = 0;
     size_t smem1 = 0;
     SensorDev* d_sens = nullptr;
@@ -596,6 +608,10 @@ sonar_status batch_plan(sonar_batch* b) {
     int64_t best = -1;
     for (auto& kv : block_votes)
         if (kv.second > best) { best = kv.second; b->block = kv.first; }
+    // the trace launch takes the occupancy variant of the sensor shape with most rays
+    int64_t most = -1;
+    for (const SensorDev& S : b->hs)
+        if ((int64_t)S.nb * S.ne > most) { most = (int64_t)S.nb * S.ne; b->trace_occ = S.occ; }
     b->total_rows = rows;
     b->total_polar = polar_end;
     int64_t all_rays = 0;
@@ -669,7 +685,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     t.params = *p;
     t.hits = hits;
     t.err = ctx->d_err;
-    CU(launch_trace(t, b->trace_prefix.back(), s), "batch trace launch");
+    CU(launch_trace(t, b->trace_prefix.back(), b->trace_occ, s), "batch trace launch");
     if (events) CU(cudaEventRecordWithFlags(b->ev[6], s, cudaEventRecordExternal), "cudaEventRecord");
     BinArgs a{};
     a.sensors = b->d_sens;
@@ -778,7 +794,7 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
     for (int k = 0; k < n; ++k) {
         SensorDev S = b->hs[k];
         const sonar_batch_item& it = items[k];
-        const SensorDev fresh = make_sensor(it.sensor, it.seed, it.frame, Tune{S.cols, S.tb, b->block},
+        const SensorDev fresh = make_sensor(it.sensor, it.seed, it.frame, Tune{S.cols, S.tb, b->block, S.occ},
                                             it.fan_w, it.fan_h);
         memcpy(S.pos, fresh.pos, sizeof S.pos);
         memcpy(S.rot, fresh.rot, sizeof S.rot);
@@ -1027,25 +1043,28 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
         Tune best;
         best.block = 128;
         float best_ms = 1e30f;
-        // the trace warp tile (beams x elevations per warp) with default binning shapes
-        for (int tb : {1, 2, 4, 8, 16, 32}) {
-            ctx->tune[k] = Tune{0, tb, 128};
-            if ((st = batch_plan(b)) != SONAR_OK) goto restore;
-            const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
-            if (cudaGetLastError() != cudaSuccess) continue;
-            if (ms < best_ms) { best_ms = ms; best.tb = tb; }
-        }
-        // then columns per binning unit and the binning block size
-        best_ms = 1e30f;
-        const int tb = best.tb;
-        for (int block : {64, 128, 256}) {
-            for (int cols : {1, 2, 4, 8, 16, 32}) {
-                if (cols > k[3] || (size_t)cols * k[2] * 4 > kMaxDynSmem / 2) continue;
-                ctx->tune[k] = Tune{cols, tb, block};
+        // the trace warp tile (beams x elevations per warp) and register budget,
+        // with default binning shapes
+        for (int occ : {0, 8}) {
+            for (int tb : {1, 2, 4, 8, 16, 32}) {
+                ctx->tune[k] = Tune{0, tb, 128, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
                 const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
                 if (cudaGetLastError() != cudaSuccess) continue;
-                if (ms < best_ms) { best_ms = ms; best = Tune{cols, tb, block}; }
+                if (ms < best_ms) { best_ms = ms; best.tb = tb; best.occ = occ; }
+            }
+        }
+        // then columns per binning unit and the binning block size
+        best_ms = 1e30f;
+        const int tb = best.tb, occ = best.occ;
+        for (int block : {64, 128, 256}) {
+            for (int cols : {1, 2, 4, 8, 16, 32}) {
+                if (cols > k[3] || (size_t)cols * k[2] * 4 > kMaxDynSmem / 2) continue;
+                ctx->tune[k] = Tune{cols, tb, block, occ};
+                if ((st = batch_plan(b)) != SONAR_OK) goto restore;
+                const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
+                if (cudaGetLastError() != cudaSuccess) continue;
+                if (ms < best_ms) { best_ms = ms; best = Tune{cols, tb, block, occ}; }
             }
         }
         ctx->tune[k] = best;
@@ -1067,7 +1086,7 @@ extern "C" sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t c
         if (rows && k < cap) {
             int32_t* r = rows + 8 * k;
             r[0] = kv.first[0]; r[1] = kv.first[1]; r[2] = kv.first[2]; r[3] = kv.first[3];
-            r[4] = kv.second.cols; r[5] = kv.second.tb; r[6] = kv.second.block; r[7] = 0;
+            r[4] = kv.second.cols; r[5] = kv.second.tb; r[6] = kv.second.block; r[7] = kv.second.occ;
         }
         ++k;
     }
@@ -1080,9 +1099,9 @@ extern "C" sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int
     for (int k = 0; k < count; ++k) {
         const int32_t* r = rows + 8 * k;
         if (r[0] < 1 || r[1] < 1 || r[2] < 1 || r[3] < 1 || r[4] < 1 || r[5] < 1 || r[5] > 32 ||
-            (r[5] & (r[5] - 1)) || r[6] < 32 || r[6] > 512 || (r[6] & 31))
+            (r[5] & (r[5] - 1)) || r[6] < 32 || r[6] > 512 || (r[6] & 31) || (r[7] != 0 && r[7] != 8))
             return fail(ctx, SONAR_ERR_ARG, "bad tune row " + std::to_string(k));
-        ctx->tune[ShapeKey{r[0], r[1], r[2], r[3]}] = Tune{r[4], r[5], r[6]};
+        ctx->tune[ShapeKey{r[0], r[1], r[2], r[3]}] = Tune{r[4], r[5], r[6], r[7]};
     }
     return SONAR_OK;
 }
@@ -1195,7 +1214,7 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     uint32_t* rowmax = (uint32_t*)base;
     sonar_hit* hits = out->hits ? out->hits : (sonar_hit*)((float*)base + 64);
     float* noised = out->noised ? out->noised : (float*)base + noised_at;
-    const Tune t = tune_for(ctx, *sensor);
+    const Tune t = single_tune(ctx, *sensor);
     const SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
     // single_forward clears the maximum (the array still holds the previous
     // call's values); hit records and the noised image are fully overwritten

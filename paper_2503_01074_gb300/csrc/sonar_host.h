@@ -32,7 +32,7 @@ inline SceneDev scene_dev(const SceneStore& s) {
 
 // Kernel launchers (render.cu).
 void set_kernel_attributes();
-cudaError_t launch_trace(const TraceArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st);
 cudaError_t launch_bin(const BinArgs& a, int det, int grid, int block, size_t smem, cudaStream_t st);
 int bin_blocks_per_sm(int det, int block, size_t smem);
 constexpr size_t kMaxDynSmem = 200 * 1024;

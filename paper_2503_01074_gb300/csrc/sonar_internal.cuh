@@ -52,6 +52,7 @@ struct SensorDev {
     int32_t cols;        // binning: azimuth columns per work unit
     int32_t n_tiles;     // binning work units of this sensor = ceil(naz / cols)
     int32_t tb;          // trace: beams per warp tile (elevations = 32 / tb)
+    int32_t occ;         // trace: 8 = register budget for 8 blocks of 128 per SM, else none
     int32_t trace_blocks;  // trace: blocks of 4 warp tiles covering the sensor
     int64_t polar_off, hits_off, fan_off, rowmax_off;
 };
