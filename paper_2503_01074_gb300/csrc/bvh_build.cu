@@ -6,11 +6,14 @@
 //   3. radix sort                     stable LSD, 8-bit digits, histogram / scan / scatter
 //   4. Karras hierarchy               one thread per internal node (Karras, HPG 2012)
 //   5. bottom-up refit                leaf-to-root climb, second visitor merges boxes
-//   6. packing                        64-byte child-pair nodes, runs of <= kLeafMax
-//                                     triangles collapsed into leaves, 48-byte triangles
+//   6. packing                        runs of <= kLeafMax triangles collapsed into
+//                                     leaves; binary child pairs collapsed into
+//                                     4-wide 128-byte nodes; 48-byte triangles
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstring>
 #include <string>
 
 #include "sonar_internal.cuh"
@@ -382,6 +385,55 @@ __global__ void k_pack_tris(const float* verts, const int32_t* tris, const int32
     mat_orig[o] = m;
 }
 
+// 4-wide nodes: the binary nodes kept are the reachable ones (covering more
+// than kLeafMax triangles, so not inside a collapsed leaf) at even depth; each
+// takes its grandchildren in place of its internal children.
+__global__ void k_node4_flags(int64_t n, const int32_t* parent, const int2* range, uint32_t* flag) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n - 1) return;
+    int depth = 0;
+    for (int32_t q = parent[p]; q >= 0; q = parent[q]) ++depth;
+    const int2 r = range[p];
+    flag[p] = (r.y - r.x + 1 > kLeafMax && (depth & 1) == 0) ? 1u : 0u;
+}
+
+__global__ void k_pack4(int64_t n, const float4* pairs, const uint32_t* flag, const uint32_t* index,
+                        float4* nodes4) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n - 1 || !flag[p]) return;
+    float lo[3][4], hi[3][4];
+    int32_t h[4];
+    int k = 0;
+    for (int side = 0; side < 2; ++side) {
+        const float4 a = pairs[4 * p + 2 * side], b = pairs[4 * p + 2 * side + 1];
+        const int32_t c = __float_as_int(a.w);
+        if (c >= 0) {
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const float4 a2 = pairs[4 * (int64_t)c + 2 * s2], b2 = pairs[4 * (int64_t)c + 2 * s2 + 1];
+                const int32_t g = __float_as_int(a2.w);
+                lo[0][k] = a2.x; lo[1][k] = a2.y; lo[2][k] = a2.z;
+                hi[0][k] = b2.x; hi[1][k] = b2.y; hi[2][k] = b2.z;
+                h[k++] = g >= 0 ? (int32_t)index[g] : g;
+            }
+        } else {
+            lo[0][k] = a.x; lo[1][k] = a.y; lo[2][k] = a.z;
+            hi[0][k] = b.x; hi[1][k] = b.y; hi[2][k] = b.z;
+            h[k++] = c;
+        }
+    }
+    for (; k < 4; ++k) {   // empty slot: a box no ray enters
+        for (int a = 0; a < 3; ++a) lo[a][k] = hi[a][k] = __int_as_float(0x7F800000);
+        h[k] = kEmpty;
+    }
+    float4* o = nodes4 + 8 * (int64_t)index[p];
+    for (int a = 0; a < 3; ++a) {
+        o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+        o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+    }
+    o[6] = make_float4(__int_as_float(h[0]), __int_as_float(h[1]), __int_as_float(h[2]), __int_as_float(h[3]));
+    o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -481,46 +533,72 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
         uint32_t* tv = v0; v0 = v1; v1 = tv;
     }
 
-    // persistent buffers
-    const int64_t n_pairs = n > 1 ? n - 1 : 1;
-    float4* nodes = nullptr;
+    // persistent buffers: triangles now, nodes once their count is known
     float4* tri_out = nullptr;
     int32_t* mat_orig = nullptr;
-    if (cudaMalloc(&nodes, sizeof(float4) * 4 * n_pairs) != cudaSuccess ||
-        cudaMalloc(&tri_out, sizeof(float4) * 3 * n) != cudaSuccess ||
+    if (cudaMalloc(&tri_out, sizeof(float4) * 3 * n) != cudaSuccess ||
         cudaMalloc(&mat_orig, sizeof(int32_t) * n) != cudaSuccess) {
-        cudaFree(nodes); cudaFree(tri_out); cudaFree(mat_orig);
+        cudaFree(tri_out); cudaFree(mat_orig);
         *msg = "out of device memory (scene)";
         return SONAR_ERR_OOM;
     }
-    out->nodes = nodes;
     out->tris = tri_out;
     out->mat_orig = mat_orig;
-    out->n_pairs = n > 1 ? n - 1 : 0;
-    out->bytes = sizeof(float4) * (4 * n_pairs + 3 * n) + sizeof(int32_t) * n;
+    out->bytes = sizeof(float4) * 3 * n + sizeof(int32_t) * n;
 
     k_pack_tris<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, mat, v0, n, tri_out, mat_orig);
     int height = 0;
-    if (n == 1) {
-        out->root = leaf_handle(0, 1);
+    if (n <= kLeafMax) {
+        out->root = leaf_handle(0, (int32_t)n);
+        if (n > 1) {
+            k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(k0, n, child, parent, range);
+            cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
+            k_refit<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, parent, visits,
+                                                                   blo, bhi);
+        }
     } else {
+        float4* pairs = S.get<float4>(4 * (n - 1));
+        uint32_t* flag = S.get<uint32_t>(n);
+        uint32_t* index = S.get<uint32_t>(n);
+        const int64_t fchunks = (n - 1 + kScanChunk - 1) / kScanChunk;
+        uint32_t* fsums = S.get<uint32_t>(fchunks);
+        if (S.err != cudaSuccess) { *msg = "out of device memory (build scratch)"; return SONAR_ERR_OOM; }
         k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(k0, n, child, parent, range);
         cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
         k_refit<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, parent, visits,
                                                                blo, bhi);
         k_pack_nodes<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, range,
-                                                                        blo, bhi, pad, nodes);
+                                                                        blo, bhi, pad, pairs);
+        k_node4_flags<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(n, parent, range, flag);
+        k_scan_sums<<<(unsigned)fchunks, kThreads, 0, st>>>(flag, n - 1, fsums);
+        k_scan_top<<<1, 1024, 0, st>>>(fsums, fchunks);
+        k_scan_apply<<<(unsigned)fchunks, kThreads, 0, st>>>(flag, n - 1, fsums, index);
+        uint32_t last[2] = {0, 0};
         float4 root_hi;
-        e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(&last[0], index + (n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&last[1], flag + (n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { *msg = std::string("build failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
         memcpy(&height, &root_hi.w, 4);
-        out->root = n <= kLeafMax ? leaf_handle(0, (int32_t)n) : 0;
+        const int64_t n4 = (int64_t)last[0] + last[1];
+        float4* nodes = nullptr;
+        if (cudaMalloc(&nodes, sizeof(float4) * 8 * std::max<int64_t>(n4, 1)) != cudaSuccess) {
+            *msg = "out of device memory (scene nodes)";
+            return SONAR_ERR_OOM;
+        }
+        out->nodes = nodes;
+        out->n_pairs = n4;
+        out->bytes += sizeof(float4) * 8 * n4;
+        k_pack4<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(n, pairs, flag, index, nodes);
+        out->root = 0;
     }
     out->height = height;
     e = cudaGetLastError();
     if (e != cudaSuccess) { *msg = std::string("build kernel launch failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
-    if (height >= kStackMax) {
+    // a 4-wide node sits on every second binary level and pushes at most three
+    // children: the walk never needs more than 3 * ceil(height / 2) + 1 entries
+    if (3 * ((height + 1) / 2) + 1 > kStackMax) {
         *msg = "hierarchy too deep for the traversal stack (height " + std::to_string(height) + ")";
         return SONAR_ERR_ARG;
     }

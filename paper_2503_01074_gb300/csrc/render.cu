@@ -172,44 +172,55 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
 
     for (;;) {
         if (node >= 0) {
-            const float4* p = sc.nodes + 4 * (int64_t)node;
-            const float4 a0 = __ldg(p), b0 = __ldg(p + 1), a1 = __ldg(p + 2), b1 = __ldg(p + 3);
+            const float4* p = sc.nodes + 8 * (int64_t)node;
+            const float4 lx = __ldg(p), hx = __ldg(p + 1), ly = __ldg(p + 2), hy = __ldg(p + 3);
+            const float4 lz = __ldg(p + 4), hz = __ldg(p + 5);
+            const int4 ch = __ldg(reinterpret_cast<const int4*>(p + 6));
             if (STATS) {
                 ++visits;
                 atomicOr(tc->node_bits + (node >> 5), 1u << (node & 31));
             }
             const float tcut = best_t * 1.00002f;
-            float t0 = fmaf(a0.x, inv.x, -oinv.x), t1 = fmaf(b0.x, inv.x, -oinv.x);
-            float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
-            t0 = fmaf(a0.y, inv.y, -oinv.y); t1 = fmaf(b0.y, inv.y, -oinv.y);
-            lo0 = fmaxf(lo0, fminf(t0, t1)); hi0 = fminf(hi0, fmaxf(t0, t1));
-            t0 = fmaf(a0.z, inv.z, -oinv.z); t1 = fmaf(b0.z, inv.z, -oinv.z);
-            lo0 = fmaxf(fmaxf(lo0, fminf(t0, t1)), 0.0f); hi0 = fminf(fminf(hi0, fmaxf(t0, t1)), tcut);
-            t0 = fmaf(a1.x, inv.x, -oinv.x); t1 = fmaf(b1.x, inv.x, -oinv.x);
-            float lo1 = fminf(t0, t1), hi1 = fmaxf(t0, t1);
-            t0 = fmaf(a1.y, inv.y, -oinv.y); t1 = fmaf(b1.y, inv.y, -oinv.y);
-            lo1 = fmaxf(lo1, fminf(t0, t1)); hi1 = fminf(hi1, fmaxf(t0, t1));
-            t0 = fmaf(a1.z, inv.z, -oinv.z); t1 = fmaf(b1.z, inv.z, -oinv.z);
-            lo1 = fmaxf(fmaxf(lo1, fminf(t0, t1)), 0.0f); hi1 = fminf(fminf(hi1, fmaxf(t0, t1)), tcut);
-            const bool h0 = lo0 <= hi0 * 1.0000005f, h1 = lo1 <= hi1 * 1.0000005f;
-            const int32_t c0 = __float_as_int(a0.w), c1 = __float_as_int(a1.w);
-            if (h0 && h1) {
-                if (sp >= kStackMax) {
-                    atomicOr(err, SONAR_DEVERR_STACK);
-                    best = -1;
-                    break;
-                }
-                const bool first0 = lo0 <= lo1;
-                stack[sp++] = first0 ? c1 : c0;
-                node = first0 ? c0 : c1;
-            } else if (h0) {
-                node = c0;
-            } else if (h1) {
-                node = c1;
-            } else {
+            float tn[4];
+            int32_t hn[4];
+            const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
+            const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
+            const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
+            const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
+                float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+                t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
+                lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
+                t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
+                lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
+                const bool hit = hs[c] != kEmpty && lo <= hi * 1.0000005f;
+                tn[c] = hit ? lo : CUDART_INF_F;
+                hn[c] = hs[c];
+            }
+            // nearest first: a 4-input sorting network on (entry distance, handle)
+#define SONAR_CSWAP(a, b)                                                    \
+            if (tn[b] < tn[a]) {                                             \
+                const float tt = tn[a]; tn[a] = tn[b]; tn[b] = tt;           \
+                const int32_t hh = hn[a]; hn[a] = hn[b]; hn[b] = hh;         \
+            }
+            SONAR_CSWAP(0, 1) SONAR_CSWAP(2, 3) SONAR_CSWAP(0, 2) SONAR_CSWAP(1, 3) SONAR_CSWAP(1, 2)
+#undef SONAR_CSWAP
+            const int nhit = (tn[0] < CUDART_INF_F) + (tn[1] < CUDART_INF_F) + (tn[2] < CUDART_INF_F) +
+                             (tn[3] < CUDART_INF_F);
+            if (nhit == 0) {
                 if (sp == 0) break;
                 node = stack[--sp];
+                continue;
             }
+            if (sp + nhit - 1 > kStackMax) {
+                atomicOr(err, SONAR_DEVERR_STACK);
+                best = -1;
+                break;
+            }
+            for (int c = nhit - 1; c >= 1; --c) stack[sp++] = hn[c];
+            node = hn[0];
             continue;
         }
         // leaf: a run of triangles in leaf order

@@ -1,12 +1,12 @@
 // Internal device-side definitions of libsonar (GB300, sm_103a).
 //
 // Data layout in HBM
-//   node pairs  float4[4] per internal node p of the LBVH (64 B, 64-B aligned):
-//               [0] (lo0.x, lo0.y, lo0.z, handle0)  [1] (hi0.x, hi0.y, hi0.z, 0)
-//               [2] (lo1.x, lo1.y, lo1.z, handle1)  [3] (hi1.x, hi1.y, hi1.z, 0)
-//               i.e. the two 32-byte child records of p, each loaded as two float4.
-//   handles     int32: >= 0 an internal node pair index; < 0 a leaf
-//               ~((first << 3) | (count - 1)), a run of 1..8 triangles in leaf order.
+//   nodes       4-wide, float4[8] = 128 B (one cache line) per node, children in
+//               structure-of-arrays form: [0] lo.x of children 0..3, [1] hi.x,
+//               [2] lo.y, [3] hi.y, [4] lo.z, [5] hi.z, [6] the 4 child handles,
+//               [7] unused.  Empty slots: boxes at +inf (never entered), kEmpty.
+//   handles     int32: >= 0 a node index; < 0 a leaf ~((first << 3) | (count - 1)),
+//               a run of 1..8 triangles in leaf order; kEmpty an empty slot.
 //   triangles   float4[3] per triangle in leaf order (48 B):
 //               (v0, material id bits), (v1, caller's index bits), (v2, 0).
 //   polar       [n_range_bins][n_az_bins] f32 per sensor (row = range bin).
@@ -20,7 +20,7 @@
 namespace sonar {
 
 constexpr int kLeafMax = 4;          // triangles per collapsed leaf
-constexpr int kStackMax = 64;        // traversal stack entries (tree height is checked at build)
+constexpr int kStackMax = 96;        // traversal stack entries (tree height is checked at build)
 constexpr int32_t kEmpty = (int32_t)0x80000000;
 constexpr int kMaxMat = 1024;
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
@@ -31,7 +31,7 @@ __host__ __device__ inline int32_t leaf_handle(int32_t first, int32_t count) {
 
 // The scene as the kernels see it.
 struct SceneDev {
-    const float4* nodes;      // [n_pairs * 4]
+    const float4* nodes;      // [n_nodes * 8], 4-wide
     const float4* tris;       // [n_tris * 3]
     const int32_t* mat_orig;  // [n_tris] material of the caller's triangle index
     int32_t root;             // root handle (kEmpty if the scene has no triangles)
