@@ -440,13 +440,15 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 // Temporary device buffers of one build, freed in stream order on exit.
 struct BuildScratch {
+    static constexpr int kMax = 32;
     cudaStream_t st;
-    void* ptrs[16] = {};
+    void* ptrs[kMax] = {};
     int n = 0;
     cudaError_t err = cudaSuccess;
     template <class T>
     T* get(size_t count) {
         void* p = nullptr;
+        if (n >= kMax) err = cudaErrorMemoryAllocation;   // more buffers than slots: refuse, never overflow
         if (err == cudaSuccess) err = cudaMallocAsync(&p, count * sizeof(T) + 16, st);
         if (err != cudaSuccess) return nullptr;
         ptrs[n++] = p;
