@@ -136,18 +136,34 @@ __device__ bool mt64(const double o[3], const double d[3], float4 a, float4 b, f
 // closest hit: LBVH walk with a short stack
 // ---------------------------------------------------------------------------
 
-// The FP64 decision for one triangle: builds the exact ray of (i, j) and runs
-// mt64.  Out of line so that the FP32 walk keeps no FP64 state in registers;
-// it runs only for tests FP32 cannot decide.
-__device__ __noinline__ bool exact_hit(const SensorDev& s, int i, int j, float4 a, float4 b, float4 c,
-                                       double* t) {
+// The FP64 decisions, out of line and returning no double: the FP32 walk then
+// carries no FP64-typed state, which would otherwise occupy the FP64 pipe on
+// every candidate even though these functions run for few tests.
+//
+// exact_hit: does the exact ray of (i, j) hit the triangle?  *t = its distance
+// rounded to FP32.
+__device__ __noinline__ bool exact_hit(const SensorDev& s, int i, int j, float4 a, float4 b, float4 c, float* t) {
     double d[3];
     ray_dir64(s, i, j, d);
     const double o[3] = {s.pos[0], s.pos[1], s.pos[2]};
     double tt;
     if (!mt64(o, d, a, b, c, tt)) return false;
-    *t = tt;
+    *t = (float)tt;
     return true;
+}
+
+// exact_closer: along the exact ray of (i, j), is triangle `p` (index id_p) the
+// closest-hit choice over triangle `q` (index id_q)?  Nearer exact distance
+// first, then the lower index; a triangle the exact ray misses never wins.
+__device__ __noinline__ bool exact_closer(const SensorDev& s, int i, int j, const float4* p, uint32_t id_p,
+                                          const float4* q, uint32_t id_q) {
+    double d[3];
+    ray_dir64(s, i, j, d);
+    const double o[3] = {s.pos[0], s.pos[1], s.pos[2]};
+    double tp, tq;
+    if (!mt64(o, d, __ldg(p), __ldg(p + 1), __ldg(p + 2), tp)) return false;
+    if (!mt64(o, d, __ldg(q), __ldg(q + 1), __ldg(q + 2), tq)) return true;
+    return tp < tq || (tp == tq && id_p < id_q);
 }
 
 template <bool STATS>
@@ -166,8 +182,6 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
     int best = -1;
     uint32_t best_id = 0xFFFFFFFFu;
     float best_t = tlimit;
-    bool best_exact = false;
-    double best_t64 = 0.0;
     uint64_t visits = 0, tests = 0, exact_n = 0;
 
     for (;;) {
@@ -241,13 +255,9 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
             float t;
             const int r = mt32(o, d, a, b, c, t);
             if (r == 0) continue;
-            bool exact = false;
-            double t64 = 0.0;
             if (r == 2) {
                 if (STATS) ++exact_n;
-                if (!exact_hit(s, ri, rj, a, b, c, &t64)) continue;
-                t = (float)t64;
-                exact = true;
+                if (!exact_hit(s, ri, rj, a, b, c, &t)) continue;
             }
             if (!(t < tlimit)) continue;
             const uint32_t id = __float_as_uint(b.w);
@@ -256,28 +266,15 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
                 take = true;
             } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
                 // near tie: decide on the exact distances, then on the caller's index
-                if (!exact) {
-                    if (STATS) ++exact_n;
-                    if (!exact_hit(s, ri, rj, a, b, c, &t64)) continue;
-                    exact = true;
-                }
-                if (!best_exact) {
-                    const float4* bp = sc.tris + 3 * (int64_t)best;
-                    double bt;
-                    if (STATS) ++exact_n;
-                    best_t64 = exact_hit(s, ri, rj, __ldg(bp), __ldg(bp + 1), __ldg(bp + 2), &bt) ? bt : CUDART_INF;
-                    best_exact = true;
-                }
-                take = t64 < best_t64 || (t64 == best_t64 && id < best_id);
+                if (STATS) ++exact_n;
+                take = exact_closer(s, ri, rj, tp, id, sc.tris + 3 * (int64_t)best, best_id);
             } else {
                 take = t < best_t;
             }
             if (take) {
                 best = f;
                 best_id = id;
-                best_t = exact ? (float)t64 : t;
-                best_exact = exact;
-                best_t64 = t64;
+                best_t = t;
             }
         }
         if (sp == 0) break;
