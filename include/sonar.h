@@ -169,9 +169,10 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
                           void* stream);
 
 /* Maximum scratch, in 4-byte words, that sonar_render_noalloc can use: 64
- * words, plus 4 words a ray for the hit records when out->hits is NULL, plus
- * (rounded up to 64 words first) n_range_bins * n_az_bins words for the
- * noised image when out->noised is NULL. */
+ * words, plus 4 words a beam and an elevation (exact-ray tables), plus 4 words
+ * a ray for the hit records when out->hits is NULL, plus n_range_bins *
+ * n_az_bins words for the noised image when out->noised is NULL (each part
+ * rounded up to 64 words). */
 #define SONAR_NOALLOC_SCRATCH_WORDS (1u << 20)
 
 /* sonar_render for callers that must not allocate device memory: a render
@@ -183,8 +184,8 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
  * until the process exits.  The caller still provides every input and
  * output, as for sonar_render, and gets the same results.
  *   - A frame needing more scratch than the array holds is rejected with
- *     SONAR_ERR_ARG before anything is enqueued (with out->hits and
- *     out->noised given, 64 words suffice).
+ *     SONAR_ERR_ARG before anything is enqueued (pass out->hits and
+ *     out->noised to need only the small fixed parts).
  *   - The first call on a device looks up the array's device address (which
  *     may load the library's device code) and caches it; make that first call
  *     before any stream capture on that device.

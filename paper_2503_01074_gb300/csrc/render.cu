@@ -57,22 +57,62 @@ __device__ __forceinline__ float3 ray_dir32(const SensorDev& s, int i, int j) {
     return f3(w.x * inv, w.y * inv, w.z * inv);
 }
 
-// The exact ray direction, computed as the definition states, in FP64.
-__device__ void ray_dir64(const SensorDev& s, int i, int j, double d[3]) {
-    const double H = s.hfov, V = s.vfov;
-    const double phi = -H / 2.0 + (i + 0.5) * H / s.nb;
-    const double th = -V / 2.0 + (j + 0.5) * V / s.ne;
-    double sp, cp, st, ct;
-    sincos(phi, &sp, &cp);
-    sincos(th, &st, &ct);
-    const double ds[3] = {sp * ct, cp * ct, st};
-    double w[3];
+// ---- float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2 ----
+// Error-free transforms (Knuth's two-sum, FMA-based two-product) carried out
+// with explicit round-to-nearest operations so that no contraction or
+// reassociation can change them.  About 48 significand bits, all on the FP32
+// pipes.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {   // requires |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    const ff t = ff_two_sum(a.lo, b.lo);
+    s = ff_quick(s.hi, __fadd_rn(s.lo, t.hi));
+    return ff_quick(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ int ff_sign(ff a) {
+    return a.hi > 0.0f ? 1 : a.hi < 0.0f ? -1 : (a.lo > 0.0f ? 1 : a.lo < 0.0f ? -1 : 0);
+}
+__device__ __forceinline__ ff ff_dot(const ff a[3], const ff b[3]) {
+    return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
+
+// The exact ray of (i, j) in float-float, unnormalised: w = R ds with ds from
+// the sensor's float-float sine/cosine tables (beam i, elevation j).  The hit
+// decisions below only use signs and ratios, which a positive scale leaves
+// unchanged.
+__device__ __forceinline__ void ray_dir_ff(const SensorDev& s, int i, int j, ff w[3]) {
+    const float4 bp = __ldg(s.trig + i), el = __ldg(s.trig + s.nb + j);
+    const ff sp{bp.x, bp.y}, cp{bp.z, bp.w}, st{el.x, el.y}, ct{el.z, el.w};
+    const ff ds[3] = {ff_mul(sp, ct), ff_mul(cp, ct), st};
     for (int a = 0; a < 3; ++a)
-        w[a] = (double)s.rot[3 * a] * ds[0] + (double)s.rot[3 * a + 1] * ds[1] + (double)s.rot[3 * a + 2] * ds[2];
-    const double n = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-    d[0] = w[0] / n;
-    d[1] = w[1] / n;
-    d[2] = w[2] / n;
+        w[a] = ff_add(ff_add(ff_mulf(ds[0], s.rot[3 * a]), ff_mulf(ds[1], s.rot[3 * a + 1])),
+                      ff_mulf(ds[2], s.rot[3 * a + 2]));
 }
 
 // ---------------------------------------------------------------------------
@@ -110,25 +150,32 @@ __device__ __forceinline__ int mt32(float3 o, float3 d, float4 a, float4 b, floa
     return 2;
 }
 
-// FP64 Moller-Trumbore on the exact ray: hit iff det != 0, u >= 0, v >= 0,
-// u + v <= 1, t > 0.
-__device__ bool mt64(const double o[3], const double d[3], float4 a, float4 b, float4 c, double& t) {
-    const double v0[3] = {a.x, a.y, a.z};
-    const double e1[3] = {(double)b.x - v0[0], (double)b.y - v0[1], (double)b.z - v0[2]};
-    const double e2[3] = {(double)c.x - v0[0], (double)c.y - v0[1], (double)c.z - v0[2]};
-    const double p[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
-    const double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
-    if (det == 0.0) return false;
-    const double inv = 1.0 / det;
-    const double s[3] = {o[0] - v0[0], o[1] - v0[1], o[2] - v0[2]};
-    const double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) * inv;
-    if (u < 0.0 || u > 1.0) return false;
-    const double q[3] = {s[1] * e1[2] - s[2] * e1[1], s[2] * e1[0] - s[0] * e1[2], s[0] * e1[1] - s[1] * e1[0]};
-    const double v = (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]) * inv;
-    if (v < 0.0 || u + v > 1.0) return false;
-    const double tt = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * inv;
-    if (!(tt > 0.0)) return false;
-    t = tt;
+// Moller-Trumbore on the exact ray in float-float, without division: with
+// D = |det| and U, V, T the u, v, t numerators times sign(det), the test
+// "det != 0, u >= 0, v >= 0, u + v <= 1, t > 0" becomes
+// "D != 0, U >= 0, V >= 0, D - U - V >= 0, T > 0"; t = T / D along w.
+// Edge vectors and s = o - v0 are exact (two-sum of FP32 inputs).
+__device__ __forceinline__ bool mt_ff(const float o[3], const ff d[3], float4 a, float4 b, float4 c, ff& D,
+                                      ff& T) {
+    const ff e1[3] = {ff_two_sum(b.x, -a.x), ff_two_sum(b.y, -a.y), ff_two_sum(b.z, -a.z)};
+    const ff e2[3] = {ff_two_sum(c.x, -a.x), ff_two_sum(c.y, -a.y), ff_two_sum(c.z, -a.z)};
+    const ff sv[3] = {ff_two_sum(o[0], -a.x), ff_two_sum(o[1], -a.y), ff_two_sum(o[2], -a.z)};
+    const ff p[3] = {ff_sub(ff_mul(d[1], e2[2]), ff_mul(d[2], e2[1])),
+                     ff_sub(ff_mul(d[2], e2[0]), ff_mul(d[0], e2[2])),
+                     ff_sub(ff_mul(d[0], e2[1]), ff_mul(d[1], e2[0]))};
+    const ff det = ff_dot(e1, p);
+    const int sg = ff_sign(det);
+    if (sg == 0) return false;
+    ff u = ff_dot(sv, p);
+    const ff q[3] = {ff_sub(ff_mul(sv[1], e1[2]), ff_mul(sv[2], e1[1])),
+                     ff_sub(ff_mul(sv[2], e1[0]), ff_mul(sv[0], e1[2])),
+                     ff_sub(ff_mul(sv[0], e1[1]), ff_mul(sv[1], e1[0]))};
+    ff v = ff_dot(d, q);
+    ff t = ff_dot(e2, q);
+    D = det;
+    if (sg < 0) { D = ff_neg(det); u = ff_neg(u); v = ff_neg(v); t = ff_neg(t); }
+    if (ff_sign(u) < 0 || ff_sign(v) < 0 || ff_sign(ff_sub(ff_sub(D, u), v)) < 0 || ff_sign(t) <= 0) return false;
+    T = t;
     return true;
 }
 
@@ -136,34 +183,58 @@ __device__ bool mt64(const double o[3], const double d[3], float4 a, float4 b, f
 // closest hit: LBVH walk with a short stack
 // ---------------------------------------------------------------------------
 
-// The FP64 decisions, out of line and returning no double: the FP32 walk then
-// carries no FP64-typed state, which would otherwise occupy the FP64 pipe on
-// every candidate even though these functions run for few tests.
+// The exact decisions, out of line (rarely needed; they would otherwise add
+// registers to the FP32 walk) and in float-float on the FP32 pipes.
 //
-// exact_hit: does the exact ray of (i, j) hit the triangle?  *t = its distance
-// rounded to FP32.
+// exact_hit: does the exact ray of (i, j) hit the triangle?  *t = the hit
+// distance in FP32.
 __device__ __noinline__ bool exact_hit(const SensorDev& s, int i, int j, float4 a, float4 b, float4 c, float* t) {
-    double d[3];
-    ray_dir64(s, i, j, d);
-    const double o[3] = {s.pos[0], s.pos[1], s.pos[2]};
-    double tt;
-    if (!mt64(o, d, a, b, c, tt)) return false;
-    *t = (float)tt;
+    ff w[3];
+    ray_dir_ff(s, i, j, w);
+    const float o[3] = {s.pos[0], s.pos[1], s.pos[2]};
+    ff D, T;
+    if (!mt_ff(o, w, a, b, c, D, T)) return false;
+    const float len = sqrtf(w[0].hi * w[0].hi + w[1].hi * w[1].hi + w[2].hi * w[2].hi);
+    *t = (T.hi / D.hi) * len;
     return true;
 }
 
 // exact_closer: along the exact ray of (i, j), is triangle `p` (index id_p) the
 // closest-hit choice over triangle `q` (index id_q)?  Nearer exact distance
-// first, then the lower index; a triangle the exact ray misses never wins.
+// first (T_p / D_p < T_q / D_q, compared as T_p D_q < T_q D_p), then the lower
+// index; a triangle the exact ray misses never wins.
 __device__ __noinline__ bool exact_closer(const SensorDev& s, int i, int j, const float4* p, uint32_t id_p,
                                           const float4* q, uint32_t id_q) {
-    double d[3];
-    ray_dir64(s, i, j, d);
-    const double o[3] = {s.pos[0], s.pos[1], s.pos[2]};
-    double tp, tq;
-    if (!mt64(o, d, __ldg(p), __ldg(p + 1), __ldg(p + 2), tp)) return false;
-    if (!mt64(o, d, __ldg(q), __ldg(q + 1), __ldg(q + 2), tq)) return true;
-    return tp < tq || (tp == tq && id_p < id_q);
+    ff w[3];
+    ray_dir_ff(s, i, j, w);
+    const float o[3] = {s.pos[0], s.pos[1], s.pos[2]};
+    ff Dp, Tp, Dq, Tq;
+    if (!mt_ff(o, w, __ldg(p), __ldg(p + 1), __ldg(p + 2), Dp, Tp)) return false;
+    if (!mt_ff(o, w, __ldg(q), __ldg(q + 1), __ldg(q + 2), Dq, Tq)) return true;
+    const int c = ff_sign(ff_sub(ff_mul(Tp, Dq), ff_mul(Tq, Dp)));
+    return c < 0 || (c == 0 && id_p < id_q);
+}
+
+// Float-float sine and cosine tables of the sensor's beam azimuths
+// phi_i = -H/2 + (i + 1/2) H / N_b and elevations theta_j = -V/2 + (j + 1/2) V / N_e
+// (computed in FP64 once per sensor, split into hi + lo floats): trig[i] for
+// beams, trig[N_b + j] for elevations, each (sin hi, sin lo, cos hi, cos lo).
+__global__ void k_trig(const SensorDev* sensors, SensorDev one) {
+    const SensorDev& s = sensors ? sensors[blockIdx.y] : one;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.nb + s.ne) return;
+    double a;
+    if (k < s.nb) {
+        const double H = s.hfov;
+        a = -H / 2.0 + (k + 0.5) * H / s.nb;
+    } else {
+        const double V = s.vfov;
+        a = -V / 2.0 + (k - s.nb + 0.5) * V / s.ne;
+    }
+    double sn, cs;
+    sincos(a, &sn, &cs);
+    const float sh = (float)sn, ch = (float)cs;
+    s.trig[k] = make_float4(sh, (float)(sn - (double)sh), ch, (float)(cs - (double)ch));
 }
 
 template <bool STATS>
@@ -875,6 +946,13 @@ void set_kernel_attributes() {
     cudaFuncSetAttribute(k_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
+
+cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_sensors, int max_angles,
+                        cudaStream_t st) {
+    const dim3 grid((unsigned)((max_angles + 127) / 128), (unsigned)n_sensors);
+    k_trig<<<grid, 128, 0, st>>>(sensors, one);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st) {

@@ -44,7 +44,7 @@ struct sonar_ctx {
     std::vector<bool> alive;
     std::string last_error;
     uint32_t* d_err = nullptr;
-    Scratch rowmax, noised, rowinfo, partials, counters, hits;
+    Scratch rowmax, noised, rowinfo, partials, counters, hits, trig;
     std::map<ShapeKey, Tune> tune;
 };
 
@@ -223,7 +223,8 @@ extern "C" sonar_status sonar_destroy(sonar_ctx_t ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto& s : ctx->scenes) free_scene(&s);
-    for (Scratch* s : {&ctx->rowmax, &ctx->noised, &ctx->rowinfo, &ctx->partials, &ctx->counters, &ctx->hits})
+    for (Scratch* s : {&ctx->rowmax, &ctx->noised, &ctx->rowinfo, &ctx->partials, &ctx->counters, &ctx->hits,
+                       &ctx->trig})
         if (s->p) cudaFreeAsync(s->p, 0);
     cudaDeviceSynchronize();
     cudaFree(ctx->d_err);
@@ -313,6 +314,7 @@ sonar_status single_forward(sonar_ctx* ctx, const SensorDev& S, const SceneDev& 
                             const float* d_theta, int32_t n_mat, sonar_hit* hits, float* noised, float* binned,
                             uint32_t* gmax, int block, cudaStream_t s) {
     if (p->normalise == 2) CU(cudaMemsetAsync(gmax, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
+    CU(launch_trig(nullptr, S, 1, S.nb + S.ne, s), "trig launch");
     TraceArgs t{};
     t.one = S;
     t.one_scene = sc;
@@ -397,6 +399,8 @@ extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const so
         CU(grow(ctx->hits, sizeof(sonar_hit) * (size_t)S.nb * S.ne, s), "scratch allocation");
         hits = (sonar_hit*)ctx->hits.p;
     }
+    CU(grow(ctx->trig, sizeof(float4) * (size_t)(S.nb + S.ne), s), "scratch allocation");
+    S.trig = (float4*)ctx->trig.p;
     sonar_status st2 = single_forward(ctx, S, scene_dev(ctx->scenes[scene_id]), params, d_theta, n_mat, hits, noised,
                                       out->binned, (uint32_t*)ctx->rowmax.p, t.block, s);
     if (st2 != SONAR_OK) return st2;
@@ -440,9 +444,14 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
     const Tune t = tune_for(ctx, *sensor);
-    const SensorDev S = make_sensor(*sensor, seed, frame, t, 0, 0);
+    SensorDev S = make_sensor(*sensor, seed, frame, t, 0, 0);
     const int groups = params->normalise == 1 ? S.nr : 1;
     CU(grow(ctx->rowinfo, sizeof(RowInfo) * groups, s), "scratch allocation");
+    if (!d_hits) {   // re-casting the rays needs the exact-ray tables
+        CU(grow(ctx->trig, sizeof(float4) * (size_t)(S.nb + S.ne), s), "scratch allocation");
+        S.trig = (float4*)ctx->trig.p;
+        CU(launch_trig(nullptr, S, 1, S.nb + S.ne, s), "trig launch");
+    }
     const int nq = n_mat + 2;
     const int64_t rays = (int64_t)S.nb * S.ne;
     const int chunk = adj_chunk(rays, ctx->sm_count, t.block);
@@ -495,6 +504,8 @@ struct sonar_batch {
     int32_t* d_fan_prefix = nullptr;
     int32_t* d_trace_prefix = nullptr;
     sonar_hit* d_hits = nullptr;      // hit records when the caller asks for none
+    float4* d_trig = nullptr;         // per-sensor exact-ray tables
+    int max_angles = 0;
     uint32_t* d_rowmax = nullptr;
     float* d_noised = nullptr;
     RowInfo* d_rowinfo = nullptr;
@@ -520,11 +531,13 @@ namespace {
 
 void batch_free_device(sonar_batch* b) {
     for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_adj_units, (void*)b->d_scenes,
-                    (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_hits, (void*)b->d_rowmax,
+                    (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_hits, (void*)b->d_trig,
+                    (void*)b->d_rowmax,
                     (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters})
         if (p) cudaFree(p);
     b->d_trace_prefix = nullptr;
     b->d_hits = nullptr;
+    b->d_trig = nullptr;
     b->n_mat_cap = 0;
     b->d_sens = nullptr; b->d_units = nullptr; b->d_adj_units = nullptr; b->d_scenes = nullptr;
     b->d_fan_prefix = nullptr;
@@ -635,6 +648,20 @@ sonar_status batch_plan(sonar_batch* b) {
     alloc((void**)&b->d_adj_units, sizeof(AdjUnit) * na);
     alloc((void**)&b->d_fan_prefix, sizeof(int32_t) * (n + 1));
     alloc((void**)&b->d_trace_prefix, sizeof(int32_t) * (n + 1));
+    int64_t angles = 0;
+    b->max_angles = 0;
+    for (const SensorDev& S : b->hs) {
+        angles += S.nb + S.ne;
+        b->max_angles = std::max(b->max_angles, S.nb + S.ne);
+    }
+    alloc((void**)&b->d_trig, sizeof(float4) * angles);
+    if (e == cudaSuccess) {
+        int64_t off = 0;
+        for (SensorDev& S : b->hs) {
+            S.trig = b->d_trig + off;
+            off += S.nb + S.ne;
+        }
+    }
     alloc((void**)&b->d_rowmax, sizeof(uint32_t) * rows);
     alloc((void**)&b->d_rowinfo, sizeof(RowInfo) * rows);
     alloc((void**)&b->d_counters, sizeof(int32_t) * 4);
@@ -677,6 +704,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
         CU(cudaMalloc(&b->d_hits, sizeof(sonar_hit) * std::max<int64_t>(1, b->total_rays)), "batch scratch");
     sonar_hit* hits = out->hits ? out->hits : b->d_hits;
     if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
+    CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
     TraceArgs t{};
     t.sensors = b->d_sens;
     t.scenes = b->d_scenes;
@@ -860,6 +888,7 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     sonar_ctx* ctx = b->ctx;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
     CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
+    if (!hits) CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
     if (p->normalise != 0)
         CU(launch_adj_rows(b->d_sens, SensorDev{}, (int)b->items.size(),
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
@@ -1131,7 +1160,11 @@ extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, con
     TraceCounters tc{cnt, cnt + 1, cnt + 2, nb, tb};
     Tune t;
     t.cols = 1;
-    const SensorDev S = make_sensor(*sensor, 0, 0, t, 0, 0);
+    SensorDev S = make_sensor(*sensor, 0, 0, t, 0, 0);
+    float4* trig = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&trig, sizeof(float4) * (S.nb + S.ne));
+    S.trig = trig;
+    if (e == cudaSuccess) e = launch_trig(nullptr, S, 1, S.nb + S.ne, s);
     if (e == cudaSuccess) e = launch_stats(S, scene_dev(sc), *params, tc, ctx->d_err, s);
     if (e == cudaSuccess) e = launch_popcount(nb, node_words, cnt + 3, s);
     if (e == cudaSuccess) e = launch_popcount(tb, tri_words, cnt + 4, s);
@@ -1141,6 +1174,7 @@ extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, con
     cudaFree(cnt);
     cudaFree(nb);
     cudaFree(tb);
+    cudaFree(trig);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "trace statistics");
     out[0] = (int64_t)h[0];
     out[1] = (int64_t)h[1];
@@ -1195,12 +1229,15 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     if (!out || !out->polar) return fail(ctx, SONAR_ERR_ARG, "outputs or outputs->polar is NULL");
     if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
     if (out->fan && (out->fan_w < 1 || out->fan_h < 1)) return fail(ctx, SONAR_ERR_ARG, "fan size must be >= 1");
-    // scratch layout (words): the image maximum at 0; from 64 the hit records
-    // (4 words a ray) unless the caller passes them; then, at a 256-byte
-    // boundary, the noised image unless the caller passes it
+    // scratch layout (words): the image maximum at 0; from 64 the exact-ray
+    // tables (4 words a beam and an elevation); then, each at a 256-byte
+    // boundary, the hit records (4 words a ray) and the noised image unless the
+    // caller passes them
     const int64_t npol = (int64_t)sensor->n_range_bins * sensor->n_az_bins;
+    const int64_t trig_words = 4 * ((int64_t)sensor->n_beams + sensor->n_elev);
+    const int64_t hits_at = 64 + (trig_words + 63) / 64 * 64;
     const int64_t hit_words = out->hits ? 0 : 4 * (int64_t)sensor->n_beams * sensor->n_elev;
-    const int64_t noised_at = 64 + (hit_words + 63) / 64 * 64;
+    const int64_t noised_at = hits_at + (hit_words + 63) / 64 * 64;
     const int64_t need = out->noised ? noised_at : noised_at + npol;
     if (need > (int64_t)SONAR_NOALLOC_SCRATCH_WORDS)
         return fail(ctx, SONAR_ERR_ARG, "sonar_render_noalloc: frame needs " + std::to_string(need) +
@@ -1212,10 +1249,11 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     void* base = nullptr;
     CU(noalloc_scratch(ctx->device, &base), "cudaGetSymbolAddress of the fixed scratch");
     uint32_t* rowmax = (uint32_t*)base;
-    sonar_hit* hits = out->hits ? out->hits : (sonar_hit*)((float*)base + 64);
+    sonar_hit* hits = out->hits ? out->hits : (sonar_hit*)((float*)base + hits_at);
     float* noised = out->noised ? out->noised : (float*)base + noised_at;
     const Tune t = single_tune(ctx, *sensor);
-    const SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
+    SensorDev S = make_sensor(*sensor, seed, frame, t, out->fan ? out->fan_w : 0, out->fan ? out->fan_h : 0);
+    S.trig = (float4*)((float*)base + 64);
     // single_forward clears the maximum (the array still holds the previous
     // call's values); hit records and the noised image are fully overwritten
     st = single_forward(ctx, S, scene_dev(ctx->scenes[scene_id]), params, d_theta, n_mat, hits, noised, out->binned,

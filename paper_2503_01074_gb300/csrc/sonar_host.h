@@ -32,6 +32,8 @@ inline SceneDev scene_dev(const SceneStore& s) {
 
 // Kernel launchers (render.cu).
 void set_kernel_attributes();
+cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_sensors, int max_angles,
+                        cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st);
 cudaError_t launch_bin(const BinArgs& a, int det, int grid, int block, size_t smem, cudaStream_t st);
 int bin_blocks_per_sm(int det, int block, size_t smem);

@@ -55,6 +55,7 @@ struct SensorDev {
     int32_t occ;         // trace: 8 = register budget for 8 blocks of 128 per SM, else none
     int32_t trace_blocks;  // trace: blocks of 4 warp tiles covering the sensor
     int64_t polar_off, hits_off, fan_off, rowmax_off;
+    float4* trig;        // float-float sin/cos of the beam azimuths [nb] and elevations [ne]
 };
 
 // A work unit: the azimuth columns [c0, c1) of one sensor, i.e. every ray
