@@ -249,14 +249,18 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
     const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
     int32_t stack[kStackMax];
     int sp = 0;
-    int32_t node = sc.root;
     int best = -1;
     uint32_t best_id = 0xFFFFFFFFu;
     float best_t = tlimit;
     uint64_t visits = 0, tests = 0, exact_n = 0;
-
+    // `node`: the internal node to visit next (or kEmpty); `leaf`: a leaf whose
+    // triangles wait to be tested (0 = none; leaf handles are negative).  Lanes
+    // that reach a leaf park it and keep descending until every active lane of
+    // the warp holds one, so that the triangle tests run together.
+    int32_t node = sc.root, leaf = 0;
+    if (node < 0) { leaf = node; node = kEmpty; }
     for (;;) {
-        if (node >= 0) {
+        while (node >= 0) {
             const float4* p = sc.nodes + 8 * (int64_t)node;
             const float4 lx = __ldg(p), hx = __ldg(p + 1), ly = __ldg(p + 2), hy = __ldg(p + 3);
             const float4 lz = __ldg(p + 4), hz = __ldg(p + 5);
@@ -266,12 +270,14 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
                 atomicOr(tc->node_bits + (node >> 5), 1u << (node & 31));
             }
             const float tcut = best_t * 1.00002f;
-            float tn[4];
-            int32_t hn[4];
             const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
             const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
             const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
             const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
+            // sort key per child: entry distance bits (>= 0, so integer order is
+            // distance order) with the child slot in the two low bits; a missed
+            // child sorts last as 0xFFFFFFFF
+            uint32_t key[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
@@ -281,75 +287,90 @@ __device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int
                 t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
                 lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
                 const bool hit = hs[c] != kEmpty && lo <= hi * 1.0000005f;
-                tn[c] = hit ? lo : CUDART_INF_F;
-                hn[c] = hs[c];
+                key[c] = hit ? ((__float_as_uint(lo) & ~3u) | (uint32_t)c) : 0xFFFFFFFFu;
             }
-            // nearest first: a 4-input sorting network on (entry distance, handle)
-#define SONAR_CSWAP(a, b)                                                    \
-            if (tn[b] < tn[a]) {                                             \
-                const float tt = tn[a]; tn[a] = tn[b]; tn[b] = tt;           \
-                const int32_t hh = hn[a]; hn[a] = hn[b]; hn[b] = hh;         \
+#define SONAR_USORT(a, b)                                  \
+            {                                              \
+                const uint32_t mn = min(key[a], key[b]);   \
+                key[b] = max(key[a], key[b]);              \
+                key[a] = mn;                               \
             }
-            SONAR_CSWAP(0, 1) SONAR_CSWAP(2, 3) SONAR_CSWAP(0, 2) SONAR_CSWAP(1, 3) SONAR_CSWAP(1, 2)
-#undef SONAR_CSWAP
-            const int nhit = (tn[0] < CUDART_INF_F) + (tn[1] < CUDART_INF_F) + (tn[2] < CUDART_INF_F) +
-                             (tn[3] < CUDART_INF_F);
+            SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
+#undef SONAR_USORT
+            const int nhit = (key[0] != 0xFFFFFFFFu) + (key[1] != 0xFFFFFFFFu) + (key[2] != 0xFFFFFFFFu) +
+                             (key[3] != 0xFFFFFFFFu);
             if (nhit == 0) {
-                if (sp == 0) break;
-                node = stack[--sp];
-                continue;
-            }
-            if (sp + nhit - 1 > kStackMax) {
-                atomicOr(err, SONAR_DEVERR_STACK);
-                best = -1;
-                break;
-            }
-            for (int c = nhit - 1; c >= 1; --c) stack[sp++] = hn[c];
-            node = hn[0];
-            continue;
-        }
-        // leaf: a run of triangles in leaf order
-        const int32_t x = ~node;
-        const int32_t first = x >> 3, count = (x & 7) + 1;
-        for (int k = 0; k < count; ++k) {
-            const int32_t f = first + k;
-            if (f >= sc.n_tris) {
-                atomicOr(err, SONAR_DEVERR_INDEX);
-                break;
-            }
-            const float4* tp = sc.tris + 3 * (int64_t)f;
-            const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-            if (STATS) {
-                ++tests;
-                atomicOr(tc->tri_bits + (f >> 5), 1u << (f & 31));
-            }
-            float t;
-            const int r = mt32(o, d, a, b, c, t);
-            if (r == 0) continue;
-            if (r == 2) {
-                if (STATS) ++exact_n;
-                if (!exact_hit(s, ri, rj, a, b, c, &t)) continue;
-            }
-            if (!(t < tlimit)) continue;
-            const uint32_t id = __float_as_uint(b.w);
-            bool take;
-            if (best < 0) {
-                take = true;
-            } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
-                // near tie: decide on the exact distances, then on the caller's index
-                if (STATS) ++exact_n;
-                take = exact_closer(s, ri, rj, tp, id, sc.tris + 3 * (int64_t)best, best_id);
+                node = sp > 0 ? stack[--sp] : kEmpty;
             } else {
-                take = t < best_t;
+                if (sp + nhit - 1 > kStackMax) {
+                    atomicOr(err, SONAR_DEVERR_STACK);
+                    t_out = best_t;
+                    return -1;
+                }
+#pragma unroll
+                for (int c = 3; c >= 1; --c) {
+                    if (c < nhit) {
+                        const uint32_t k = key[c] & 3u;
+                        stack[sp++] = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
+                    }
+                }
+                const uint32_t k = key[0] & 3u;
+                node = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
             }
-            if (take) {
-                best = f;
-                best_id = id;
-                best_t = t;
+            if (node < 0 && node != kEmpty && leaf == 0) {   // park the leaf, keep descending
+                leaf = node;
+                node = sp > 0 ? stack[--sp] : kEmpty;
+            }
+            if (!__any_sync(__activemask(), leaf == 0)) break;
+        }
+        while (leaf != 0) {
+            // a run of triangles in leaf order
+            const int32_t x = ~leaf;
+            const int32_t first = x >> 3, count = (x & 7) + 1;
+            for (int k = 0; k < count; ++k) {
+                const int32_t f = first + k;
+                if (f >= sc.n_tris) {
+                    atomicOr(err, SONAR_DEVERR_INDEX);
+                    break;
+                }
+                const float4* tp = sc.tris + 3 * (int64_t)f;
+                const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+                if (STATS) {
+                    ++tests;
+                    atomicOr(tc->tri_bits + (f >> 5), 1u << (f & 31));
+                }
+                float t;
+                const int r = mt32(o, d, a, b, c, t);
+                if (r == 0) continue;
+                if (r == 2) {
+                    if (STATS) ++exact_n;
+                    if (!exact_hit(s, ri, rj, a, b, c, &t)) continue;
+                }
+                if (!(t < tlimit)) continue;
+                const uint32_t id = __float_as_uint(b.w);
+                bool take;
+                if (best < 0) {
+                    take = true;
+                } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
+                    // near tie: decide on the exact distances, then on the caller's index
+                    if (STATS) ++exact_n;
+                    take = exact_closer(s, ri, rj, tp, id, sc.tris + 3 * (int64_t)best, best_id);
+                } else {
+                    take = t < best_t;
+                }
+                if (take) {
+                    best = f;
+                    best_id = id;
+                    best_t = t;
+                }
+            }
+            leaf = 0;
+            if (node < 0 && node != kEmpty) {   // the next stacked entry is a leaf too
+                leaf = node;
+                node = sp > 0 ? stack[--sp] : kEmpty;
             }
         }
-        if (sp == 0) break;
-        node = stack[--sp];
+        if (node == kEmpty) break;
     }
     if (STATS) {
         atomicAdd(tc->visits, (unsigned long long)visits);
