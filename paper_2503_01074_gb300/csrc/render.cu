@@ -449,22 +449,16 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceArgs a) {
     __shared__ SceneDev SC;
     __shared__ int s_tile;
     if (threadIdx.x == 0) {
-        int si = 0, tile = blockIdx.x;
         if (a.sensors) {
-            int lo = 0, hi = a.n_sensors - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.tile_prefix[mid] <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
-            }
-            si = lo;
-            tile = blockIdx.x - a.tile_prefix[si];
-            S = a.sensors[si];
+            const int2 m = a.block_map[blockIdx.x];
+            S = a.sensors[m.x];
             SC = a.scenes[S.scene];
+            s_tile = m.y;
         } else {
             S = a.one;
             SC = a.one_scene;
+            s_tile = blockIdx.x;
         }
-        s_tile = tile;
     }
     __syncthreads();
     const int tb = S.tb, te = 32 / S.tb;
@@ -516,8 +510,9 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
     __shared__ Unit U;
-    __shared__ int s_unit;
+    __shared__ int s_unit, s_count;
     __shared__ float s_red[32];
+    __shared__ float s_pat[kMaxCols];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
@@ -579,28 +574,59 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
             }
         }
         __syncthreads();
-        // Eq. 3-6 per bin; (row, col) advance incrementally: no division and no
-        // integer-to-float conversion instruction in this loop
+        // Eq. 3-6 per bin.  Pass 1 visits every bin: Philox words, the additive
+        // Rayleigh term, and the final value of bins without returns (P = 0 makes
+        // the multiplicative term exactly 0); bins with returns are listed.  Pass 2
+        // finishes the listed bins with the Gaussian multiplicative term.  (row,
+        // col) advance incrementally: no division and no integer-to-float
+        // conversion instruction in pass 1.
         const float dr = (S.rmax - S.rmin) / (float)S.nr, da = S.hfov / (float)S.naz;
         const float inv_rmax2 = 1.0f / (S.rmax * S.rmax);
         const float inv_sphi = 1.0f / a.params.sigma_phi;
+        const float sig_sa = a.params.sigma_sa, sig_sm = a.params.sigma_sm;
+        int* list = reinterpret_cast<int*>(acc + nbin);
+        for (int c = tid; c < cw; c += nt) {
+            const float pc = fmaf(small_u2f(U.c0 + c) + 0.5f, da, -0.5f * S.hfov);
+            s_pat[c] = 0.5f * expf(-pc * pc * inv_sphi);
+        }
+        if (tid == 0) s_count = 0;
+        __syncthreads();
         const int drow = nt / cw, dcol = nt - drow * cw;
         int row = tid / cw, col = tid - row * cw;
         for (int k = tid; k < nbin; k += nt) {
             const uint32_t b = (uint32_t)(row * S.naz + U.c0 + col);
             const float P = acc[k];
-            float w_sa, w_sm;
-            bin_noise(b, S, a.params.sigma_sa, a.params.sigma_sm, w_sa, w_sm);
+            const U4 x = philox10(U4{b, S.frame_lo, 0u, S.frame_hi}, S.seed_lo, S.seed_hi);
+            const float w_sa = sig_sa * sqrtf(neg2log_u(x.x));
             const float rc = fmaf(small_u2f(row) + 0.5f, dr, S.rmin);
-            const float pc = fmaf(small_u2f(U.c0 + col) + 0.5f, da, -0.5f * S.hfov);
-            const float additive = rc * rc * inv_rmax2 * (1.0f + 0.5f * expf(-pc * pc * inv_sphi) * w_sa);
-            const float In = P * (0.5f + w_sm) + additive;
-            a.noised[S.polar_off + b] = In;
+            const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
             if (a.binned) a.binned[S.polar_off + b] = P;
-            acc[k] = In;
+            if (P != 0.0f) {
+                list[atomicAdd(&s_count, 1)] = k;
+            } else {
+                a.noised[S.polar_off + b] = additive;
+                acc[k] = additive;
+            }
             row += drow;
             col += dcol;
             if (col >= cw) { col -= cw; ++row; }
+        }
+        __syncthreads();
+        const int nlist = s_count;
+        for (int q = tid; q < nlist; q += nt) {
+            const int k = list[q];
+            const int rw = k / cw, cl = k - rw * cw;
+            const uint32_t b = (uint32_t)(rw * S.naz + U.c0 + cl);
+            const float P = acc[k];
+            const U4 x = philox10(U4{b, S.frame_lo, 0u, S.frame_hi}, S.seed_lo, S.seed_hi);
+            const float w_sa = sig_sa * sqrtf(neg2log_u(x.x));
+            const float rc = fmaf(small_u2f(rw) + 0.5f, dr, S.rmin);
+            const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[cl] * w_sa);
+            const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);
+            const float w_sm = sig_sm * sqrtf(neg2log_u(x.y)) * cospif(2.0f * u2);
+            const float In = P * (0.5f + w_sm) + additive;
+            a.noised[S.polar_off + b] = In;
+            acc[k] = In;
         }
         __syncthreads();
         if (a.params.normalise == 2) {
@@ -628,21 +654,11 @@ __device__ __forceinline__ float norm_value(float In, float m, int mode) {
     return (mode != 0 && m > 0.0f) ? In / m : In;
 }
 
-// Sensor whose rows [rowmax_off, rowmax_off + nr) contain row g.
-__device__ __forceinline__ int sensor_of_row(const SensorDev* sensors, int n, int64_t g) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sensors[mid].rowmax_off <= g) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (g >= a.total_rows) return;
-    const SensorDev& s = a.sensors ? a.sensors[sensor_of_row(a.sensors, a.n_sensors, g)] : a.one;
+    const SensorDev& s = a.sensors ? a.sensors[a.row_map[g]] : a.one;
     const int row = (int)(g - s.rowmax_off);
     const int naz = s.naz;
     const float* In = a.noised + s.polar_off + (int64_t)row * naz;
@@ -666,8 +682,9 @@ __global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
 template <class F>
 __device__ __forceinline__ float fan_pixel(const SensorDev& s, int64_t pix, F val) {
     const int v = (int)(pix / s.fan_w), u = (int)(pix - (int64_t)v * s.fan_w);
-    const float x = ((float)u + 0.5f - 0.5f * (float)s.fan_w) / s.fan_scale;
-    const float y = ((float)s.fan_h - (float)v - 0.5f) / s.fan_scale;
+    const float inv_scale = 1.0f / s.fan_scale;
+    const float x = ((float)u + 0.5f - 0.5f * (float)s.fan_w) * inv_scale;
+    const float y = ((float)s.fan_h - (float)v - 0.5f) * inv_scale;
     const float r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
     const float phi = atan2f(x, y);
     if (r < s.rmin || r > s.rmax || fabsf(phi) > 0.5f * s.hfov) return 0.0f;
@@ -688,16 +705,10 @@ __global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
     __shared__ SensorDev S;
     __shared__ int64_t s_base;
     if (threadIdx.x == 0) {
-        int si = 0;
-        if (a.block_prefix) {
-            int lo = 0, hi = a.n_sensors - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.block_prefix[mid] <= (int32_t)blockIdx.x) lo = mid; else hi = mid - 1;
-            }
-            si = lo;
-            S = a.sensors[si];
-            s_base = (int64_t)(blockIdx.x - a.block_prefix[si]) * kFanTile;
+        if (a.block_map) {
+            const int2 m = a.block_map[blockIdx.x];
+            S = a.sensors[m.x];
+            s_base = (int64_t)m.y * kFanTile;
         } else {
             S = a.one;
             s_base = (int64_t)blockIdx.x * kFanTile;
@@ -722,8 +733,8 @@ __global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
 // Group terms of the normalisation Jacobian: m, argmax (lowest index on
 // ties) and c = sum G I~ / m^2.  Mode 1: one warp per range row; mode 2: one
 // block per sensor image.
-__global__ void k_adj_rows(const SensorDev* sensors, SensorDev one, int n_sensors, int64_t total,
-                           int mode, const float* noised, const float* grad, RowInfo* info) {
+__global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, SensorDev one, int n_sensors,
+                           int64_t total, int mode, const float* noised, const float* grad, RowInfo* info) {
     const int lane = threadIdx.x & 31;
     __shared__ float s_m[32];
     __shared__ int s_a[32];
@@ -731,7 +742,7 @@ __global__ void k_adj_rows(const SensorDev* sensors, SensorDev one, int n_sensor
     if (mode == 1) {
         const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (g >= total) return;
-        const SensorDev& s = sensors ? sensors[sensor_of_row(sensors, n_sensors, g)] : one;
+        const SensorDev& s = sensors ? sensors[row_map[g]] : one;
         const int row = (int)(g - s.rowmax_off);
         const float* In = noised + s.polar_off + (int64_t)row * s.naz;
         const float* G = grad + s.polar_off + (int64_t)row * s.naz;
@@ -1008,16 +1019,16 @@ cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_rows(const SensorDev* sensors, const SensorDev& one, int n_sensors,
+cudaError_t launch_adj_rows(const SensorDev* sensors, const int32_t* row_map, const SensorDev& one, int n_sensors,
                             int64_t total_groups, int normalise, const float* noised,
                             const float* grad, RowInfo* info, cudaStream_t st) {
     if (normalise == 1) {
         const int64_t threads = total_groups * 32;
-        k_adj_rows<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sensors, one, n_sensors, total_groups,
-                                                                      1, noised, grad, info);
+        k_adj_rows<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sensors, row_map, one, n_sensors,
+                                                                      total_groups, 1, noised, grad, info);
     } else if (normalise == 2) {
-        k_adj_rows<<<(unsigned)total_groups, 1024, 0, st>>>(sensors, one, n_sensors, total_groups, 2, noised,
-                                                            grad, info);
+        k_adj_rows<<<(unsigned)total_groups, 1024, 0, st>>>(sensors, row_map, one, n_sensors, total_groups, 2,
+                                                            noised, grad, info);
     }
     return cudaGetLastError();
 }

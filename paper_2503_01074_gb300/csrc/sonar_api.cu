@@ -138,7 +138,7 @@ Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
     const int bpc = std::max(1, s.n_beams / std::max(1, s.n_az_bins));
     if (t.cols <= 0) t.cols = std::max(1, t.block / std::max(1, s.n_elev * bpc));
     const int max_cols_smem = std::max(1, (int)(kMaxDynSmem / 4 / 2) / s.n_range_bins);
-    t.cols = std::max(1, std::min({t.cols, s.n_az_bins, max_cols_smem}));
+    t.cols = std::max(1, std::min({t.cols, s.n_az_bins, max_cols_smem, kMaxCols}));
     if (t.block < 32 || t.block > 512 || (t.block & 31)) t.block = 128;
     if (t.tb <= 0) t.tb = 8;
     if (t.tb > 32 || (t.tb & (t.tb - 1))) t.tb = 8;
@@ -307,7 +307,23 @@ extern "C" sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t id, int64_t ou
 
 namespace {
 
-size_t bin_smem(const SensorDev& s) { return (size_t)s.nr * s.cols * sizeof(float); }
+// Most rays a binning unit of this sensor covers: its columns' beams x elevations.
+int64_t unit_rays_max(const SensorDev& s) {
+    int64_t most = 0;
+    for (int t = 0; t < s.n_tiles; ++t) {
+        const int64_t c0 = (int64_t)t * s.cols, c1 = std::min<int64_t>(c0 + s.cols, s.naz);
+        most = std::max<int64_t>(most, (first_beam_of_col(c1, s.nb, s.naz) - first_beam_of_col(c0, s.nb, s.naz)) *
+                                           (int64_t)s.ne);
+    }
+    return most;
+}
+
+// Shared memory of a binning block: the column block of the unit plus the
+// list of its non-empty bins (no more entries than rays, nor than bins).
+size_t bin_smem(const SensorDev& s) {
+    const int64_t bins = (int64_t)s.nr * s.cols;
+    return (size_t)(bins + std::min<int64_t>(unit_rays_max(s), bins)) * sizeof(float);
+}
 
 // Trace, bin and noise of one sensor (polar_off = hits_off = rowmax_off = 0).
 sonar_status single_forward(sonar_ctx* ctx, const SensorDev& S, const SceneDev& sc, const sonar_params* p,
@@ -458,7 +474,7 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     const int n_units = (int)((rays + chunk - 1) / chunk);
     CU(grow(ctx->partials, sizeof(double) * (size_t)n_units * nq, s), "scratch allocation");
     if (params->normalise != 0)
-        CU(launch_adj_rows(nullptr, S, 1, groups, params->normalise, d_noised, d_grad_polar,
+        CU(launch_adj_rows(nullptr, nullptr, S, 1, groups, params->normalise, d_noised, d_grad_polar,
                            (RowInfo*)ctx->rowinfo.p, s),
            "adjoint row launch");
     AdjArgs a{};
@@ -503,6 +519,9 @@ struct sonar_batch {
     SceneDev* d_scenes = nullptr;
     int32_t* d_fan_prefix = nullptr;
     int32_t* d_trace_prefix = nullptr;
+    int2* d_trace_map = nullptr;      // per trace block: (sensor, tile)
+    int2* d_fan_map = nullptr;        // per fan block: (sensor, block)
+    int32_t* d_row_map = nullptr;     // per range row: sensor
     sonar_hit* d_hits = nullptr;      // hit records when the caller asks for none
     float4* d_trig = nullptr;         // per-sensor exact-ray tables
     int max_angles = 0;
@@ -531,11 +550,15 @@ namespace {
 
 void batch_free_device(sonar_batch* b) {
     for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_adj_units, (void*)b->d_scenes,
-                    (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_hits, (void*)b->d_trig,
+                    (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_trace_map,
+                    (void*)b->d_fan_map, (void*)b->d_row_map, (void*)b->d_hits, (void*)b->d_trig,
                     (void*)b->d_rowmax,
                     (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters})
         if (p) cudaFree(p);
     b->d_trace_prefix = nullptr;
+    b->d_trace_map = nullptr;
+    b->d_fan_map = nullptr;
+    b->d_row_map = nullptr;
     b->d_hits = nullptr;
     b->d_trig = nullptr;
     b->n_mat_cap = 0;
@@ -610,7 +633,7 @@ sonar_status batch_plan(sonar_batch* b) {
             u.rays = (int32_t)((i1 - i0) * S.ne);
             b->units.push_back(u);
         }
-        b->smem1 = std::max(b->smem1, (size_t)S.nr * S.cols * sizeof(float));
+        b->smem1 = std::max(b->smem1, bin_smem(S));
     }
     // largest units first: the persistent blocks then finish close together
     std::stable_sort(b->units.begin(), b->units.end(), [&](const Unit& x, const Unit& y) {
@@ -648,6 +671,16 @@ sonar_status batch_plan(sonar_batch* b) {
     alloc((void**)&b->d_adj_units, sizeof(AdjUnit) * na);
     alloc((void**)&b->d_fan_prefix, sizeof(int32_t) * (n + 1));
     alloc((void**)&b->d_trace_prefix, sizeof(int32_t) * (n + 1));
+    std::vector<int2> tmap, fmap;
+    std::vector<int32_t> rmap;
+    for (int k = 0; k < n; ++k) {
+        for (int t = 0; t < b->hs[k].trace_blocks; ++t) tmap.push_back(make_int2(k, t));
+        for (int t = 0; t < b->fan_prefix[k + 1] - b->fan_prefix[k]; ++t) fmap.push_back(make_int2(k, t));
+        for (int r = 0; r < b->hs[k].nr; ++r) rmap.push_back(k);
+    }
+    alloc((void**)&b->d_trace_map, sizeof(int2) * tmap.size());
+    alloc((void**)&b->d_fan_map, sizeof(int2) * std::max<size_t>(1, fmap.size()));
+    alloc((void**)&b->d_row_map, sizeof(int32_t) * rmap.size());
     int64_t angles = 0;
     b->max_angles = 0;
     for (const SensorDev& S : b->hs) {
@@ -677,6 +710,12 @@ sonar_status batch_plan(sonar_batch* b) {
         e = cudaMemcpy(b->d_fan_prefix, b->fan_prefix.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_trace_prefix, b->trace_prefix.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_trace_map, tmap.data(), sizeof(int2) * tmap.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !fmap.empty())
+        e = cudaMemcpy(b->d_fan_map, fmap.data(), sizeof(int2) * fmap.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_row_map, rmap.data(), sizeof(int32_t) * rmap.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
     return SONAR_OK;
 }
@@ -708,7 +747,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     TraceArgs t{};
     t.sensors = b->d_sens;
     t.scenes = b->d_scenes;
-    t.tile_prefix = b->d_trace_prefix;
+    t.block_map = b->d_trace_map;
     t.n_sensors = (int32_t)b->items.size();
     t.params = *p;
     t.hits = hits;
@@ -733,6 +772,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     if (events) CU(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal), "cudaEventRecord");
     NormArgs c{};
     c.sensors = b->d_sens;
+    c.row_map = b->d_row_map;
     c.n_sensors = (int32_t)b->items.size();
     c.total_rows = b->total_rows;
     c.noised = a.noised;
@@ -743,7 +783,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     if (out->fan) {
         FanArgs f{};
         f.sensors = b->d_sens;
-        f.block_prefix = b->d_fan_prefix;
+        f.block_map = b->d_fan_map;
         f.n_sensors = (int32_t)b->items.size();
         f.polar = out->polar;
         f.fan = out->fan;
@@ -890,7 +930,7 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
     if (!hits) CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
     if (p->normalise != 0)
-        CU(launch_adj_rows(b->d_sens, SensorDev{}, (int)b->items.size(),
+        CU(launch_adj_rows(b->d_sens, b->d_row_map, SensorDev{}, (int)b->items.size(),
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
                            grad, b->d_rowinfo, s),
            "batch adjoint rows");

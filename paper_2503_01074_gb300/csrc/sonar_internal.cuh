@@ -23,6 +23,7 @@ constexpr int kLeafMax = 4;          // triangles per collapsed leaf
 constexpr int kStackMax = 96;        // traversal stack entries (tree height is checked at build)
 constexpr int32_t kEmpty = (int32_t)0x80000000;
 constexpr int kMaxMat = 1024;
+constexpr int kMaxCols = 64;         // azimuth columns per binning unit, at most
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 
 __host__ __device__ inline int32_t leaf_handle(int32_t first, int32_t count) {
@@ -95,9 +96,9 @@ struct U4 { uint32_t x, y, z, w; };
 __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        // one 32x32 -> 64-bit product gives both halves
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0};
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -144,7 +145,7 @@ struct TraceCounters {
 struct TraceArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
     const SceneDev* scenes;     // batch: device table; single: nullptr (use `one_scene`)
-    const int32_t* tile_prefix; // batch: [n_sensors + 1] trace-block prefix
+    const int2* block_map;      // batch: per block (sensor, tile of that sensor)
     int32_t n_sensors;
     SensorDev one;
     SceneDev one_scene;
@@ -175,6 +176,7 @@ struct BinArgs {
 // Normalisation: one warp per (sensor, range row).
 struct NormArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
+    const int32_t* row_map;     // batch: sensor of each row
     int32_t n_sensors;
     int64_t total_rows;         // sum of n_range_bins over the sensors
     SensorDev one;
@@ -184,12 +186,12 @@ struct NormArgs {
     float* polar;
 };
 
-constexpr int kFanTile = 1024;  // fan pixels per block
+constexpr int kFanTile = 4096;  // fan pixels per block
 
 // Fan resample: blocks of kFanTile pixels of one sensor, reading the normalised image.
 struct FanArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr
-    const int32_t* block_prefix;  // batch: [n_sensors + 1] fan-block prefix; single: nullptr
+    const int2* block_map;      // batch: per block (sensor, block of that sensor); single: nullptr
     int32_t n_sensors;
     SensorDev one;
     const float* polar;
