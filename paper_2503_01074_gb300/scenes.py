@@ -28,7 +28,7 @@ __all__ = [
     "Mesh", "SensorSpec", "quad", "icosphere", "heightfield", "cylinder", "box",
     "merge", "pose_matrix", "tiny_scene", "single_frame_scene", "random_soup",
     "sensor_tiny", "sensor_single", "trajectory", "batched_workload",
-    "large_scene", "materials_uniform",
+    "large_scene", "materials_uniform", "height_function",
 ]
 
 
@@ -162,6 +162,14 @@ def _value_noise_fbm(x, y, extent, seed, octaves=6, lacunarity=2.0, persistence=
     return total / norm
 
 
+def height_function(extent: float, amplitude: float, seed: int, z0: float = 0.0):
+    """The seabed surface z0 + amplitude * fBm(x, y) of a heightfield scene,
+    evaluable at arbitrary points without building the mesh."""
+    def height_fn(x, y):
+        return z0 + amplitude * _value_noise_fbm(x, y, extent, seed)
+    return height_fn
+
+
 def heightfield(n_cells: int, extent: float, amplitude: float, seed: int,
                 patches: int = 4, mat_base: int = 0, z0: float = 0.0):
     """Regular n x n cell grid over [-extent/2, extent/2]^2 with heights
@@ -174,10 +182,7 @@ def heightfield(n_cells: int, extent: float, amplitude: float, seed: int,
     n = int(n_cells)
     xs = (np.arange(n + 1, dtype=np.float64) / n - 0.5) * extent
     X, Y = np.meshgrid(xs, xs, indexing="ij")          # vertex (i, j) at X[i,j], Y[i,j]
-
-    def height_fn(x, y):
-        return z0 + amplitude * _value_noise_fbm(x, y, extent, seed)
-
+    height_fn = height_function(extent, amplitude, seed, z0)
     Z = height_fn(X, Y)
     verts = np.stack([X, Y, Z], axis=-1).reshape(-1, 3).astype(np.float32)
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
