@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the single-frame and e2e legs")
     p.add_argument("--small", action="store_true", help="a small case for profiler captures")
+    p.add_argument("--configs", action="store_true",
+                   help="also measure the heterogeneous-batch, large and dense-ray configurations")
     return p.parse_args()
 
 
@@ -191,6 +193,95 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+def timed(fn, steps, stream):
+    """Mean device milliseconds of fn() over `steps` runs (after one warm-up)."""
+    import torch
+    fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms))
+
+
+def measure_configs(son, steps):
+    """Throughput of the other workload configurations (not the headline line)."""
+    import torch
+    from paper_2503_01074_gb300 import scenes as S
+    from paper_2503_01074_gb300.sonar import RenderParams
+    stream = torch.cuda.current_stream()
+    prm = RenderParams()
+    out = {}
+    # heterogeneous batch: 4 scenes, 128 sensors of three shapes, vs 128 single renders
+    scenes, mu, sensors = S.batched_workload()
+    sids = [son.upload_mesh(m) for m, _ in scenes]
+    items = [(sids[si], spec, 500 + k, k) for k, (si, spec) in enumerate(sensors)]
+    theta = son.theta(ALPHA, GAIN, mu)
+    b = son.batch(items)
+    b.autotune(theta, prm)
+    rays = sum(spec.n_rays for _, spec in sensors)
+    ms_b = timed(lambda: b.render(theta, prm, hits=True, fan=True), steps, stream)
+    outs = [son.render(sid, spec, theta, prm, seed, fr, hits=True, fan=True) for sid, spec, seed, fr in items]
+
+    def singles():
+        for (sid, spec, seed, fr), o in zip(items, outs):
+            son.render(sid, spec, theta, prm, seed, fr, hits=True, fan=True, outputs=o)
+    ms_s = timed(singles, max(2, steps // 2), stream)
+    out["heterogeneous_batch"] = {"sensors": len(items), "rays": rays, "batched_fwd_fps": len(items) / ms_b * 1e3,
+                                  "single_fwd_fps": len(items) / ms_s * 1e3,
+                                  "batched_Mrays_s": rays / ms_b / 1e3, "speedup": ms_s / ms_b}
+    b.close()
+    del outs
+    for sid in sids:
+        son.release(sid)
+    # large: 33.6M triangles, 1024 x 256 rays, 4000 bins, 0.1-60 m; forward + adjoint, hits recomputed
+    t0 = time.perf_counter()
+    mesh, mu, hfn = S.large_scene()
+    gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sid = son.upload_mesh(mesh)
+    torch.cuda.synchronize()
+    build_ms = 1000.0 * (time.perf_counter() - t0)
+    base = S.sensor_single(hfn, n_beams=1024, n_elev=256, n_range_bins=4000, r_min=0.1, r_max=60.0,
+                           fan_w=0, fan_h=0)
+    poses = S.trajectory(base, hfn, 256, radius=60.0, seed=7)
+    theta = son.theta(ALPHA, GAIN, mu)
+    b = son.batch([(sid, p, 900 + k, k) for k, p in enumerate(poses)])
+    b.autotune(theta, prm)
+    G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(2)).to(son.device) * 1e-3
+    d = torch.empty_like(theta)
+
+    def fwd_adj():
+        b.render(theta, prm, hits=False, fan=False)
+        b.backward(theta, prm, G, hits=False, out=d)
+    ms = timed(fwd_adj, max(2, steps // 2), stream)
+    out["large"] = {"tris": mesh.n_tris, "frames": len(poses), "rays_per_frame": base.n_rays,
+                    "fwd_adj_recompute_fps": len(poses) / ms * 1e3,
+                    "Mrays_s": len(poses) * base.n_rays / ms / 1e3, "scene_build_ms": build_ms,
+                    "scene_generation_s": gen_s, "phase_ms": b.timings()}
+    b.close()
+    son.release(sid)
+    del mesh
+    # dense rays: 3000 x 460 rays into 350 x 220 bins
+    mesh, mu, hfn = S.single_frame_scene()
+    sid = son.upload_mesh(mesh)
+    spec = S.sensor_single(hfn, n_beams=3000, n_elev=460, n_range_bins=350, n_az_bins=220, fan_w=440, fan_h=248)
+    theta = son.theta(ALPHA, GAIN, mu)
+    b = son.batch([(sid, spec, 3, 3)])
+    b.autotune(theta, prm)
+    ms = timed(lambda: b.render(theta, prm, hits=True, fan=True), steps, stream)
+    out["dense_rays"] = {"rays_per_frame": spec.n_rays, "bins": 350 * 220, "fwd_fps": 1e3 / ms,
+                         "Mrays_s": spec.n_rays / ms / 1e3, "phase_ms": b.timings()}
+    b.close()
+    son.release(sid)
+    return out
+
 
 def traffic_from_profile():
     """Per-frame DRAM bytes of the trace/bin/noise kernel from the committed ncu
@@ -377,6 +468,8 @@ def run_ours(args):
     extras["tri_tests_per_ray"] = tests / (B * base.n_rays)
     extras["fp64_tests_per_ray"] = exact / (B * base.n_rays)
 
+    configs = measure_configs(son, args.steps) if (args.configs and rank == 0) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mesh, mu, poses[0], min(args.cpu_rays, base.n_rays))
@@ -395,6 +488,8 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 7 * args.steps}
         line.update({k: float(v) for k, v in extras.items()})
+        if configs is not None:
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
     batch.close()
     son.close()

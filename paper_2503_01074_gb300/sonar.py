@@ -238,13 +238,16 @@ class Sonar:
         t = self.torch
         nr, naz = spec.n_range_bins, spec.n_az_bins
         o = outputs or {}
-        polar = o.get("polar", t.empty((nr, naz), dtype=t.float32, device=self.device))
-        noised = o.get("noised", t.empty((nr, naz), dtype=t.float32, device=self.device))
-        P = o.get("binned", t.empty((nr, naz), dtype=t.float32, device=self.device)) if binned else None
-        H = o.get("hits", t.empty((spec.n_beams * spec.n_elev, 4), dtype=t.int32, device=self.device)) \
-            if hits else None
+
+        def buf(name, shape, dtype=t.float32):
+            return o[name] if name in o else t.empty(shape, dtype=dtype, device=self.device)
+
+        polar = buf("polar", (nr, naz))
+        noised = buf("noised", (nr, naz))
+        P = buf("binned", (nr, naz)) if binned else None
+        H = buf("hits", (spec.n_beams * spec.n_elev, 4), t.int32) if hits else None
         fw, fh = (spec.fan_w, spec.fan_h) if fan and spec.fan_w > 0 else (0, 0)
-        F = o.get("fan", t.empty((fh, fw), dtype=t.float32, device=self.device)) if fw else None
+        F = buf("fan", (fh, fw)) if fw else None
         out = Outputs(polar.data_ptr(), noised.data_ptr(), P.data_ptr() if P is not None else None,
                       H.data_ptr() if H is not None else None, F.data_ptr() if F is not None else None,
                       fw, fh)
