@@ -720,6 +720,17 @@ sonar_status batch_plan(sonar_batch* b) {
     return SONAR_OK;
 }
 
+// Scratch for outputs the caller does not want (noised image, hit records),
+// allocated before any capture: an allocation inside stream capture fails.
+cudaError_t batch_scratch(sonar_batch* b, const sonar_batch_outputs* out) {
+    cudaError_t e = cudaSuccess;
+    if (!out->noised && !b->d_noised)
+        e = cudaMalloc(&b->d_noised, sizeof(float) * std::max<int64_t>(1, b->total_polar));
+    if (e == cudaSuccess && !out->hits && !b->d_hits)
+        e = cudaMalloc(&b->d_hits, sizeof(sonar_hit) * std::max<int64_t>(1, b->total_rays));
+    return e;
+}
+
 int persistent_grid(const sonar_batch* b, int det) {
     const int per_sm = bin_blocks_per_sm(det, b->block, b->smem1);
     const int64_t g = std::min<int64_t>((int64_t)b->units.size(), (int64_t)b->ctx->sm_count * per_sm);
@@ -739,9 +750,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
     if (p->normalise == 2)
         CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
-    if (!out->hits && !b->d_hits)
-        CU(cudaMalloc(&b->d_hits, sizeof(sonar_hit) * std::max<int64_t>(1, b->total_rays)), "batch scratch");
-    sonar_hit* hits = out->hits ? out->hits : b->d_hits;
+    sonar_hit* hits = out->hits ? out->hits : b->d_hits;   // scratch allocated by the caller, outside capture
     if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
     CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
     TraceArgs t{};
@@ -893,8 +902,7 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
         if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    if (!out->noised && !b->d_noised)
-        CU(cudaMalloc(&b->d_noised, sizeof(float) * std::max<int64_t>(1, b->total_polar)), "batch scratch");
+    CU(batch_scratch(b, out), "batch scratch");
     std::vector<unsigned char> key;
     append_bytes(key, *p);
     append_bytes(key, d_theta);
@@ -1094,8 +1102,7 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
         if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    if (!out->noised && !b->d_noised)
-        CU(cudaMalloc(&b->d_noised, sizeof(float) * std::max<int64_t>(1, b->total_polar)), "batch scratch");
+    CU(batch_scratch(b, out), "batch scratch");
     std::vector<ShapeKey> shapes;
     for (const sonar_batch_item& it : b->items) {
         const ShapeKey k{it.sensor.n_beams, it.sensor.n_elev, it.sensor.n_range_bins, it.sensor.n_az_bins};
@@ -1118,6 +1125,7 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
             for (int tb : {1, 2, 4, 8, 16, 32}) {
                 ctx->tune[k] = Tune{0, tb, 128, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
+                if (batch_scratch(b, out) != cudaSuccess) { st = fail(ctx, SONAR_ERR_OOM, "batch scratch"); goto restore; }
                 const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
                 if (cudaGetLastError() != cudaSuccess) continue;
                 if (ms < best_ms) { best_ms = ms; best.tb = tb; best.occ = occ; }
@@ -1131,6 +1139,7 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
                 if (cols > k[3] || (size_t)cols * k[2] * 4 > kMaxDynSmem / 2) continue;
                 ctx->tune[k] = Tune{cols, tb, block, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
+                if (batch_scratch(b, out) != cudaSuccess) { st = fail(ctx, SONAR_ERR_OOM, "batch scratch"); goto restore; }
                 const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
                 if (cudaGetLastError() != cudaSuccess) continue;
                 if (ms < best_ms) { best_ms = ms; best = Tune{cols, tb, block, occ}; }

@@ -391,8 +391,8 @@ class Batch:
             _ptr(self.hits) if hits else None, _ptr(d), _stream(stream)))
         return d
 
-    def autotune(self, theta, params: RenderParams = RenderParams(), stream=None):
-        out = self.outputs(True, True)
+    def autotune(self, theta, params: RenderParams = RenderParams(), stream=None, hits=True):
+        out = self.outputs(hits, True)
         prm = params.c()
         self.sonar._check(self.lib.sonar_autotune(self.h, C.byref(prm), _ptr(theta), theta.shape[0] - 2,
                                                   C.byref(out), _stream(stream)))

@@ -318,3 +318,25 @@ def test_autotune_keeps_results(son, tiny, tiny_sid):
         # elevation-lane mapping keeps the canonical fold order: any tile shape gives the same bits
         assert torch.equal(b.view(k)["polar"], single["polar"]), k
     b.close()
+
+
+def test_batch_without_hit_buffers(son, tiny, tiny_sid):
+    # the batch keeps its own hit-record scratch when the caller passes none,
+    # through graph capture and through the autotuner's re-planning
+    mesh, mu = tiny
+    items = batch_items(son, tiny, tiny_sid)
+    theta = son.theta(0.05, 1.0, np.concatenate([mu, [0.4, 0.6]]).astype(np.float32))
+    prm = RenderParams()
+    b = son.batch(items)
+    b.autotune(theta, prm, hits=False)
+    b.render(theta, prm, hits=False)
+    torch.cuda.synchronize()
+    ref = b.polar.clone()
+    b.render(theta, prm, hits=True)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, b.polar)
+    G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(4)).to(son.device)
+    assert torch.equal(b.backward(theta, prm, G, hits=False), b.backward(theta, prm, G, hits=True))
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+    b.close()
