@@ -210,7 +210,8 @@ sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* sensor,
 /* Adjoint of sonar_render.  d_grad_polar = dL/dN [n_range_bins][n_az_bins];
  * d_noised = the I~ that sonar_render wrote for the same (scene, sensor,
  * params, theta, seed, frame); d_hits = that render's hit records, or NULL to
- * recompute them by re-casting the rays (bitwise the same records).
+ * recompute them by re-casting the rays into context scratch (bitwise the
+ * same records).
  * Writes d_dtheta [2 + n_mat] f32 = (dL/dalpha, dL/dgain, dL/dmu[...]),
  * overwriting it.  Deterministic: the same inputs give the same bits. */
 sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
@@ -273,7 +274,8 @@ sonar_status sonar_render_batch(sonar_batch_t batch, const sonar_params* params,
 
 /* Adjoint of sonar_render_batch for the loss summed over items: d_grad_polar
  * and d_noised packed like the polar output, d_hits packed like the hit
- * output or NULL (recompute).  Writes d_dtheta [2 + n_mat], the gradient
+ * output or NULL (the records are recomputed by the ray-cast kernel into the
+ * batch's own scratch).  Writes d_dtheta [2 + n_mat], the gradient
  * summed over items.  Graph-captured like the forward. */
 sonar_status sonar_render_batch_backward(sonar_batch_t batch, const sonar_params* params,
                                          const float* d_theta, int32_t n_mat,

@@ -808,11 +808,12 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
     }
 }
 
-// Per-ray gather of dL/dP and accumulation of dtheta over a unit of rays.
+// Per-ray gather of dL/dP and accumulation of dtheta over a unit of rays,
+// reading the hit records (stored by the forward, or recomputed by the ray-cast
+// kernel just before: bitwise the same records).
 // Deterministic: each unit's sums go to its own row of `partials` (material
 // sums per warp in lane order, warp slabs added in warp order, alpha/gain per
 // thread then in a fixed tree); k_adj_final adds the rows in a fixed order.
-template <bool RECOMPUTE>
 __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
     extern __shared__ double slab[];   // [n_warps][n_mat]
     __shared__ SensorDev S;
@@ -858,26 +859,9 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
             int mat = 0;
             float v_mu = 0.0f;
             if (r < U.r1) {
-                const int i = r / S.ne, j = r - (r / S.ne) * S.ne;
-                uint32_t key, orig;
-                float rr, cf;
-                if (RECOMPUTE) {
-                    const Cast c = cast_ray<false>(S, SC, i, j, a.params, a.err, nullptr);
-                    key = kNoKey;
-                    if (c.orig != 0xFFFFFFFFu) {
-                        const int br = range_bin(S, c.t);
-                        if (br >= 0) key = (uint32_t)(br * S.naz + az_bin(S, i));
-                    }
-                    orig = c.orig;
-                    rr = c.t;
-                    cf = c.cosf;
-                } else {
-                    const uint4 h = *reinterpret_cast<const uint4*>(a.hits + S.hits_off + r);
-                    key = h.x;
-                    orig = h.y;
-                    rr = __uint_as_float(h.z);
-                    cf = __uint_as_float(h.w);
-                }
+                const uint4 h = __ldg(reinterpret_cast<const uint4*>(a.hits + S.hits_off + r));
+                const uint32_t key = h.x, orig = h.y;
+                const float rr = __uint_as_float(h.z), cf = __uint_as_float(h.w);
                 if (key != kNoKey) {
                     if (key >= (uint32_t)(S.nr * S.naz) || orig >= (uint32_t)SC.n_tris) {
                         atomicOr(a.err, SONAR_DEVERR_INDEX);
@@ -976,8 +960,7 @@ __global__ void k_popcount(const uint32_t* bits, int64_t words, unsigned long lo
 void set_kernel_attributes() {
     cudaFuncSetAttribute(k_bin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
 cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_sensors, int max_angles,
@@ -1033,20 +1016,17 @@ cudaError_t launch_adj_rows(const SensorDev* sensors, const int32_t* row_map, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a, bool recompute, int grid, int block, size_t smem,
-                           float* dtheta, cudaStream_t st) {
-    if (recompute) k_adjoint<true><<<grid, block, smem, st>>>(a);
-    else k_adjoint<false><<<grid, block, smem, st>>>(a);
+cudaError_t launch_adjoint(const AdjArgs& a, int grid, int block, size_t smem, float* dtheta, cudaStream_t st) {
+    k_adjoint<<<grid, block, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adj_final<<<a.n_mat + 2, 256, 0, st>>>(a.partials, a.n_units, a.n_mat + 2, dtheta);
     return cudaGetLastError();
 }
 
-int adjoint_blocks_per_sm(bool recompute, int block, size_t smem) {
+int adjoint_blocks_per_sm(int block, size_t smem) {
     int n = 0;
-    const void* f = recompute ? (const void*)k_adjoint<true> : (const void*)k_adjoint<false>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k_adjoint, block, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 

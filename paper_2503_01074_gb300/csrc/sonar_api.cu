@@ -463,10 +463,20 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     SensorDev S = make_sensor(*sensor, seed, frame, t, 0, 0);
     const int groups = params->normalise == 1 ? S.nr : 1;
     CU(grow(ctx->rowinfo, sizeof(RowInfo) * groups, s), "scratch allocation");
-    if (!d_hits) {   // re-casting the rays needs the exact-ray tables
+    const sonar_hit* hits = d_hits;
+    if (!hits) {   // recompute the hit records with the ray-cast kernel (bitwise the forward's)
         CU(grow(ctx->trig, sizeof(float4) * (size_t)(S.nb + S.ne), s), "scratch allocation");
+        CU(grow(ctx->hits, sizeof(sonar_hit) * (size_t)S.nb * S.ne, s), "scratch allocation");
         S.trig = (float4*)ctx->trig.p;
         CU(launch_trig(nullptr, S, 1, S.nb + S.ne, s), "trig launch");
+        TraceArgs tr{};
+        tr.one = S;
+        tr.one_scene = scene_dev(ctx->scenes[scene_id]);
+        tr.params = *params;
+        tr.hits = (sonar_hit*)ctx->hits.p;
+        tr.err = ctx->d_err;
+        CU(launch_trace(tr, S.trace_blocks, S.occ, s), "trace launch");
+        hits = (const sonar_hit*)ctx->hits.p;
     }
     const int nq = n_mat + 2;
     const int64_t rays = (int64_t)S.nb * S.ne;
@@ -486,12 +496,12 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     a.theta = d_theta;
     a.params = *params;
     a.grad = d_grad_polar;
-    a.hits = d_hits;
+    a.hits = hits;
     a.rowinfo = (const RowInfo*)ctx->rowinfo.p;
     a.partials = (double*)ctx->partials.p;
     a.err = ctx->d_err;
     const size_t smem = sizeof(double) * (t.block / 32) * n_mat;
-    CU(launch_adjoint(a, d_hits == nullptr, n_units, t.block, smem, d_dtheta, s), "adjoint launch");
+    CU(launch_adjoint(a, n_units, t.block, smem, d_dtheta, s), "adjoint launch");
     return SONAR_OK;
 }
 
@@ -936,7 +946,19 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     sonar_ctx* ctx = b->ctx;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
     CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
-    if (!hits) CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
+    if (!hits) {   // recompute the hit records with the ray-cast kernel into the batch scratch
+        CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
+        TraceArgs tr{};
+        tr.sensors = b->d_sens;
+        tr.scenes = b->d_scenes;
+        tr.block_map = b->d_trace_map;
+        tr.n_sensors = (int32_t)b->items.size();
+        tr.params = *p;
+        tr.hits = b->d_hits;
+        tr.err = ctx->d_err;
+        CU(launch_trace(tr, b->trace_prefix.back(), b->trace_occ, s), "batch trace launch");
+        hits = b->d_hits;
+    }
     if (p->normalise != 0)
         CU(launch_adj_rows(b->d_sens, b->d_row_map, SensorDev{}, (int)b->items.size(),
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
@@ -959,10 +981,10 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     a.partials = b->d_partials;
     a.err = ctx->d_err;
     const size_t smem = sizeof(double) * (b->block / 32) * n_mat;
-    const int per_sm = adjoint_blocks_per_sm(hits == nullptr, b->block, smem);
+    const int per_sm = adjoint_blocks_per_sm(b->block, smem);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->adj_units.size(),
                                                                     (int64_t)ctx->sm_count * per_sm));
-    CU(launch_adjoint(a, hits == nullptr, grid, b->block, smem, dtheta, s), "batch adjoint launch");
+    CU(launch_adjoint(a, grid, b->block, smem, dtheta, s), "batch adjoint launch");
     CU(cudaEventRecordWithFlags(b->ev[5], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
 }
@@ -981,6 +1003,8 @@ extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar
     for (const sonar_batch_item& it : b->items)
         if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!d_hits && !b->d_hits)   // recomputed records need the scratch; allocate outside capture
+        CU(cudaMalloc(&b->d_hits, sizeof(sonar_hit) * std::max<int64_t>(1, b->total_rays)), "batch scratch");
     if (n_mat > b->n_mat_cap) {
         if (b->d_partials) cudaFree(b->d_partials);
         b->d_partials = nullptr;

@@ -43,9 +43,8 @@ cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_adj_rows(const SensorDev* sensors, const int32_t* row_map, const SensorDev& one, int n_sensors,
                             int64_t total_groups, int normalise, const float* noised,
                             const float* grad, RowInfo* info, cudaStream_t st);
-cudaError_t launch_adjoint(const AdjArgs& a, bool recompute, int grid, int block, size_t smem,
-                           float* dtheta, cudaStream_t st);
-int adjoint_blocks_per_sm(bool recompute, int block, size_t smem);
+cudaError_t launch_adjoint(const AdjArgs& a, int grid, int block, size_t smem, float* dtheta, cudaStream_t st);
+int adjoint_blocks_per_sm(int block, size_t smem);
 cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
                          const TraceCounters& tc, uint32_t* err, cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out,

@@ -223,7 +223,7 @@ struct AdjArgs {
     const float* theta;
     sonar_params params;
     const float* grad;          // dL/dN, packed like the polar output
-    const sonar_hit* hits;      // nullptr: re-cast the rays
+    const sonar_hit* hits;      // the hit records (stored, or recomputed just before)
     const RowInfo* rowinfo;     // per sensor: at rowmax_off
     double* partials;           // [n_units][2 + n_mat]
     uint32_t* err;
