@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the single-frame and e2e legs")
     p.add_argument("--small", action="store_true", help="a small case for profiler captures")
+    p.add_argument("--tune", default=None, metavar="COLS,TB,BLOCK,OCC",
+                   help="fixed launch configuration instead of autotuning (profiler captures, whose "
+                        "replays distort the autotuner's timings)")
     p.add_argument("--configs", action="store_true",
                    help="also measure the heterogeneous-batch, large and dense-ray configurations")
     return p.parse_args()
@@ -68,15 +71,46 @@ def rank_info():
     return rank, world, local
 
 
-def workload(rank: int, frames: int, small: bool):
+SEED = 1   # Philox key of every frame; the counter's frame word is the global frame index
+
+
+def frame_shard(rank: int, world: int, frames: int):
+    """Global frame indices rendered by `rank`: the job's world x frames frames
+    (poses of one trajectory) are split into contiguous blocks, one per rank,
+    so no frame is rendered twice and no rank needs another's data."""
+    if not 0 <= rank < world or frames < 0:
+        raise ValueError(f"bad shard: rank {rank}, world {world}, frames {frames}")
+    return list(range(rank * frames, (rank + 1) * frames))
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The maximum of `x` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(frames_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job frames/s: the frames all ranks rendered over the slowest rank's time."""
+    return frames_per_rank * steps * world / (max_ms / 1000.0)
+
+
+def workload(rank: int, world: int, frames: int, small: bool):
+    """The scene, its sonar, and this rank's share of a trajectory of
+    world x frames poses (with their global frame indices)."""
     from paper_2503_01074_gb300 import scenes as S
     if small:
         mesh, mu, hfn = S.single_frame_scene(n_cells=512, extent=100.0)
     else:
         mesh, mu, hfn = S.single_frame_scene()
     base = S.sensor_single(hfn)
-    poses = S.trajectory(base, hfn, frames, radius=20.0 + 2.0 * rank, seed=rank)
-    return mesh, mu, base, poses
+    fids = frame_shard(rank, world, frames)
+    every = S.trajectory(base, hfn, world * frames, radius=20.0, seed=0)
+    return mesh, mu, base, [every[f] for f in fids], fids
 
 
 # ---------------------------------------------------------------------------
@@ -84,24 +118,84 @@ def workload(rank: int, frames: int, small: bool):
 # ---------------------------------------------------------------------------
 
 class Clocks:
+    """SM clock and throttle reasons sampled while the timed region runs.
+
+    A poller thread reads the driver's NVML library (through ctypes, read-only
+    queries) every millisecond, since the timed region can be shorter than
+    nvidia-smi's sampling period; where NVML does not load, nvidia-smi samples
+    every 200 ms instead."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clocks-event reason bits
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, uuid: str | None = None):
         self.proc = None
         self.path = None
-        self.gpu = gpu_index
+        self.thread = None
+        self.samples = []
+        self.source = None
+        if self._start_nvml(gpu_index, uuid):
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi, 200 ms"
         except Exception:
             self.proc = None
 
+    def _start_nvml(self, gpu_index, uuid):
+        import ctypes
+        import threading
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            ok = False
+            if uuid:
+                ok = lib.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(h)) == 0
+            if not ok:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(h)) == 0
+            if not ok:
+                return False
+            reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0:   # 1 = SM clock
+                return False
+        except Exception:
+            return False
+        self.max_mhz = float(mx.value)
+        self.stop_flag = threading.Event()
+
+        def poll():
+            clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop_flag.is_set():
+                if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
+                        reasons_fn(h, ctypes.byref(rs)) == 0:
+                    self.samples.append((float(clk.value), int(rs.value)))
+                time.sleep(0.001)
+
+        self.thread = threading.Thread(target=poll, daemon=True)
+        self.thread.start()
+        self.source = "NVML, 1 ms"
+        return True
+
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            if not self.samples:
+                return None
+            reasons = sorted({n for _, r in self.samples for n, b in self.REASON_BITS.items() if r & b})
+            return {"sm_mhz": float(np.median([c for c, _ in self.samples])), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.samples), "source": self.source}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -127,7 +221,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 # ---------------------------------------------------------------------------
@@ -166,7 +260,7 @@ def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return 0
-    mesh, mu, base, poses = workload(0, max(args.frames, 1), args.small)
+    mesh, mu, base, poses, _ = workload(0, 1, max(args.frames, 1), args.small)
     import oracle as O
     tv = O.tri_verts(mesh)
     n = min(args.cpu_rays, 2048)
@@ -312,7 +406,7 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     B = args.frames
-    mesh, mu, base, poses = workload(rank, B, args.small)
+    mesh, mu, base, poses, fids = workload(rank, world, B, args.small)
     son = Sonar(local)
     verts = torch.from_numpy(mesh.verts).to(dev)
     tris = torch.from_numpy(mesh.tris).to(dev)
@@ -324,9 +418,13 @@ def run_ours(args):
     build_ms = 1000.0 * (time.perf_counter() - t0)
     prm = RenderParams()
     theta = son.theta(ALPHA, GAIN, mu)
-    items = [(sid, p, 1000 * rank + k, k) for k, p in enumerate(poses)]
+    items = [(sid, p, SEED, f) for p, f in zip(poses, fids)]
+    if args.tune:
+        cols, tb, block, occ = (int(x) for x in args.tune.split(","))
+        son.tune_set([[base.n_beams, base.n_elev, base.n_range_bins, base.n_az_bins, cols, tb, block, occ]])
     batch = son.batch(items)
-    batch.autotune(theta, prm)
+    if not args.tune:
+        batch.autotune(theta, prm)
     G = torch.randn(batch.n_polar, generator=torch.Generator().manual_seed(5)).to(dev) * 1e-3
     dtheta = torch.empty_like(theta)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -341,7 +439,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = Clocks(local) if rank == 0 else None
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", "") or "") or None
+    clocks = Clocks(local, uuid) if rank == 0 else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     phase = []
     torch.cuda.nvtx.range_push("timed")
@@ -354,15 +453,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
     frames_total = B * args.steps * world
-    value = frames_total / (total_ms / 1000.0)
+    value = job_value(B, args.steps, world, total_ms)
     rays_per_frame = base.n_rays
     trace_ms = float(np.mean([p["trace"] for p in phase]))
     bin_ms = float(np.mean([p["bin_noise"] for p in phase]))
@@ -397,9 +493,9 @@ def run_ours(args):
                 flush.zero_()
                 e_f[0].record(stream)
                 for j, p in enumerate(poses):
-                    son.render(sid, p, theta, prm, 1000 * rank + j, j, hits=True, fan=True, outputs=out)
+                    son.render(sid, p, theta, prm, SEED, fids[j], hits=True, fan=True, outputs=out)
                     if with_adj:
-                        son.backward(sid, p, theta, prm, 1000 * rank + j, j, g1, out["noised"], out["hits"])
+                        son.backward(sid, p, theta, prm, SEED, fids[j], g1, out["noised"], out["hits"])
                 e_f[1].record(stream)
                 torch.cuda.synchronize()
                 ms.append(e_f[0].elapsed_time(e_f[1]))
@@ -429,12 +525,8 @@ def run_ours(args):
         from paper_2503_01074_gb300.sonar import BatchItem
         h2d = theta.numel() * 4 + G.numel() * 4 + B * __import__("ctypes").sizeof(BatchItem)
         d2h = batch.polar.numel() * 4 + batch.fan.numel() * 4 + dtheta.numel() * 4
-        e2e_total = float(sum(e2e_ms))
-        if world > 1:
-            t = torch.tensor([e2e_total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_total = float(t.item())
-        e2e = {"value": frames_total / (e2e_total / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e_total = max_over_ranks(float(sum(e2e_ms)), dev)
+        e2e = {"value": job_value(B, args.steps, world, e2e_total), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     # algorithmic bytes of one ray-cast launch: per frame, the 4-wide BVH nodes

@@ -18,9 +18,11 @@
 //
 // Ray casting precision: the walk and the triangle tests run in FP32.  A test
 // whose barycentric or distance outcome lies inside a certified FP32 error
-// bound, and any two candidates within 2e-5 t of each other, are re-decided in
-// FP64 against the exact ray (direction from FP64 trigonometry), so hit
-// decisions agree with an FP64 reference except for genuinely ambiguous rays.
+// bound, and any two candidates within 2e-5 t of each other, are re-decided
+// exactly in float-float arithmetic (about 48 significant bits, on the FP32
+// pipes) against the exact ray, whose direction comes from per-sensor sin/cos
+// tables computed in FP64 once; hit decisions therefore agree with an FP64
+// reference except for genuinely ambiguous rays.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -121,9 +123,10 @@ __device__ __forceinline__ void ray_dir_ff(const SensorDev& s, int i, int j, ff 
 
 // FP32 Moller-Trumbore with a certified error bound.  Returns 0 for a certain
 // miss, 1 for a certain hit (t set), 2 when FP32 cannot decide.  Each bound is
-// g * (product of the magnitudes entering the numerator) / |det|, g = 32 ulp,
-// which covers the rounding of the edge vectors, of the FP32 direction against
-// the exact one, and of the cross and dot products.
+// g * (product of the magnitudes entering the numerator) / |det|, with
+// g = 2^-19 (32 unit roundoffs), which covers the rounding of the edge vectors,
+// of the FP32 direction against the exact one, and of the cross and dot
+// products.
 __device__ __forceinline__ int mt32(float3 o, float3 d, float4 a, float4 b, float4 c, float& t) {
     const float3 v0 = f3(a.x, a.y, a.z);
     const float3 e1 = sub(f3(b.x, b.y, b.z), v0), e2 = sub(f3(c.x, c.y, c.z), v0);
@@ -136,7 +139,7 @@ __device__ __forceinline__ int mt32(float3 o, float3 d, float4 a, float4 b, floa
     const float ad = l1(d), as = l1(s), ae1 = l1(e1), ae2 = l1(e2);
     const float Edet = g * ae1 * ad * ae2;
     const float adet = fabsf(det);
-    if (adet <= Edet) return 2;   // near-parallel: decided in FP64
+    if (adet <= Edet) return 2;   // near-parallel: decided exactly
     const float inv = 1.0f / det;
     const float u = un * inv, v = vn * inv, w = 1.0f - u - v;
     t = tn * inv;
