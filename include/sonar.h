@@ -322,11 +322,12 @@ sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int32_t count)
 
 /* ---- counters (roofline evidence) ---- */
 
-/* Re-casts the rays of one sensor and counts, per ray, BVH node pairs
- * visited and triangles tested; also marks every node pair and triangle
- * touched.  out[0] node-pair visits, out[1] triangle tests, out[2] distinct
- * node pairs touched, out[3] distinct triangles touched, out[4] rays,
- * out[5] triangle tests resolved in FP64.  Synchronises the stream. */
+/* Re-casts the rays of one sensor (with the warp tiles tuned for its shape)
+ * and counts 4-wide BVH node visits (128 bytes each) and triangle tests;
+ * also marks every node and triangle touched.  out[0] node visits, out[1]
+ * triangle tests, out[2] distinct nodes touched, out[3] distinct triangles
+ * touched, out[4] rays, out[5] decisions taken exactly in float-float
+ * arithmetic (uncertain FP32 tests and near ties).  Synchronises the stream. */
 sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
                                const sonar_params* params, void* stream, int64_t out[6]);
 

@@ -240,185 +240,6 @@ __global__ void k_trig(const SensorDev* sensors, SensorDev one) {
     s.trig[k] = make_float4(sh, (float)(sn - (double)sh), ch, (float)(cs - (double)ch));
 }
 
-template <bool STATS>
-__device__ int trace_closest(const SceneDev& sc, const SensorDev& s, int ri, int rj, float3 o,
-                             float3 d, float tlimit, float& t_out, uint32_t* err,
-                             const TraceCounters* tc) {
-    if (sc.root == kEmpty) return -1;
-    const float tiny = 1e-20f;
-    const float3 inv = f3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
-                          1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
-                          1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
-    const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
-    int32_t stack[kStackMax];
-    int sp = 0;
-    int best = -1;
-    uint32_t best_id = 0xFFFFFFFFu;
-    float best_t = tlimit;
-    uint64_t visits = 0, tests = 0, exact_n = 0;
-    // `node`: the internal node to visit next (or kEmpty); `leaf`: a leaf whose
-    // triangles wait to be tested (0 = none; leaf handles are negative).  Lanes
-    // that reach a leaf park it and keep descending until every active lane of
-    // the warp holds one, so that the triangle tests run together.
-    int32_t node = sc.root, leaf = 0;
-    if (node < 0) { leaf = node; node = kEmpty; }
-    for (;;) {
-        while (node >= 0) {
-            const float4* p = sc.nodes + 8 * (int64_t)node;
-            const float4 lx = __ldg(p), hx = __ldg(p + 1), ly = __ldg(p + 2), hy = __ldg(p + 3);
-            const float4 lz = __ldg(p + 4), hz = __ldg(p + 5);
-            const int4 ch = __ldg(reinterpret_cast<const int4*>(p + 6));
-            if (STATS) {
-                ++visits;
-                atomicOr(tc->node_bits + (node >> 5), 1u << (node & 31));
-            }
-            const float tcut = best_t * 1.00002f;
-            const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
-            const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
-            const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
-            const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
-            // sort key per child: entry distance bits (>= 0, so integer order is
-            // distance order) with the child slot in the two low bits; a missed
-            // child sorts last as 0xFFFFFFFF
-            uint32_t key[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
-                float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-                t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
-                lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
-                t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
-                lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
-                const bool hit = hs[c] != kEmpty && lo <= hi * 1.0000005f;
-                key[c] = hit ? ((__float_as_uint(lo) & ~3u) | (uint32_t)c) : 0xFFFFFFFFu;
-            }
-#define SONAR_USORT(a, b)                                  \
-            {                                              \
-                const uint32_t mn = min(key[a], key[b]);   \
-                key[b] = max(key[a], key[b]);              \
-                key[a] = mn;                               \
-            }
-            SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
-#undef SONAR_USORT
-            const int nhit = (key[0] != 0xFFFFFFFFu) + (key[1] != 0xFFFFFFFFu) + (key[2] != 0xFFFFFFFFu) +
-                             (key[3] != 0xFFFFFFFFu);
-            if (nhit == 0) {
-                node = sp > 0 ? stack[--sp] : kEmpty;
-            } else {
-                if (sp + nhit - 1 > kStackMax) {
-                    atomicOr(err, SONAR_DEVERR_STACK);
-                    t_out = best_t;
-                    return -1;
-                }
-#pragma unroll
-                for (int c = 3; c >= 1; --c) {
-                    if (c < nhit) {
-                        const uint32_t k = key[c] & 3u;
-                        stack[sp++] = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-                    }
-                }
-                const uint32_t k = key[0] & 3u;
-                node = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-            }
-            if (node < 0 && node != kEmpty && leaf == 0) {   // park the leaf, keep descending
-                leaf = node;
-                node = sp > 0 ? stack[--sp] : kEmpty;
-            }
-            if (!__any_sync(__activemask(), leaf == 0)) break;
-        }
-        while (leaf != 0) {
-            // a run of triangles in leaf order
-            const int32_t x = ~leaf;
-            const int32_t first = x >> 3, count = (x & 7) + 1;
-            for (int k = 0; k < count; ++k) {
-                const int32_t f = first + k;
-                if (f >= sc.n_tris) {
-                    atomicOr(err, SONAR_DEVERR_INDEX);
-                    break;
-                }
-                const float4* tp = sc.tris + 3 * (int64_t)f;
-                const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-                if (STATS) {
-                    ++tests;
-                    atomicOr(tc->tri_bits + (f >> 5), 1u << (f & 31));
-                }
-                float t;
-                const int r = mt32(o, d, a, b, c, t);
-                if (r == 0) continue;
-                if (r == 2) {
-                    if (STATS) ++exact_n;
-                    if (!exact_hit(s, ri, rj, a, b, c, &t)) continue;
-                }
-                if (!(t < tlimit)) continue;
-                const uint32_t id = __float_as_uint(b.w);
-                bool take;
-                if (best < 0) {
-                    take = true;
-                } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
-                    // near tie: decide on the exact distances, then on the caller's index
-                    if (STATS) ++exact_n;
-                    take = exact_closer(s, ri, rj, tp, id, sc.tris + 3 * (int64_t)best, best_id);
-                } else {
-                    take = t < best_t;
-                }
-                if (take) {
-                    best = f;
-                    best_id = id;
-                    best_t = t;
-                }
-            }
-            leaf = 0;
-            if (node < 0 && node != kEmpty) {   // the next stacked entry is a leaf too
-                leaf = node;
-                node = sp > 0 ? stack[--sp] : kEmpty;
-            }
-        }
-        if (node == kEmpty) break;
-    }
-    if (STATS) {
-        atomicAdd(tc->visits, (unsigned long long)visits);
-        atomicAdd(tc->tests, (unsigned long long)tests);
-        atomicAdd(tc->exact, (unsigned long long)exact_n);
-    }
-    t_out = best_t;
-    return best;
-}
-
-struct Cast {
-    uint32_t orig;   // caller's triangle index (0xFFFFFFFF: miss)
-    int32_t mat;
-    float t;
-    float cosf;      // incidence factor
-};
-
-template <bool STATS>
-__device__ __forceinline__ Cast cast_ray(const SensorDev& s, const SceneDev& sc, int i, int j,
-                                         const sonar_params& p, uint32_t* err,
-                                         const TraceCounters* tc) {
-    const float3 o = f3(s.pos[0], s.pos[1], s.pos[2]);
-    const float3 d = ray_dir32(s, i, j);
-    float t;
-    const int f = trace_closest<STATS>(sc, s, i, j, o, d, p.clip_tmax ? s.rmax : CUDART_INF_F, t, err, tc);
-    Cast c;
-    if (f < 0) {
-        c.orig = 0xFFFFFFFFu;
-        c.mat = 0;
-        c.t = CUDART_INF_F;
-        c.cosf = 0.0f;
-        return c;
-    }
-    const float4* tp = sc.tris + 3 * (int64_t)f;
-    const float4 a = __ldg(tp), b = __ldg(tp + 1), cc = __ldg(tp + 2);
-    const float3 v0 = f3(a.x, a.y, a.z);
-    const float3 n = cross3(sub(f3(b.x, b.y, b.z), v0), sub(f3(cc.x, cc.y, cc.z), v0));
-    const float dn = dot3(d, n) / sqrtf(dot3(n, n));
-    c.orig = __float_as_uint(b.w);
-    c.mat = __float_as_int(a.w);
-    c.t = t;
-    c.cosf = p.two_sided ? fabsf(dn) : fmaxf(-dn, 0.0f);
-    return c;
-}
-
 // Range bin of a hit, or -1 when r is outside [r_min, r_max).
 __device__ __forceinline__ int range_bin(const SensorDev& s, float r) {
     if (!(r >= s.rmin && r < s.rmax)) return -1;
@@ -446,7 +267,15 @@ __device__ __forceinline__ float small_u2f(uint32_t v) {
 // sensor; lane l of warp w traces beam i0 + w * tb + l % tb, elevation
 // j0 + l / tb, so that a warp's rays sample a compact patch of the field of
 // view.  Records go to their canonical index i * n_elev + j.
-template <int MINB>
+//
+// The walk over the 4-wide hierarchy is a while-while loop: a lane descends
+// nearest child first, pushing the other entered children; a lane that
+// reaches a leaf parks it and keeps descending until every active lane of the
+// warp holds one, so that the triangle tests run together.  A lane whose ray
+// is finished writes its record at once and idles until the warp is done.
+// With STATS the kernel also counts node visits and triangle tests and marks
+// the nodes and triangles it touches (records are then not written).
+template <int MINB, bool STATS>
 __global__ void __launch_bounds__(128, MINB) k_trace(TraceArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
@@ -467,20 +296,176 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceArgs a) {
     const int tb = S.tb, te = 32 / S.tb;
     const int bb = 4 * tb;
     const int tiles_b = (S.nb + bb - 1) / bb;
-    const int tile = s_tile;
-    const int ty = tile / tiles_b, tx = tile - ty * tiles_b;
+    const int ty = s_tile / tiles_b, tx = s_tile - ty * tiles_b;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = tx * bb + warp * tb + (lane % tb);
-    const int j = ty * te + lane / tb;
-    if (i >= S.nb || j >= S.ne) return;
-    const Cast c = cast_ray<false>(S, SC, i, j, a.params, a.err, nullptr);
-    uint32_t key = kNoKey;
-    if (c.orig != 0xFFFFFFFFu) {
-        const int br = range_bin(S, c.t);
-        if (br >= 0) key = (uint32_t)(br * S.naz + az_bin(S, i));
+    const int ri = tx * bb + warp * tb + (lane % tb);
+    const int rj = ty * te + lane / tb;
+    const SceneDev& sc = SC;
+    const sonar_params& p = a.params;
+    const float tlimit = p.clip_tmax ? S.rmax : CUDART_INF_F;
+    const float3 o = f3(S.pos[0], S.pos[1], S.pos[2]);
+    const bool inside = ri < S.nb && rj < S.ne;
+    const float3 d = inside ? ray_dir32(S, ri, rj) : f3(0.0f, 0.0f, 1.0f);
+    const float tiny = 1e-20f;
+    const float3 inv = f3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+                          1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+                          1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    int32_t stack[kStackMax];
+    int sp = 0, best = -1;
+    uint32_t best_id = 0xFFFFFFFFu;
+    float best_t = tlimit;
+    uint64_t visits = 0, tests = 0, exact_n = 0;
+    // `node`: the internal node to visit next (or kEmpty); `leaf`: a parked
+    // leaf whose triangles wait to be tested (0 = none; leaf handles are negative)
+    int32_t node = inside ? sc.root : kEmpty, leaf = 0;
+    if (node < 0 && node != kEmpty) { leaf = node; node = kEmpty; }
+    bool live = inside;
+    for (;;) {
+        if (live) {
+            while (node >= 0) {
+                const float4* pn = sc.nodes + 8 * (int64_t)node;
+                const float4 lx = __ldg(pn), hx = __ldg(pn + 1), ly = __ldg(pn + 2), hy = __ldg(pn + 3);
+                const float4 lz = __ldg(pn + 4), hz = __ldg(pn + 5);
+                const int4 ch = __ldg(reinterpret_cast<const int4*>(pn + 6));
+                if (STATS) {
+                    ++visits;
+                    atomicOr(a.tc.node_bits + (node >> 5), 1u << (node & 31));
+                }
+                const float tcut = best_t * 1.00002f;
+                const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
+                const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
+                const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
+                const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
+                // sort key per child: entry distance bits (>= 0, so integer order
+                // is distance order) with the child slot in the two low bits; a
+                // missed child sorts last as 0xFFFFFFFF
+                uint32_t key[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
+                    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+                    t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
+                    lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
+                    t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
+                    lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
+                    const bool hit = hs[c] != kEmpty && lo <= hi * 1.0000005f;
+                    key[c] = hit ? ((__float_as_uint(lo) & ~3u) | (uint32_t)c) : 0xFFFFFFFFu;
+                }
+#define SONAR_USORT(x, y)                                    \
+                {                                            \
+                    const uint32_t mn = min(key[x], key[y]); \
+                    key[y] = max(key[x], key[y]);            \
+                    key[x] = mn;                             \
+                }
+                SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
+#undef SONAR_USORT
+                const int nhit = (key[0] != 0xFFFFFFFFu) + (key[1] != 0xFFFFFFFFu) + (key[2] != 0xFFFFFFFFu) +
+                                 (key[3] != 0xFFFFFFFFu);
+                if (nhit == 0) {
+                    node = sp > 0 ? stack[--sp] : kEmpty;
+                } else {
+                    if (sp + nhit - 1 > kStackMax) {   // cannot happen for a checked height: give up the ray
+                        atomicOr(a.err, SONAR_DEVERR_STACK);
+                        node = kEmpty;
+                        leaf = 0;
+                        sp = 0;
+                        best = -1;
+                        break;
+                    }
+#pragma unroll
+                    for (int c = 3; c >= 1; --c) {
+                        if (c < nhit) {
+                            const uint32_t k = key[c] & 3u;
+                            stack[sp++] = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
+                        }
+                    }
+                    const uint32_t k = key[0] & 3u;
+                    node = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
+                }
+                if (node < 0 && node != kEmpty && leaf == 0) {   // park the leaf, keep descending
+                    leaf = node;
+                    node = sp > 0 ? stack[--sp] : kEmpty;
+                }
+                if (!__any_sync(__activemask(), leaf == 0)) break;
+            }
+            while (leaf != 0) {
+                // a run of triangles in leaf order
+                const int32_t x = ~leaf;
+                const int32_t first = x >> 3, count = (x & 7) + 1;
+                for (int k = 0; k < count; ++k) {
+                    const int32_t f = first + k;
+                    if (f >= sc.n_tris) {
+                        atomicOr(a.err, SONAR_DEVERR_INDEX);
+                        break;
+                    }
+                    const float4* tp = sc.tris + 3 * (int64_t)f;
+                    const float4 va = __ldg(tp), vb = __ldg(tp + 1), vc = __ldg(tp + 2);
+                    if (STATS) {
+                        ++tests;
+                        atomicOr(a.tc.tri_bits + (f >> 5), 1u << (f & 31));
+                    }
+                    float t;
+                    const int r = mt32(o, d, va, vb, vc, t);
+                    if (r == 0) continue;
+                    if (r == 2) {
+                        if (STATS) ++exact_n;
+                        if (!exact_hit(S, ri, rj, va, vb, vc, &t)) continue;
+                    }
+                    if (!(t < tlimit)) continue;
+                    const uint32_t id = __float_as_uint(vb.w);
+                    bool take;
+                    if (best < 0) {
+                        take = true;
+                    } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
+                        // near tie: decide on the exact distances, then on the caller's index
+                        if (STATS) ++exact_n;
+                        take = exact_closer(S, ri, rj, tp, id, sc.tris + 3 * (int64_t)best, best_id);
+                    } else {
+                        take = t < best_t;
+                    }
+                    if (take) {
+                        best = f;
+                        best_id = id;
+                        best_t = t;
+                    }
+                }
+                leaf = 0;
+                if (node < 0 && node != kEmpty) {   // the next stacked entry is a leaf too
+                    leaf = node;
+                    node = sp > 0 ? stack[--sp] : kEmpty;
+                }
+            }
+        }
+        if (live && node == kEmpty) {
+            // the ray is finished: its hit record (bin key, triangle, range, incidence)
+            live = false;
+            if (!STATS) {
+                uint32_t key = kNoKey, orig = 0xFFFFFFFFu, cosb = 0u;
+                float tr = CUDART_INF_F;
+                if (best >= 0) {
+                    const float4* tp = sc.tris + 3 * (int64_t)best;
+                    const float4 va = __ldg(tp), vb = __ldg(tp + 1), vc = __ldg(tp + 2);
+                    const float3 v0 = f3(va.x, va.y, va.z);
+                    const float3 n = cross3(sub(f3(vb.x, vb.y, vb.z), v0), sub(f3(vc.x, vc.y, vc.z), v0));
+                    const float dn = dot3(d, n) / sqrtf(dot3(n, n));
+                    orig = __float_as_uint(vb.w);
+                    tr = best_t;
+                    cosb = __float_as_uint(p.two_sided ? fabsf(dn) : fmaxf(-dn, 0.0f));
+                    const int br = range_bin(S, best_t);
+                    if (br >= 0) key = (uint32_t)(br * S.naz + az_bin(S, ri));
+                }
+                *reinterpret_cast<uint4*>(a.hits + S.hits_off + (int64_t)ri * S.ne + rj) =
+                    make_uint4(key, orig, __float_as_uint(tr), cosb);
+            }
+        }
+        if (__ballot_sync(0xFFFFFFFFu, live) == 0u) break;
     }
-    *reinterpret_cast<uint4*>(a.hits + S.hits_off + (int64_t)i * S.ne + j) =
-        make_uint4(key, c.orig, __float_as_uint(c.t), __float_as_uint(c.cosf));
+    if (STATS) {
+        atomicAdd(a.tc.visits, (unsigned long long)visits);
+        atomicAdd(a.tc.tests, (unsigned long long)tests);
+        atomicAdd(a.tc.exact, (unsigned long long)exact_n);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -596,11 +581,12 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         __syncthreads();
         const int drow = nt / cw, dcol = nt - drow * cw;
         int row = tid / cw, col = tid - row * cw;
+        const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
         for (int k = tid; k < nbin; k += nt) {
             const uint32_t b = (uint32_t)(row * S.naz + U.c0 + col);
             const float P = acc[k];
-            const U4 x = philox10(U4{b, S.frame_lo, 0u, S.frame_hi}, S.seed_lo, S.seed_hi);
-            const float w_sa = sig_sa * sqrtf(neg2log_u(x.x));
+            const U4 x = bin_draws(b, S, K);
+            const float w_sa = rayleigh_of(x, sig_sa);
             const float rc = fmaf(small_u2f(row) + 0.5f, dr, S.rmin);
             const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
             if (a.binned) a.binned[S.polar_off + b] = P;
@@ -621,12 +607,11 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
             const int rw = k / cw, cl = k - rw * cw;
             const uint32_t b = (uint32_t)(rw * S.naz + U.c0 + cl);
             const float P = acc[k];
-            const U4 x = philox10(U4{b, S.frame_lo, 0u, S.frame_hi}, S.seed_lo, S.seed_hi);
-            const float w_sa = sig_sa * sqrtf(neg2log_u(x.x));
+            const U4 x = bin_draws(b, S, K);
+            const float w_sa = rayleigh_of(x, sig_sa);
             const float rc = fmaf(small_u2f(rw) + 0.5f, dr, S.rmin);
             const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[cl] * w_sa);
-            const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);
-            const float w_sm = sig_sm * sqrtf(neg2log_u(x.y)) * cospif(2.0f * u2);
+            const float w_sm = gauss_of(x, sig_sm);
             const float In = P * (0.5f + w_sm) + additive;
             a.noised[S.polar_off + b] = In;
             acc[k] = In;
@@ -667,6 +652,35 @@ __global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
     const float* In = a.noised + s.polar_off + (int64_t)row * naz;
     float* out = a.polar + s.polar_off + (int64_t)row * naz;
     float m = 0.0f;
+    if (((s.polar_off | naz) & 3) == 0 && naz <= 1024) {
+        // 16-byte rows of up to 1024 bins: the row stays in registers between
+        // the maximum and the division (one read of I~)
+        const int n4 = naz >> 2;
+        const float4* In4 = reinterpret_cast<const float4*>(In);
+        float4* out4 = reinterpret_cast<float4*>(out);
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int q = lane + 32 * k;
+            v[k] = q < n4 ? __ldg(In4 + q) : make_float4(-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
+        }
+        if (a.normalise == 1) {
+            m = -CUDART_INF_F;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m = fmaxf(fmaxf(m, fmaxf(v[k].x, v[k].y)), fmaxf(v[k].z, v[k].w));
+            for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        } else if (a.normalise == 2) {
+            m = ord_dec(a.gmax[s.rowmax_off]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int q = lane + 32 * k;
+            if (q < n4)
+                out4[q] = make_float4(norm_value(v[k].x, m, a.normalise), norm_value(v[k].y, m, a.normalise),
+                                      norm_value(v[k].z, m, a.normalise), norm_value(v[k].w, m, a.normalise));
+        }
+        return;
+    }
     if (a.normalise == 1) {
         m = -CUDART_INF_F;
         for (int j = lane; j < naz; j += 32) m = fmaxf(m, In[j]);
@@ -681,16 +695,25 @@ __global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
 // phase 2b: fan resample of the normalised image
 // ---------------------------------------------------------------------------
 
-// Fan pixel value; `val(row, col)` returns the normalised polar value.
-template <class F>
-__device__ __forceinline__ float fan_pixel(const SensorDev& s, int64_t pix, F val) {
-    const int v = (int)(pix / s.fan_w), u = (int)(pix - (int64_t)v * s.fan_w);
+// Where fan pixel `pix` samples the polar image: x = index of bin (ia, ja),
+// y = (ib != ia ? naz : 0) << 1 | (jb != ja), z, w = the bilinear weights wr,
+// wa (bit patterns); x = 0xFFFFFFFF outside the fan.  Bilinear over bin
+// centres, clamped to the edge bins.
+__device__ __forceinline__ uint4 fan_coord(const SensorDev& s, int64_t pix) {
+    int v, u;
+    if ((int64_t)s.fan_w * s.fan_h < (1ll << 31)) {
+        v = (int)((uint32_t)pix / (uint32_t)s.fan_w);
+        u = (int)pix - v * s.fan_w;
+    } else {
+        v = (int)(pix / s.fan_w);
+        u = (int)(pix - (int64_t)v * s.fan_w);
+    }
     const float inv_scale = 1.0f / s.fan_scale;
     const float x = ((float)u + 0.5f - 0.5f * (float)s.fan_w) * inv_scale;
     const float y = ((float)s.fan_h - (float)v - 0.5f) * inv_scale;
     const float r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
     const float phi = atan2f(x, y);
-    if (r < s.rmin || r > s.rmax || fabsf(phi) > 0.5f * s.hfov) return 0.0f;
+    if (r < s.rmin || r > s.rmax || fabsf(phi) > 0.5f * s.hfov) return make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     const float fr = __fsub_rn(__fmul_rn(r - s.rmin, s.inv_dr), 0.5f);
     const float fa = __fsub_rn(__fmul_rn(phi + 0.5f * s.hfov, (float)s.naz / s.hfov), 0.5f);
     const float i0f = floorf(fr), j0f = floorf(fa);
@@ -698,34 +721,121 @@ __device__ __forceinline__ float fan_pixel(const SensorDev& s, int64_t pix, F va
     const int i0 = (int)i0f, j0 = (int)j0f;
     const int ia = min(max(i0, 0), s.nr - 1), ib = min(max(i0 + 1, 0), s.nr - 1);
     const int ja = min(max(j0, 0), s.naz - 1), jb = min(max(j0 + 1, 0), s.naz - 1);
+    return make_uint4((uint32_t)(ia * s.naz + ja), ((ib != ia ? (uint32_t)s.naz : 0u) << 1) | (jb != ja ? 1u : 0u),
+                      __float_as_uint(wr), __float_as_uint(wa));
+}
+
+// The fan value at coordinates c over polar image P (explicit roundings: the
+// table and the direct path give the same bits).
+__device__ __forceinline__ float fan_blend(uint4 c, const float* P) {
+    if (c.x == 0xFFFFFFFFu) return 0.0f;
+    const uint32_t dj = c.y & 1u, dn = c.y >> 1;
+    const float* q = P + c.x;
+    const float wr = __uint_as_float(c.z), wa = __uint_as_float(c.w);
     const float ua = 1.0f - wa, ur = 1.0f - wr;
-    const float top = __fadd_rn(__fmul_rn(ua, val(ia, ja)), __fmul_rn(wa, val(ia, jb)));
-    const float bot = __fadd_rn(__fmul_rn(ua, val(ib, ja)), __fmul_rn(wa, val(ib, jb)));
+    const float top = __fadd_rn(__fmul_rn(ua, q[0]), __fmul_rn(wa, q[dj]));
+    const float bot = __fadd_rn(__fmul_rn(ua, q[dn]), __fmul_rn(wa, q[dn + dj]));
     return __fadd_rn(__fmul_rn(ur, top), __fmul_rn(wr, bot));
 }
 
+// One block = a kFanSide x kFanSide square of one sensor's fan (a square maps
+// to a compact patch of the polar image, so its gathers stay in cache); lane
+// x of a 64-thread row takes column x, rows step by 4.  A sensor with a
+// coordinate table reads its pixels' coordinates from it.
 __global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
     __shared__ SensorDev S;
-    __shared__ int64_t s_base;
+    __shared__ int s_sq;
     if (threadIdx.x == 0) {
         if (a.block_map) {
             const int2 m = a.block_map[blockIdx.x];
             S = a.sensors[m.x];
-            s_base = (int64_t)m.y * kFanTile;
+            s_sq = m.y;
         } else {
             S = a.one;
-            s_base = (int64_t)blockIdx.x * kFanTile;
+            s_sq = blockIdx.x;
         }
     }
     __syncthreads();
-    const int64_t n = (int64_t)S.fan_w * S.fan_h;
+    const int sx = (S.fan_w + kFanSide - 1) / kFanSide;
+    const int u = (s_sq % sx) * kFanSide + (threadIdx.x & (kFanSide - 1));
+    const int v0 = (s_sq / sx) * kFanSide + (threadIdx.x / kFanSide);
+    if (u >= S.fan_w) return;
     const float* P = a.polar + S.polar_off;
     float* F = a.fan + S.fan_off;
-    const int naz = S.naz;
+    const uint4* lut = S.fan_lut;
+#pragma unroll 4
+    for (int k = 0; k < kFanSide; k += 256 / kFanSide) {
+        const int v = v0 + k;
+        if (v >= S.fan_h) break;
+        const int64_t pix = (int64_t)v * S.fan_w + u;
+        F[pix] = fan_blend(lut ? __ldg(lut + pix) : fan_coord(S, pix), P);
+    }
+}
+
+// The fan of the frames that share one coordinate table, in the same squares:
+// one thread reads a pixel's table entry once and resamples that pixel for up
+// to kFanGroup frames (a frame whose geometry no longer matches the table
+// computes its own coordinates).
+__global__ void __launch_bounds__(256) k_fan_group(FanGroupArgs a) {
+    __shared__ SensorDev M[kFanGroup];
+    __shared__ int4 s_m;
+    __shared__ int s_w, s_h;
+    __shared__ const uint4* s_lut;
+    if (threadIdx.x == 0) {
+        s_m = a.block_map[blockIdx.x];
+        const SensorDev& o = a.sensors[s_m.x];
+        s_w = o.fan_w;
+        s_h = o.fan_h;
+        s_lut = o.fan_lut;
+    }
+    __syncthreads();
+    const int nm = s_m.w - s_m.z;
+    constexpr int kWords = (int)(sizeof(SensorDev) / 4);
+    for (int i = threadIdx.x; i < nm * kWords; i += blockDim.x) {
+        const int q = i / kWords;
+        reinterpret_cast<uint32_t*>(M)[i] =
+            reinterpret_cast<const uint32_t*>(a.sensors + a.members[s_m.z + q])[i - q * kWords];
+    }
+    __syncthreads();
+    const int w = s_w, h = s_h;
+    const int sx = (w + kFanSide - 1) / kFanSide;
+    const int u = (s_m.y % sx) * kFanSide + (threadIdx.x & (kFanSide - 1));
+    const int v0 = (s_m.y / sx) * kFanSide + (threadIdx.x / kFanSide);
+    if (u >= w) return;
+    const uint4* lut = s_lut;
+#pragma unroll 1
+    for (int k = 0; k < kFanSide; k += 256 / kFanSide) {
+        const int v = v0 + k;
+        if (v >= h) break;
+        const int64_t pix = (int64_t)v * w + u;
+        const uint4 c = lut ? __ldg(lut + pix) : fan_coord(M[0], pix);
+#pragma unroll
+        for (int q = 0; q < kFanGroup; ++q) {
+            if (q < nm) {
+                const uint4 cq = M[q].fan_lut ? c : fan_coord(M[q], pix);
+                a.fan[M[q].fan_off + pix] = fan_blend(cq, a.polar + M[q].polar_off);
+            }
+        }
+    }
+}
+
+// Fills the coordinate table of each owner sensor (one block = kFanTile pixels).
+__global__ void __launch_bounds__(256) k_fan_lut(FanLutArgs a) {
+    __shared__ SensorDev S;
+    __shared__ int64_t s_base;
+    __shared__ uint4* s_lut;
+    if (threadIdx.x == 0) {
+        const int2 m = a.block_map[blockIdx.x];
+        S = a.sensors[m.x];
+        s_base = (int64_t)m.y * kFanTile;
+        s_lut = a.luts[m.x];
+    }
+    __syncthreads();
+    const int64_t n = (int64_t)S.fan_w * S.fan_h;
 #pragma unroll 1
     for (int k = 0; k < kFanTile / 256; ++k) {
         const int64_t pix = s_base + k * 256 + threadIdx.x;
-        if (pix < n) F[pix] = fan_pixel(S, pix, [&](int row, int col) { return P[(int64_t)row * naz + col]; });
+        if (pix < n) s_lut[pix] = fan_coord(S, pix);
     }
 }
 
@@ -741,7 +851,7 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
     const int lane = threadIdx.x & 31;
     __shared__ float s_m[32];
     __shared__ int s_a[32];
-    __shared__ double s_d[32];
+    __shared__ ff s_d[32];
     if (mode == 1) {
         const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (g >= total) return;
@@ -752,23 +862,45 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
         float m = -CUDART_INF_F;
         int am = 0x7FFFFFFF;
         float dl = 0.0f;                      // per-lane partial of sum G I~ (few terms)
-        for (int j = lane; j < s.naz; j += 32) {
-            const float x = In[j];
-            if (x > m) { m = x; am = j; }
-            dl = fmaf(G[j], x, dl);
+        if (((s.polar_off | s.naz) & 3) == 0) {
+            // 16-byte rows: each lane takes 4 consecutive bins per load, in index order
+            const float4* In4 = reinterpret_cast<const float4*>(In);
+            const float4* G4 = reinterpret_cast<const float4*>(G);
+#pragma unroll 4
+            for (int q = lane; q < (s.naz >> 2); q += 32) {
+                const float4 x = __ldg(In4 + q), y = __ldg(G4 + q);
+                const int j = q << 2;
+                if (x.x > m) { m = x.x; am = j; }
+                if (x.y > m) { m = x.y; am = j + 1; }
+                if (x.z > m) { m = x.z; am = j + 2; }
+                if (x.w > m) { m = x.w; am = j + 3; }
+                dl = fmaf(y.x, x.x, dl);
+                dl = fmaf(y.y, x.y, dl);
+                dl = fmaf(y.z, x.z, dl);
+                dl = fmaf(y.w, x.w, dl);
+            }
+        } else {
+            for (int j = lane; j < s.naz; j += 32) {
+                const float x = In[j];
+                if (x > m) { m = x; am = j; }
+                dl = fmaf(G[j], x, dl);
+            }
         }
-        double dot = dl;
+        // lane partials added across the warp in float-float (error-free
+        // two-sums on the FP32 pipes: FP64 would cost more than the row's loads)
+        ff dot{dl, 0.0f};
         for (int o = 16; o; o >>= 1) {
             const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o);
             const int a2 = __shfl_xor_sync(0xFFFFFFFFu, am, o);
             if (m2 > m || (m2 == m && a2 < am)) { m = m2; am = a2; }
-            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, o);
+            const ff d2{__shfl_xor_sync(0xFFFFFFFFu, dot.hi, o), __shfl_xor_sync(0xFFFFFFFFu, dot.lo, o)};
+            dot = ff_add(dot, d2);
         }
         if (lane == 0) {
             RowInfo r;
             r.m = m;
             r.valid = m > 0.0f;
-            r.c = r.valid ? (float)(dot / ((double)m * (double)m)) : 0.0f;
+            r.c = r.valid ? (__fadd_rn(dot.hi, dot.lo) / m) / m : 0.0f;
             r.arg = row * s.naz + am;
             info[g] = r;
         }
@@ -781,17 +913,19 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
         const float* G = grad + s.polar_off;
         float m = -CUDART_INF_F;
         int am = 0x7FFFFFFF;
-        double dot = 0.0;
+        ff dot{0.0f, 0.0f};   // float-float: products exact (FMA), sums error-free
         for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-            const float x = In[j];
+            const float x = In[j], y = G[j];
             if (x > m) { m = x; am = (int)j; }
-            dot += (double)G[j] * (double)x;
+            const float p = __fmul_rn(y, x);
+            dot = ff_add(dot, ff{p, fmaf(y, x, -p)});
         }
         for (int o = 16; o; o >>= 1) {
             const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o);
             const int a2 = __shfl_xor_sync(0xFFFFFFFFu, am, o);
             if (m2 > m || (m2 == m && a2 < am)) { m = m2; am = a2; }
-            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, o);
+            const ff d2{__shfl_xor_sync(0xFFFFFFFFu, dot.hi, o), __shfl_xor_sync(0xFFFFFFFFu, dot.lo, o)};
+            dot = ff_add(dot, d2);
         }
         const int w = threadIdx.x >> 5;
         if (lane == 0) { s_m[w] = m; s_a[w] = am; s_d[w] = dot; }
@@ -799,12 +933,12 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
         if (threadIdx.x == 0) {
             for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
                 if (s_m[k] > m || (s_m[k] == m && s_a[k] < am)) { m = s_m[k]; am = s_a[k]; }
-                dot += s_d[k];
+                dot = ff_add(dot, s_d[k]);
             }
             RowInfo r;
             r.m = m;
             r.valid = m > 0.0f;
-            r.c = r.valid ? (float)(dot / ((double)m * (double)m)) : 0.0f;
+            r.c = r.valid ? (__fadd_rn(dot.hi, dot.lo) / m) / m : 0.0f;
             r.arg = am;
             info[s.rowmax_off] = r;
         }
@@ -855,6 +989,7 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
         }
         for (int k = tid; k < nw * nm; k += nt) slab[k] = 0.0;
         __syncthreads();
+        const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
         float acc_a = 0.0f, acc_g = 0.0f;
         for (int base = U.r0; base < U.r1; base += nt) {
             const int r = base + tid;
@@ -875,7 +1010,7 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
                             const RowInfo ri = a.rowinfo[S.rowmax_off + (mode == 1 ? (int)(key / S.naz) : 0)];
                             if (ri.valid) gI = G / ri.m - ((int)key == ri.arg ? ri.c : 0.0f);
                         }
-                        const float gP = gI * (0.5f + w_sm_of(key, S, a.params.sigma_sm));
+                        const float gP = gI * (0.5f + w_sm_of(key, S, a.params.sigma_sm, K));
                         mat = SC.mat_orig[orig];
                         mat = mat < nm ? mat : nm - 1;
                         const float mu = __ldg(a.theta + 2 + mat);
@@ -938,14 +1073,6 @@ __global__ void __launch_bounds__(256) k_adj_final(const double* partials, int n
 // counters
 // ---------------------------------------------------------------------------
 
-__global__ void k_stats(SensorDev s, SceneDev sc, sonar_params p, TraceCounters tc, uint32_t* err) {
-    const int64_t n = (int64_t)s.nb * s.ne;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int i = (int)(k / s.ne), j = (int)(k - (int64_t)i * s.ne);
-    cast_ray<true>(s, sc, i, j, p, err, &tc);
-}
-
 __global__ void k_popcount(const uint32_t* bits, int64_t words, unsigned long long* out) {
     unsigned long long c = 0;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x)
@@ -975,8 +1102,8 @@ cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_se
 
 cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st) {
     if (blocks > 0) {
-        if (occupancy >= 8) k_trace<8><<<blocks, 128, 0, st>>>(a);
-        else k_trace<1><<<blocks, 128, 0, st>>>(a);
+        if (occupancy >= 8) k_trace<8, false><<<blocks, 128, 0, st>>>(a);
+        else k_trace<1, false><<<blocks, 128, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1002,6 +1129,16 @@ cudaError_t launch_norm(const NormArgs& a, cudaStream_t st) {
 
 cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st) {
     if (blocks > 0) k_fan_tiles<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fan_group(const FanGroupArgs& a, int blocks, cudaStream_t st) {
+    if (blocks > 0) k_fan_group<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fan_lut(const FanLutArgs& a, int blocks, cudaStream_t st) {
+    if (blocks > 0) k_fan_lut<<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1035,8 +1172,14 @@ int adjoint_blocks_per_sm(int block, size_t smem) {
 
 cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
                          const TraceCounters& tc, uint32_t* err, cudaStream_t st) {
-    const int64_t n = (int64_t)s.nb * s.ne;
-    k_stats<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(s, sc, p, tc, err);
+    TraceArgs a{};
+    a.one = s;
+    a.one_scene = sc;
+    a.n_sensors = 1;
+    a.params = p;
+    a.err = err;
+    a.tc = tc;
+    if (s.trace_blocks > 0) k_trace<1, true><<<s.trace_blocks, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -181,9 +181,10 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     d.frame_hi = (uint32_t)(frame >> 32);
     d.cols = t.cols;
     d.n_tiles = (s.n_az_bins + t.cols - 1) / t.cols;
-    d.tb = t.tb;
+    const int tb = (t.tb >= 1 && t.tb <= 32 && (t.tb & (t.tb - 1)) == 0) ? t.tb : 8;   // beams per warp tile
+    d.tb = tb;
     d.occ = t.occ;
-    const int64_t bb = 4 * t.tb, be = 32 / t.tb;
+    const int64_t bb = 4 * tb, be = 32 / tb;
     d.trace_blocks = (int32_t)(((s.n_beams + bb - 1) / bb) * ((s.n_elev + be - 1) / be));
     return d;
 }
@@ -195,7 +196,7 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
 // ===========================================================================
 
 extern "C" const char* sonar_version(void) {
-    return "libsonar 1.0 (sm_103a; LBVH + FP32/FP64-certified Moller-Trumbore; Philox4x32-10)";
+    return "libsonar 1.0 (sm_103a; 4-wide LBVH + certified FP32 Moller-Trumbore with float-float exact decisions; Philox4x32-10)";
 }
 
 extern "C" sonar_status sonar_create(int32_t device, sonar_ctx_t* out) {
@@ -370,8 +371,7 @@ sonar_status single_post(sonar_ctx* ctx, const SensorDev& S, int normalise, cons
         f.one = S;
         f.polar = polar;
         f.fan = fan;
-        const int64_t px = (int64_t)S.fan_w * S.fan_h;
-        CU(launch_fan_tiles(f, (int)((px + kFanTile - 1) / kFanTile), s), "fan launch");
+        CU(launch_fan_tiles(f, fan_squares(S.fan_w, S.fan_h), s), "fan launch");
     }
     return SONAR_OK;
 }
@@ -379,7 +379,9 @@ sonar_status single_post(sonar_ctx* ctx, const SensorDev& S, int normalise, cons
 // Rays per adjoint work unit: about four units per SM over the whole render,
 // a multiple of the block size.
 int adj_chunk(int64_t rays, int sm_count, int block) {
-    int64_t c = rays / (4 * (int64_t)sm_count);
+    // about 16 units per SM: the per-ray gather is latency-bound and wants
+    // many resident blocks
+    int64_t c = rays / (16 * (int64_t)sm_count);
     c = (c + block - 1) / block * block;
     return (int)std::max<int64_t>(block, std::min<int64_t>(c, 64ll * block));
 }
@@ -439,8 +441,7 @@ extern "C" sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* 
     f.one = S;
     f.polar = d_polar;
     f.fan = d_fan;
-    const int64_t px = (int64_t)fan_w * fan_h;
-    CU(launch_fan_tiles(f, (int)((px + kFanTile - 1) / kFanTile), (cudaStream_t)stream), "fan launch");
+    CU(launch_fan_tiles(f, fan_squares(S.fan_w, S.fan_h), (cudaStream_t)stream), "fan launch");
     return SONAR_OK;
 }
 
@@ -532,6 +533,17 @@ struct sonar_batch {
     int2* d_trace_map = nullptr;      // per trace block: (sensor, tile)
     int2* d_fan_map = nullptr;        // per fan block: (sensor, block)
     int32_t* d_row_map = nullptr;     // per range row: sensor
+    // fan coordinate tables: sensors with the same fan geometry share one,
+    // filled from the owner's descriptor on every forward replay
+    std::vector<int> lut_owner;       // per sensor: owner of its table (-1: none)
+    std::vector<uint4*> lut_of;       // per sensor: the table of its owner (nullptr: none)
+    uint4* d_fan_lut = nullptr;       // all tables
+    uint4** d_luts = nullptr;         // per sensor: its own table when it is an owner
+    int2* d_lut_map = nullptr;        // per table block: (owner, block)
+    int4* d_group_map = nullptr;      // per grouped fan block: (owner, pixel block, users [m0, m1))
+    int32_t* d_members = nullptr;     // users of each table, by owner
+    int lut_blocks = 0, group_blocks = 0;
+    int fan_blocks = 0;               // blocks of the per-sensor fan launch
     sonar_hit* d_hits = nullptr;      // hit records when the caller asks for none
     float4* d_trig = nullptr;         // per-sensor exact-ray tables
     int max_angles = 0;
@@ -563,8 +575,16 @@ void batch_free_device(sonar_batch* b) {
                     (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_trace_map,
                     (void*)b->d_fan_map, (void*)b->d_row_map, (void*)b->d_hits, (void*)b->d_trig,
                     (void*)b->d_rowmax,
-                    (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters})
+                    (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters,
+                    (void*)b->d_fan_lut, (void*)b->d_luts, (void*)b->d_lut_map, (void*)b->d_group_map,
+                    (void*)b->d_members})
         if (p) cudaFree(p);
+    b->d_fan_lut = nullptr;
+    b->d_luts = nullptr;
+    b->d_lut_map = nullptr;
+    b->d_group_map = nullptr;
+    b->d_members = nullptr;
+    b->lut_blocks = b->group_blocks = b->fan_blocks = 0;
     b->d_trace_prefix = nullptr;
     b->d_trace_map = nullptr;
     b->d_fan_map = nullptr;
@@ -581,6 +601,13 @@ void batch_free_device(sonar_batch* b) {
     b->fwd = b->bwd = nullptr;
     b->fwd_key.clear();
     b->bwd_key.clear();
+}
+
+// Fan pixels sample the same bins with the same weights exactly when these agree.
+bool same_fan_geometry(const SensorDev& x, const SensorDev& y) {
+    auto eq = [](float a, float b) { return memcmp(&a, &b, sizeof a) == 0; };
+    return x.nr == y.nr && x.naz == y.naz && x.fan_w == y.fan_w && x.fan_h == y.fan_h && eq(x.hfov, y.hfov) &&
+           eq(x.rmin, y.rmin) && eq(x.rmax, y.rmax) && eq(x.inv_dr, y.inv_dr) && eq(x.fan_scale, y.fan_scale);
 }
 
 std::vector<SceneDev> scene_table(const sonar_ctx* ctx) {
@@ -631,7 +658,7 @@ sonar_status batch_plan(sonar_batch* b) {
         polar_end = std::max<int64_t>(polar_end, it.polar_offset + (int64_t)S.nr * S.naz);
         b->hs[k] = S;
         b->fan_prefix[k + 1] =
-            b->fan_prefix[k] + (int32_t)(((int64_t)S.fan_w * S.fan_h + kFanTile - 1) / kFanTile);
+            b->fan_prefix[k] + (S.fan_w > 0 ? fan_squares(S.fan_w, S.fan_h) : 0);
         b->trace_prefix[k + 1] = b->trace_prefix[k] + S.trace_blocks;
         block_votes[t.block] += (int64_t)S.nb * S.ne;
         for (int tile = 0; tile < S.n_tiles; ++tile) {
@@ -681,15 +708,80 @@ sonar_status batch_plan(sonar_batch* b) {
     alloc((void**)&b->d_adj_units, sizeof(AdjUnit) * na);
     alloc((void**)&b->d_fan_prefix, sizeof(int32_t) * (n + 1));
     alloc((void**)&b->d_trace_prefix, sizeof(int32_t) * (n + 1));
+    // fan coordinate tables for geometries that more than one sensor shares
+    b->lut_owner.assign(n, -1);
+    b->lut_of.assign(n, nullptr);
+    std::vector<int> owners;
+    std::vector<int> members(n, 0);
+    for (int k = 0; k < n; ++k) {
+        if (b->hs[k].fan_w <= 0) continue;
+        for (int o : owners)
+            if (same_fan_geometry(b->hs[k], b->hs[o])) { b->lut_owner[k] = o; ++members[o]; break; }
+        if (b->lut_owner[k] < 0) { owners.push_back(k); b->lut_owner[k] = k; members[k] = 1; }
+    }
+    int64_t lut_px = 0;
+    std::vector<int64_t> lut_at(n, -1);
+    std::vector<int2> lmap;
+    for (int o : owners) {
+        if (members[o] < 2) continue;
+        const int64_t px = (int64_t)b->hs[o].fan_w * b->hs[o].fan_h;
+        lut_at[o] = lut_px;
+        lut_px += px;
+        for (int64_t t = 0; t < (px + kFanTile - 1) / kFanTile; ++t) lmap.push_back(make_int2(o, (int)t));
+    }
+    for (int k = 0; k < n; ++k)
+        if (b->lut_owner[k] >= 0 && lut_at[b->lut_owner[k]] < 0) b->lut_owner[k] = -1;
+    b->lut_blocks = (int)lmap.size();
+    // the fan of a table's users: blocks of (owner, pixel block, run of up to
+    // kFanGroup users), so that a table entry serves several frames
+    std::vector<int4> gmap;
+    std::vector<int32_t> mem;
+    for (int o : owners) {
+        if (lut_at[o] < 0) continue;
+        const int32_t m0 = (int32_t)mem.size();
+        for (int k = 0; k < n; ++k)
+            if (b->lut_owner[k] == o) mem.push_back(k);
+        const int32_t m1 = (int32_t)mem.size();
+        for (int32_t a0 = m0; a0 < m1; a0 += kFanGroup)
+            for (int t = 0; t < fan_squares(b->hs[o].fan_w, b->hs[o].fan_h); ++t)
+                gmap.push_back(make_int4(o, t, a0, std::min(a0 + kFanGroup, m1)));
+    }
+    b->group_blocks = (int)gmap.size();
+    if (lut_px > 0) {
+        alloc((void**)&b->d_fan_lut, sizeof(uint4) * lut_px);
+        alloc((void**)&b->d_luts, sizeof(uint4*) * n);
+        alloc((void**)&b->d_lut_map, sizeof(int2) * lmap.size());
+        alloc((void**)&b->d_group_map, sizeof(int4) * gmap.size());
+        alloc((void**)&b->d_members, sizeof(int32_t) * mem.size());
+        if (e == cudaSuccess) {
+            std::vector<uint4*> own(n, nullptr);
+            for (int k = 0; k < n; ++k) {
+                const int o = b->lut_owner[k];
+                if (o < 0) continue;
+                b->lut_of[k] = b->d_fan_lut + lut_at[o];
+                b->hs[k].fan_lut = b->lut_of[k];
+                if (o == k) own[k] = b->lut_of[k];
+            }
+            e = cudaMemcpy(b->d_luts, own.data(), sizeof(uint4*) * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b->d_lut_map, lmap.data(), sizeof(int2) * lmap.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b->d_group_map, gmap.data(), sizeof(int4) * gmap.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b->d_members, mem.data(), sizeof(int32_t) * mem.size(), cudaMemcpyHostToDevice);
+        }
+    }
     std::vector<int2> tmap, fmap;
     std::vector<int32_t> rmap;
     for (int k = 0; k < n; ++k) {
         for (int t = 0; t < b->hs[k].trace_blocks; ++t) tmap.push_back(make_int2(k, t));
-        for (int t = 0; t < b->fan_prefix[k + 1] - b->fan_prefix[k]; ++t) fmap.push_back(make_int2(k, t));
+        if (b->lut_owner[k] < 0)   // sensors with a shared table are resampled by the grouped launch
+            for (int t = 0; t < b->fan_prefix[k + 1] - b->fan_prefix[k]; ++t) fmap.push_back(make_int2(k, t));
         for (int r = 0; r < b->hs[k].nr; ++r) rmap.push_back(k);
     }
     alloc((void**)&b->d_trace_map, sizeof(int2) * tmap.size());
     alloc((void**)&b->d_fan_map, sizeof(int2) * std::max<size_t>(1, fmap.size()));
+    b->fan_blocks = (int)fmap.size();
     alloc((void**)&b->d_row_map, sizeof(int32_t) * rmap.size());
     int64_t angles = 0;
     b->max_angles = 0;
@@ -806,7 +898,13 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
         f.n_sensors = (int32_t)b->items.size();
         f.polar = out->polar;
         f.fan = out->fan;
-        CU(launch_fan_tiles(f, b->fan_prefix.back(), s), "batch fan launch");
+        if (b->lut_blocks > 0) {
+            FanLutArgs l{b->d_sens, b->d_lut_map, b->d_luts};
+            CU(launch_fan_lut(l, b->lut_blocks, s), "batch fan table launch");
+            FanGroupArgs g{b->d_sens, b->d_group_map, b->d_members, out->polar, out->fan};
+            CU(launch_fan_group(g, b->group_blocks, s), "batch grouped fan launch");
+        }
+        CU(launch_fan_tiles(f, b->fan_blocks, s), "batch fan launch");
     }
     if (events) CU(cudaEventRecordWithFlags(b->ev[2], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
@@ -890,8 +988,13 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
         S.seed_lo = fresh.seed_lo; S.seed_hi = fresh.seed_hi; S.frame_lo = fresh.frame_lo; S.frame_hi = fresh.frame_hi;
         S.scene = it.scene_id;
         b->hs[k] = S;
-        b->h_stage[slot][k] = S;
         b->items[k] = it;
+    }
+    for (int k = 0; k < n; ++k) {
+        // a sensor keeps its owner's coordinate table only while their fan geometry agrees
+        const int o = b->lut_owner.empty() ? -1 : b->lut_owner[k];
+        b->hs[k].fan_lut = (o >= 0 && same_fan_geometry(b->hs[k], b->hs[o])) ? b->lut_of[k] : nullptr;
+        b->h_stage[slot][k] = b->hs[k];
     }
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(b->d_sens, b->h_stage[slot], sizeof(SensorDev) * n, cudaMemcpyHostToDevice, s),
@@ -1231,8 +1334,9 @@ extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, con
     if (e == cudaSuccess) e = cudaMemsetAsync(nb, 0, sizeof(uint32_t) * node_words, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(tb, 0, sizeof(uint32_t) * tri_words, s);
     TraceCounters tc{cnt, cnt + 1, cnt + 2, nb, tb};
-    Tune t;
-    t.cols = 1;
+    // the tuned warp tiles of this sensor shape: a lane's visits depend a little
+    // on its warp's rays (leaves are parked until the whole warp holds one)
+    const Tune t = tune_for(ctx, *sensor);
     SensorDev S = make_sensor(*sensor, 0, 0, t, 0, 0);
     float4* trig = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&trig, sizeof(float4) * (S.nb + S.ne));

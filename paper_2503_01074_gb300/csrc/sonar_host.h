@@ -40,6 +40,8 @@ int bin_blocks_per_sm(int det, int block, size_t smem);
 constexpr size_t kMaxDynSmem = 200 * 1024;
 cudaError_t launch_norm(const NormArgs& a, cudaStream_t st);
 cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_fan_lut(const FanLutArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_fan_group(const FanGroupArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_adj_rows(const SensorDev* sensors, const int32_t* row_map, const SensorDev& one, int n_sensors,
                             int64_t total_groups, int normalise, const float* noised,
                             const float* grad, RowInfo* info, cudaStream_t st);

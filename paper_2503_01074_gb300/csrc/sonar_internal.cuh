@@ -57,6 +57,7 @@ struct SensorDev {
     int32_t trace_blocks;  // trace: blocks of 4 warp tiles covering the sensor
     int64_t polar_off, hits_off, fan_off, rowmax_off;
     float4* trig;        // float-float sin/cos of the beam azimuths [nb] and elevations [ne]
+    uint4* fan_lut;      // per-pixel fan coordinates shared with same-geometry sensors (nullptr: compute)
 };
 
 // A work unit: the azimuth columns [c0, c1) of one sensor, i.e. every ray
@@ -93,42 +94,82 @@ __device__ __forceinline__ float ord_dec(uint32_t e) {
 // between rounds.
 struct U4 { uint32_t x, y, z, w; };
 
-__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+// The ten round keys of one Philox key (k_r = k + r * Weyl increment),
+// computed once per key so that a round is two wide multiplies and two XORs.
+struct PhiloxKey {
+    uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKey philox_key(uint32_t lo, uint32_t hi) {
+    PhiloxKey K;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = lo + (uint32_t)r * 0x9E3779B9u;
+        K.k1[r] = hi + (uint32_t)r * 0xBB67AE85u;
+        // opaque to the compiler: kept in registers rather than recomputed per use
+        asm volatile("" : "+r"(K.k0[r]), "+r"(K.k1[r]));
+    }
+    return K;
+}
+__device__ __forceinline__ U4 philox10(U4 c, const PhiloxKey& K) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         // one 32x32 -> 64-bit product gives both halves
         const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.k1[r],
+               (uint32_t)p0};
     }
     return c;
 }
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) { return philox10(c, philox_key(k0, k1)); }
 
-// -2 ln u for u = (x + 1) / 2^32, accurate for u near 0 and near 1.
+// -2 ln u for u = (x + 1) / 2^32, without branches.  With u = 2^e f and f in
+// [sqrt(1/2), sqrt(2)), ln u = e ln 2 + 2 atanh(z), z = (f - 1) / (f + 1),
+// |z| <= 3 - 2 sqrt(2) < 0.1716, and 2 atanh(z) = 2 z (1 + z^2/3 + ... +
+// z^10/11) to well below FP32 rounding (the next term is < 2^-33 relative).
+// For u >= sqrt(1/2) (e = 0), f - 1 = -(2^32 - 1 - x) / 2^32 is taken from the
+// integer complement, so u close to 1 keeps its relative accuracy.
 __device__ __forceinline__ float neg2log_u(uint32_t x) {
-    if (x < 0x80000000u) {
-        return -2.0f * logf(fmaf((float)x, 0x1p-32f, 0x1p-32f));
-    }
-    // u = 1 - (2^32 - 1 - x) / 2^32: log1p keeps the small offset exact
-    return -2.0f * log1pf(-(float)(0xFFFFFFFFu - x) * 0x1p-32f);
+    const bool upper = x >= 0xB504F333u;   // (x + 1) / 2^32 >= sqrt(1/2)
+    const float u = fmaf((float)x, 0x1p-32f, 0x1p-32f);
+    const uint32_t bits = __float_as_uint(u);
+    float f = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);   // mantissa in [1, 2)
+    int e = (int)(bits >> 23) - 127;
+    const bool fold = f > 1.41421356f;
+    f = fold ? 0.5f * f : f;
+    e = fold ? e + 1 : e;
+    float d = f - 1.0f;                                                // exact
+    d = upper ? -(float)(0xFFFFFFFFu - x) * 0x1p-32f : d;
+    e = upper ? 0 : e;
+    const float z = __fdividef(d, 2.0f + d);
+    const float z2 = z * z;
+    float p = fmaf(z2, 1.0f / 11.0f, 1.0f / 9.0f);
+    p = fmaf(z2, p, 1.0f / 7.0f);
+    p = fmaf(z2, p, 1.0f / 5.0f);
+    p = fmaf(z2, p, 1.0f / 3.0f);
+    p = fmaf(z2, p, 1.0f);
+    // e in [-32, 0]: exact as a float without a conversion instruction
+    const float ef = __uint_as_float(0x4B000000u | (uint32_t)(e + 64)) - 8388672.0f;
+    return -2.0f * fmaf(ef, 0.693147180559945f, 2.0f * z * p);
 }
+
+// sqrt(v) for v >= 0 from the reciprocal square root (a few ulp).
+__device__ __forceinline__ float sqrt_nonneg(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
 
 // Per-bin noise draws: counter (bin, frame lo, 0, frame hi), key = seed.
 // Word 0 -> Rayleigh(sigma_sa) by inversion; words 1, 2 -> the cosine branch
 // of Box-Muller for N(0, sigma_sm); word 3 unused.
-__device__ __forceinline__ void bin_noise(uint32_t bin, const SensorDev& s, float sigma_sa,
-                                          float sigma_sm, float& w_sa, float& w_sm) {
-    const U4 x = philox10(U4{bin, s.frame_lo, 0u, s.frame_hi}, s.seed_lo, s.seed_hi);
-    w_sa = sigma_sa * sqrtf(neg2log_u(x.x));
-    const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);
-    w_sm = sigma_sm * sqrtf(neg2log_u(x.y)) * cospif(2.0f * u2);
+__device__ __forceinline__ U4 bin_draws(uint32_t bin, const SensorDev& s, const PhiloxKey& K) {
+    return philox10(U4{bin, s.frame_lo, 0u, s.frame_hi}, K);
 }
-
-__device__ __forceinline__ float w_sm_of(uint32_t bin, const SensorDev& s, float sigma_sm) {
-    const U4 x = philox10(U4{bin, s.frame_lo, 0u, s.frame_hi}, s.seed_lo, s.seed_hi);
+__device__ __forceinline__ float rayleigh_of(const U4& x, float sigma_sa) {
+    return sigma_sa * sqrt_nonneg(neg2log_u(x.x));
+}
+__device__ __forceinline__ float gauss_of(const U4& x, float sigma_sm) {
     const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);
-    return sigma_sm * sqrtf(neg2log_u(x.y)) * cospif(2.0f * u2);
+    return sigma_sm * sqrt_nonneg(neg2log_u(x.y)) * cospif(2.0f * u2);
+}
+__device__ __forceinline__ float w_sm_of(uint32_t bin, const SensorDev& s, float sigma_sm, const PhiloxKey& K) {
+    return gauss_of(bin_draws(bin, s, K), sigma_sm);
 }
 
 // ---- kernel argument blocks ----
@@ -150,8 +191,9 @@ struct TraceArgs {
     SensorDev one;
     SceneDev one_scene;
     sonar_params params;
-    sonar_hit* hits;            // always written (the caller's buffer or scratch)
+    sonar_hit* hits;            // written unless counting (the caller's buffer or scratch)
     uint32_t* err;
+    TraceCounters tc;           // counting launches only
 };
 
 // Binning and noise over column-tile work units.
@@ -187,6 +229,11 @@ struct NormArgs {
 };
 
 constexpr int kFanTile = 4096;  // fan pixels per block
+constexpr int kFanSide = 64;    // resample blocks are kFanSide x kFanSide pixel squares (compact in polar)
+// Square resample blocks of a w x h fan image.
+__host__ __device__ inline int32_t fan_squares(int32_t w, int32_t h) {
+    return ((w + kFanSide - 1) / kFanSide) * ((h + kFanSide - 1) / kFanSide);
+}
 
 // Fan resample: blocks of kFanTile pixels of one sensor, reading the normalised image.
 struct FanArgs {
@@ -196,6 +243,24 @@ struct FanArgs {
     SensorDev one;
     const float* polar;
     float* fan;
+};
+
+// Fan of the users of a shared coordinate table: per block (owner, block of
+// its pixels, users members[m0 .. m1)); one thread serves up to kFanGroup frames.
+constexpr int kFanGroup = 8;
+struct FanGroupArgs {
+    const SensorDev* sensors;
+    const int4* block_map;
+    const int32_t* members;
+    const float* polar;
+    float* fan;
+};
+
+// Fan coordinate tables: per table block (owner sensor, block of its pixels).
+struct FanLutArgs {
+    const SensorDev* sensors;
+    const int2* block_map;
+    uint4* const* luts;         // per owner sensor: its table
 };
 
 // A work unit of the adjoint: canonical rays [r0, r1) of one sensor.

@@ -280,6 +280,50 @@ def test_batch_equals_single_renders(son, tiny, tiny_sid):
     b.close()
 
 
+def test_batch_shared_fan_tables(son, tiny, tiny_sid):
+    """Frames with one fan geometry share a coordinate table (11 frames: two
+    runs of users); a frame whose geometry changes leaves it, and when the
+    owner's changes the others stop matching it.  Every fan stays bitwise equal
+    to a single render's."""
+    mesh, mu = tiny
+    theta = son.theta(0.05, 1.0, mu)
+    prm = RenderParams()
+    base = S.sensor_tiny(40.0)
+    base.fan_w, base.fan_h = 160, 96
+    items = [(tiny_sid, base.replace_pose((0.2 * k, 0.1 * k, 0.0), S.pose_matrix(0.05 * k, math.radians(40.0))),
+              5, k) for k in range(11)]
+    b = son.batch(items)
+
+    def check(its):
+        b.render(theta, prm, fan=True)
+        torch.cuda.synchronize()
+        for k, (sid, spec, seed, frame) in enumerate(its):
+            one = son.render(sid, spec, theta, prm, seed, frame, fan=True)
+            v = b.view(k)
+            assert torch.equal(one["polar"], v["polar"]), k
+            assert torch.equal(one["fan"], v["fan"]), k
+            assert float(v["fan"].abs().sum()) > 0.0, k
+
+    check(items)
+    moved = list(items)
+    sid, spec, seed, frame = moved[3]
+    s3 = spec.replace_pose(spec.pos, spec.rot)
+    s3.hfov = spec.hfov * 0.9
+    moved[3] = (sid, s3, seed, frame)
+    b.update(moved)
+    check(moved)
+    sid, spec, seed, frame = moved[0]
+    s0 = spec.replace_pose(spec.pos, spec.rot)
+    s0.r_max = spec.r_max * 1.1
+    moved[0] = (sid, s0, seed, frame)
+    b.update(moved)
+    check(moved)
+    b.update(items)
+    check(items)
+    assert b.info()["graphs"] == 1
+    b.close()
+
+
 def test_batch_backward_equals_sum_of_singles(son, tiny, tiny_sid):
     mesh, mu = tiny
     items = batch_items(son, tiny, tiny_sid)
