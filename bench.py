@@ -377,11 +377,21 @@ def measure_configs(son, steps):
     return out
 
 
+RAY_CAST_SOURCES = ("paper_2503_01074_gb300/csrc/render.cu", "paper_2503_01074_gb300/csrc/sonar_internal.cuh")
+
+
+def ray_cast_sources_sha():
+    h = hashlib.sha256()
+    for rel in RAY_CAST_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile():
-    """Per-frame DRAM bytes of the trace/bin/noise kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    """Per-frame DRAM bytes (read + write) of the ray-cast kernel from the
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None: the counters no longer describe the kernel)."""
     path = os.path.join(ROOT, "profiles", "k_trace_dram.txt")
-    src = os.path.join(ROOT, "paper_2503_01074_gb300", "csrc", "render.cu")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -389,8 +399,7 @@ def traffic_from_profile():
         if ":" in line:
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("render_cu_sha256_16") != sha or "dram_bytes_per_frame" not in kv:
+    if kv.get("ray_cast_sources_sha256_16") != ray_cast_sources_sha() or "dram_bytes_per_frame" not in kv:
         return None
     return float(kv["dram_bytes_per_frame"])
 

@@ -263,10 +263,11 @@ __device__ __forceinline__ float small_u2f(uint32_t v) {
 // trace: one ray per thread, hit record out
 // ---------------------------------------------------------------------------
 
-// Each block covers a tile of 4 * tb beams x (32 / tb) elevations of one
-// sensor; lane l of warp w traces beam i0 + w * tb + l % tb, elevation
-// j0 + l / tb, so that a warp's rays sample a compact patch of the field of
-// view.  Records go to their canonical index i * n_elev + j.
+// Each block is one warp on a tile of tb beams x (32 / tb) elevations of one
+// sensor: lane l traces beam i0 + l % tb, elevation j0 + l / tb, so that the
+// warp's rays sample a compact patch of the field of view.  (One-warp blocks
+// free their slot as soon as their rays are done.)  Records go to their
+// canonical index i * n_elev + j.
 //
 // The walk over the 4-wide hierarchy is a while-while loop: a lane descends
 // nearest child first, pushing the other entered children; a lane that
@@ -276,7 +277,7 @@ __device__ __forceinline__ float small_u2f(uint32_t v) {
 // With STATS the kernel also counts node visits and triangle tests and marks
 // the nodes and triangles it touches (records are then not written).
 template <int MINB, bool STATS>
-__global__ void __launch_bounds__(128, MINB) k_trace(TraceArgs a) {
+__global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
     __shared__ int s_tile;
@@ -294,11 +295,10 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceArgs a) {
     }
     __syncthreads();
     const int tb = S.tb, te = 32 / S.tb;
-    const int bb = 4 * tb;
-    const int tiles_b = (S.nb + bb - 1) / bb;
+    const int tiles_b = (S.nb + tb - 1) / tb;
     const int ty = s_tile / tiles_b, tx = s_tile - ty * tiles_b;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ri = tx * bb + warp * tb + (lane % tb);
+    const int lane = threadIdx.x;
+    const int ri = tx * tb + (lane % tb);
     const int rj = ty * te + lane / tb;
     const SceneDev& sc = SC;
     const sonar_params& p = a.params;
@@ -1102,8 +1102,8 @@ cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_se
 
 cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st) {
     if (blocks > 0) {
-        if (occupancy >= 8) k_trace<8, false><<<blocks, 128, 0, st>>>(a);
-        else k_trace<1, false><<<blocks, 128, 0, st>>>(a);
+        if (occupancy >= 8) k_trace<32, false><<<blocks, 32, 0, st>>>(a);
+        else k_trace<4, false><<<blocks, 32, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1179,7 +1179,7 @@ cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_par
     a.params = p;
     a.err = err;
     a.tc = tc;
-    if (s.trace_blocks > 0) k_trace<1, true><<<s.trace_blocks, 128, 0, st>>>(a);
+    if (s.trace_blocks > 0) k_trace<4, true><<<s.trace_blocks, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -184,8 +184,8 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     const int tb = (t.tb >= 1 && t.tb <= 32 && (t.tb & (t.tb - 1)) == 0) ? t.tb : 8;   // beams per warp tile
     d.tb = tb;
     d.occ = t.occ;
-    const int64_t bb = 4 * tb, be = 32 / tb;
-    d.trace_blocks = (int32_t)(((s.n_beams + bb - 1) / bb) * ((s.n_elev + be - 1) / be));
+    const int64_t be = 32 / tb;   // ray-cast blocks: one warp on tb beams x be elevations
+    d.trace_blocks = (int32_t)(((s.n_beams + tb - 1) / tb) * ((s.n_elev + be - 1) / be));
     return d;
 }
 

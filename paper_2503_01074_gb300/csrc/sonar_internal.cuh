@@ -182,7 +182,7 @@ struct TraceCounters {
     uint32_t* tri_bits;             // touched triangles (bitmap)
 };
 
-// Ray casting: blocks of 128 rays.
+// Ray casting: one-warp blocks of 32 rays.
 struct TraceArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
     const SceneDev* scenes;     // batch: device table; single: nullptr (use `one_scene`)
