@@ -96,10 +96,15 @@ __global__ void k_morton(const float* verts, const int32_t* tris, int64_t nt, co
                  r = load_v(verts, tris[3 * t + 2]);
     const float c[3] = {(p.x + q.x + r.x) * (1.0f / 3.0f), (p.y + q.y + r.y) * (1.0f / 3.0f),
                         (p.z + q.z + r.z) * (1.0f / 3.0f)};
+    // one scale for all axes (the largest extent): a flat scene (a seabed is
+    // ~100 m wide and a few m high) then splits across its width first and in
+    // height only at fine levels; per-axis scaling split it in height as early
+    // as in x and y, into wide overlapping boxes (+30 % node visits per ray)
     uint32_t g[3];
+    float ext = 0.0f;
+    for (int a = 0; a < 3; ++a) ext = fmaxf(ext, ord_dec(st->hi[a]) - ord_dec(st->lo[a]));
     for (int a = 0; a < 3; ++a) {
-        const float lo = ord_dec(st->lo[a]), hi = ord_dec(st->hi[a]);
-        const float ext = hi - lo;
+        const float lo = ord_dec(st->lo[a]);
         float u = ext > 0.0f ? (c[a] - lo) / ext : 0.0f;
         u = fminf(fmaxf(u, 0.0f), 1.0f);
         g[a] = (uint32_t)fminf(u * 2097152.0f, 2097151.0f);    // 21 bits

@@ -951,13 +951,16 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
 // Deterministic: each unit's sums go to its own row of `partials` (material
 // sums per warp in lane order, warp slabs added in warp order, alpha/gain per
 // thread then in a fixed tree); k_adj_final adds the rows in a fixed order.
+// A unit holds a few hundred rays: its sums are FP32 (float-float across
+// lanes), its row of partials FP64.
 __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
-    extern __shared__ double slab[];   // [n_warps][n_mat]
+    extern __shared__ double slab_d[];   // [n_warps][n_mat] (FP32 sums; sized in doubles by the host)
+    float* slab = reinterpret_cast<float*>(slab_d);
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
     __shared__ AdjUnit U;
     __shared__ int s_unit;
-    __shared__ double s_ag[2][32];
+    __shared__ ff s_ag[2][32];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int nm = a.n_mat, nq = nm + 2;
@@ -987,7 +990,7 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
                 U.r1 = min(U.r0 + a.chunk, a.one.nb * a.one.ne);
             }
         }
-        for (int k = tid; k < nw * nm; k += nt) slab[k] = 0.0;
+        for (int k = tid; k < nw * nm; k += nt) slab[k] = 0.0f;
         __syncthreads();
         const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
         float acc_a = 0.0f, acc_g = 0.0f;
@@ -1027,27 +1030,27 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
             if (valid) {
                 float sum = 0.0f;
                 for (uint32_t m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v_mu, __ffs(m) - 1);
-                if (lane == __ffs(peers) - 1) slab[warp * nm + mat] += (double)sum;
+                if (lane == __ffs(peers) - 1) slab[warp * nm + mat] += sum;
             }
         }
-        double da = acc_a, dg = acc_g;
+        ff da{acc_a, 0.0f}, dg{acc_g, 0.0f};
         for (int o = 16; o; o >>= 1) {
-            da += __shfl_down_sync(0xFFFFFFFFu, da, o);
-            dg += __shfl_down_sync(0xFFFFFFFFu, dg, o);
+            da = ff_add(da, ff{__shfl_down_sync(0xFFFFFFFFu, da.hi, o), __shfl_down_sync(0xFFFFFFFFu, da.lo, o)});
+            dg = ff_add(dg, ff{__shfl_down_sync(0xFFFFFFFFu, dg.hi, o), __shfl_down_sync(0xFFFFFFFFu, dg.lo, o)});
         }
         if (lane == 0) { s_ag[0][warp] = da; s_ag[1][warp] = dg; }
         __syncthreads();
         double* out = a.partials + (int64_t)u * nq;
         for (int m = tid; m < nm; m += nt) {
-            double v = 0.0;
-            for (int w = 0; w < nw; ++w) v += slab[w * nm + m];
-            out[2 + m] = v;
+            ff v{0.0f, 0.0f};
+            for (int w = 0; w < nw; ++w) v = ff_add(v, ff{slab[w * nm + m], 0.0f});
+            out[2 + m] = (double)v.hi + (double)v.lo;
         }
         if (tid == 0) {
-            double va = 0.0, vg = 0.0;
-            for (int w = 0; w < nw; ++w) { va += s_ag[0][w]; vg += s_ag[1][w]; }
-            out[0] = va;
-            out[1] = vg;
+            ff va{0.0f, 0.0f}, vg{0.0f, 0.0f};
+            for (int w = 0; w < nw; ++w) { va = ff_add(va, s_ag[0][w]); vg = ff_add(vg, s_ag[1][w]); }
+            out[0] = (double)va.hi + (double)va.lo;
+            out[1] = (double)vg.hi + (double)vg.lo;
         }
         __syncthreads();
     }
