@@ -7,14 +7,18 @@
 //   4. Karras hierarchy               one thread per internal node (Karras, HPG 2012)
 //   5. bottom-up refit                leaf-to-root climb, second visitor merges boxes
 //   6. packing                        runs of <= kLeafMax triangles collapsed into
-//                                     leaves; binary child pairs collapsed into
-//                                     4-wide 128-byte nodes; 48-byte triangles
+//                                     leaves; 48-byte triangles
+//   7. 4-wide collapse                top-down, one 4-wide level per pass: a node
+//                                     opens its largest-area internal child until
+//                                     it has four children; 128-byte SoA nodes in
+//                                     breadth-first order
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "sonar_internal.cuh"
 #include "sonar_host.h"
@@ -390,52 +394,90 @@ __global__ void k_pack_tris(const float* verts, const int32_t* tris, const int32
     mat_orig[o] = m;
 }
 
-// 4-wide nodes: the binary nodes kept are the reachable ones (covering more
-// than kLeafMax triangles, so not inside a collapsed leaf) at even depth; each
-// takes its grandchildren in place of its internal children.
-__global__ void k_node4_flags(int64_t n, const int32_t* parent, const int2* range, uint32_t* flag) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n - 1) return;
-    int depth = 0;
-    for (int32_t q = parent[p]; q >= 0; q = parent[q]) ++depth;
-    const int2 r = range[p];
-    flag[p] = (r.y - r.x + 1 > kLeafMax && (depth & 1) == 0) ? 1u : 0u;
+// ---- greedy 4-wide collapse (top-down, one level of the 4-wide tree per pass) ----
+// A child under construction is a side of a binary node: x = 2 * p + side, its
+// box and handle at pairs[2 x] (lo, handle bits) and pairs[2 x + 1] (hi).
+
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
 }
 
-__global__ void k_pack4(int64_t n, const float4* pairs, const uint32_t* flag, const uint32_t* index,
-                        float4* nodes4) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n - 1 || !flag[p]) return;
-    float lo[3][4], hi[3][4];
-    int32_t h[4];
-    int k = 0;
-    for (int side = 0; side < 2; ++side) {
-        const float4 a = pairs[4 * p + 2 * side], b = pairs[4 * p + 2 * side + 1];
-        const int32_t c = __float_as_int(a.w);
-        if (c >= 0) {
-            for (int s2 = 0; s2 < 2; ++s2) {
-                const float4 a2 = pairs[4 * (int64_t)c + 2 * s2], b2 = pairs[4 * (int64_t)c + 2 * s2 + 1];
-                const int32_t g = __float_as_int(a2.w);
-                lo[0][k] = a2.x; lo[1][k] = a2.y; lo[2][k] = a2.z;
-                hi[0][k] = b2.x; hi[1][k] = b2.y; hi[2][k] = b2.z;
-                h[k++] = g >= 0 ? (int32_t)index[g] : g;
-            }
-        } else {
-            lo[0][k] = a.x; lo[1][k] = a.y; lo[2][k] = a.z;
-            hi[0][k] = b.x; hi[1][k] = b.y; hi[2][k] = b.z;
-            h[k++] = c;
+// The children of entry e (internal binary node q[e]): start from its two
+// sides; while there are fewer than four and one of them is internal, replace
+// the internal child with the largest surface area by its two sides.
+__global__ void k_collapse_pick(const int32_t* q, int64_t nq, const float4* pairs, int32_t* picks,
+                                uint32_t* nint) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nq) return;
+    const int32_t p = q[e];
+    int32_t c[4] = {2 * p, 2 * p + 1, -1, -1};
+    int cnt = 2;
+    while (cnt < 4) {
+        int best = -1;
+        float best_a = -1.0f;
+        for (int k = 0; k < cnt; ++k) {
+            const float4 lo = pairs[2 * (int64_t)c[k]];
+            if (__float_as_int(lo.w) < 0) continue;   // a leaf
+            const float a = half_area(lo, pairs[2 * (int64_t)c[k] + 1]);
+            if (a > best_a) { best_a = a; best = k; }
         }
+        if (best < 0) break;
+        const int32_t h = __float_as_int(pairs[2 * (int64_t)c[best]].w);
+        c[best] = 2 * h;
+        c[cnt++] = 2 * h + 1;
     }
-    for (; k < 4; ++k) {   // empty slot: a box no ray enters
-        for (int a = 0; a < 3; ++a) lo[a][k] = hi[a][k] = __int_as_float(0x7F800000);
-        h[k] = kEmpty;
+    uint32_t ni = 0;
+    for (int k = 0; k < 4; ++k) {
+        picks[4 * e + k] = c[k];
+        if (c[k] >= 0 && __float_as_int(pairs[2 * (int64_t)c[k]].w) >= 0) ++ni;
     }
-    float4* o = nodes4 + 8 * (int64_t)index[p];
+    nint[e] = ni;
+}
+
+// The next level's entries: the internal children, in entry and slot order.
+__global__ void k_collapse_enqueue(const int32_t* picks, const uint32_t* prefix, int64_t nq, const float4* pairs,
+                                   int32_t* q_next) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nq) return;
+    uint32_t r = prefix[e];
+    for (int k = 0; k < 4; ++k) {
+        const int32_t x = picks[4 * e + k];
+        if (x < 0) continue;
+        const int32_t h = __float_as_int(pairs[2 * (int64_t)x].w);
+        if (h >= 0) q_next[r++] = h;
+    }
+}
+
+// Writes the 4-wide nodes of one level: entry e is node base + e; its r-th
+// internal child is node base_next + prefix[e] + r.  Empty slots hold an
+// inverted box that no ray enters and the empty handle.
+__global__ void k_collapse_write(const int32_t* picks, const uint32_t* prefix, int64_t nq, int64_t base,
+                                 int64_t base_next, const float4* pairs, float4* nodes4) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nq) return;
+    float lo[3][4], hi[3][4];
+    int32_t hh[4];
+    uint32_t r = prefix[e];
+    for (int k = 0; k < 4; ++k) {
+        const int32_t x = picks[4 * e + k];
+        if (x < 0) {
+            for (int a = 0; a < 3; ++a) lo[a][k] = hi[a][k] = __int_as_float(0x7F800000);
+            hh[k] = kEmpty;
+            continue;
+        }
+        const float4 l = pairs[2 * (int64_t)x], h = pairs[2 * (int64_t)x + 1];
+        lo[0][k] = l.x; lo[1][k] = l.y; lo[2][k] = l.z;
+        hi[0][k] = h.x; hi[1][k] = h.y; hi[2][k] = h.z;
+        const int32_t c = __float_as_int(l.w);
+        hh[k] = c >= 0 ? (int32_t)(base_next + r++) : c;
+    }
+    float4* o = nodes4 + 8 * (base + e);
     for (int a = 0; a < 3; ++a) {
         o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
         o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
     }
-    o[6] = make_float4(__int_as_float(h[0]), __int_as_float(h[1]), __int_as_float(h[2]), __int_as_float(h[3]));
+    o[6] = make_float4(__int_as_float(hh[0]), __int_as_float(hh[1]), __int_as_float(hh[2]), __int_as_float(hh[3]));
     o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
@@ -554,7 +596,7 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
     out->bytes = sizeof(float4) * 3 * n + sizeof(int32_t) * n;
 
     k_pack_tris<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, mat, v0, n, tri_out, mat_orig);
-    int height = 0;
+    int height = 0, depth4 = 0;
     if (n <= kLeafMax) {
         out->root = leaf_handle(0, (int32_t)n);
         if (n > 1) {
@@ -565,9 +607,12 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
         }
     } else {
         float4* pairs = S.get<float4>(4 * (n - 1));
-        uint32_t* flag = S.get<uint32_t>(n);
-        uint32_t* index = S.get<uint32_t>(n);
-        const int64_t fchunks = (n - 1 + kScanChunk - 1) / kScanChunk;
+        int32_t* qa = S.get<int32_t>(n);
+        int32_t* qb = S.get<int32_t>(n);
+        int32_t* picks = S.get<int32_t>(4 * n);
+        uint32_t* nint = S.get<uint32_t>(n);
+        uint32_t* prefix = S.get<uint32_t>(n);
+        const int64_t fchunks = (n + kScanChunk - 1) / kScanChunk;
         uint32_t* fsums = S.get<uint32_t>(fchunks);
         if (S.err != cudaSuccess) { *msg = "out of device memory (build scratch)"; return SONAR_ERR_OOM; }
         k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(k0, n, child, parent, range);
@@ -576,19 +621,38 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
                                                                blo, bhi);
         k_pack_nodes<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, range,
                                                                         blo, bhi, pad, pairs);
-        k_node4_flags<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(n, parent, range, flag);
-        k_scan_sums<<<(unsigned)fchunks, kThreads, 0, st>>>(flag, n - 1, fsums);
-        k_scan_top<<<1, 1024, 0, st>>>(fsums, fchunks);
-        k_scan_apply<<<(unsigned)fchunks, kThreads, 0, st>>>(flag, n - 1, fsums, index);
-        uint32_t last[2] = {0, 0};
+        // greedy collapse, level by level: picks and prefixes of all levels are
+        // kept (indexed by 4-wide node), nodes written once their count is known
         float4 root_hi;
-        e = cudaMemcpyAsync(&last[0], index + (n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&last[1], flag + (n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
+        const int32_t zero = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(qa, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
+        std::vector<int64_t> lbase, lcount;
+        int64_t base = 0, nq = 1;
+        while (e == cudaSuccess && nq > 0) {
+            if (base + nq > n) { e = cudaErrorInvalidValue; break; }   // cannot happen: nodes are distinct
+            lbase.push_back(base);
+            lcount.push_back(nq);
+            const int64_t ch = (nq + kScanChunk - 1) / kScanChunk;
+            k_collapse_pick<<<blocks_for(nq, kThreads), kThreads, 0, st>>>(qa, nq, pairs, picks + 4 * base,
+                                                                            nint + base);
+            k_scan_sums<<<(unsigned)ch, kThreads, 0, st>>>(nint + base, nq, fsums);
+            k_scan_top<<<1, 1024, 0, st>>>(fsums, ch);
+            k_scan_apply<<<(unsigned)ch, kThreads, 0, st>>>(nint + base, nq, fsums, prefix + base);
+            k_collapse_enqueue<<<blocks_for(nq, kThreads), kThreads, 0, st>>>(picks + 4 * base, prefix + base, nq,
+                                                                               pairs, qb);
+            uint32_t last[2] = {0, 0};
+            e = cudaMemcpyAsync(&last[0], prefix + base + nq - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&last[1], nint + base + nq - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            base += nq;
+            nq = (int64_t)last[0] + last[1];
+            int32_t* t = qa; qa = qb; qb = t;
+        }
         if (e != cudaSuccess) { *msg = std::string("build failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
         memcpy(&height, &root_hi.w, 4);
-        const int64_t n4 = (int64_t)last[0] + last[1];
+        const int64_t n4 = base;
         float4* nodes = nullptr;
         if (cudaMalloc(&nodes, sizeof(float4) * 8 * std::max<int64_t>(n4, 1)) != cudaSuccess) {
             *msg = "out of device memory (scene nodes)";
@@ -597,16 +661,21 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
         out->nodes = nodes;
         out->n_pairs = n4;
         out->bytes += sizeof(float4) * 8 * n4;
-        k_pack4<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(n, pairs, flag, index, nodes);
+        for (size_t L = 0; L < lbase.size(); ++L) {
+            const int64_t nxt = L + 1 < lbase.size() ? lbase[L + 1] : n4;
+            k_collapse_write<<<blocks_for(lcount[L], kThreads), kThreads, 0, st>>>(
+                picks + 4 * lbase[L], prefix + lbase[L], lcount[L], lbase[L], nxt, pairs, nodes);
+        }
+        depth4 = (int)lbase.size();
         out->root = 0;
     }
     out->height = height;
     e = cudaGetLastError();
     if (e != cudaSuccess) { *msg = std::string("build kernel launch failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
-    // a 4-wide node sits on every second binary level and pushes at most three
-    // children: the walk never needs more than 3 * ceil(height / 2) + 1 entries
-    if (3 * ((height + 1) / 2) + 1 > kStackMax) {
-        *msg = "hierarchy too deep for the traversal stack (height " + std::to_string(height) + ")";
+    // a visit pushes at most three children, one visit per level of the 4-wide
+    // tree on any path: the walk never needs more than 3 * depth + 1 entries
+    if (3 * depth4 + 1 > kStackMax) {
+        *msg = "hierarchy too deep for the traversal stack (4-wide depth " + std::to_string(depth4) + ")";
         return SONAR_ERR_ARG;
     }
     return SONAR_OK;
