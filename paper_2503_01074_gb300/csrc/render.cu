@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
     __shared__ int s_unit, s_count;
     __shared__ float s_red[32];
     __shared__ float s_pat[kMaxCols];
+    __shared__ int s_b0[kMaxCols + 1];   // per-beam fold: first local beam of each column
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
@@ -521,10 +522,52 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         const int i0 = first_beam_of_col(U.c0, S.nb, S.naz), i1 = first_beam_of_col(U.c1, S.nb, S.naz);
         const int64_t r0 = (int64_t)i0 * S.ne, r1 = (int64_t)i1 * S.ne;
         const int nbin = S.nr * cw;
-        for (int k = tid; k < nbin; k += nt) acc[k] = 0.0f;
-        __syncthreads();
         const sonar_hit* H = a.hits + S.hits_off;
-        for (int64_t base = r0; base < r1; base += nt) {
+        // Deterministic fold, per-beam form: warp w owns beams w, w + nw, ... of the
+        // unit and folds each beam's rays in elevation order into that beam's own
+        // row accumulator (one writer: no barriers); a bin then adds its column's
+        // beams in beam order.  With one beam per column this is exactly the
+        // sequential canonical-order fold.
+        const int nbeam = i1 - i0;
+        const bool per_beam = DET && S.fold_beams;
+        float* accb = acc + nbin;
+        int* list = reinterpret_cast<int*>(acc + nbin + (per_beam ? nbeam * S.nr : 0));
+        if (per_beam) {
+            for (int k = tid; k < nbeam * S.nr; k += nt) accb[k] = 0.0f;
+            for (int c = tid; c <= cw; c += nt) s_b0[c] = first_beam_of_col(U.c0 + c, S.nb, S.naz) - i0;
+        } else {
+            for (int k = tid; k < nbin; k += nt) acc[k] = 0.0f;
+        }
+        __syncthreads();
+        if (per_beam) {
+            for (int bb = warp; bb < nbeam; bb += nw) {
+                const sonar_hit* Hb = H + (int64_t)(i0 + bb) * S.ne;
+                float* racc = accb + bb * S.nr;
+                for (int jb = 0; jb < S.ne; jb += 32) {
+                    const int j = jb + lane;
+                    uint32_t row = kNoKey;
+                    float score = 0.0f;
+                    if (j < S.ne) {
+                        const uint4 h = __ldg(reinterpret_cast<const uint4*>(Hb + j));
+                        if (h.x != kNoKey) {
+                            row = h.x / (uint32_t)S.naz;
+                            int m = SC.mat_orig[h.y];
+                            m = m < a.n_mat ? m : a.n_mat - 1;
+                            score = __ldg(a.theta + 2 + m) * __uint_as_float(h.w) *
+                                    expf(-2.0f * alpha * __uint_as_float(h.z)) * gain;
+                        }
+                    }
+                    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, row);
+                    if (row != kNoKey) {
+                        const int leader = __ffs(peers) - 1;
+                        float v = lane == leader ? racc[row] : 0.0f;
+                        for (uint32_t m = peers; m; m &= m - 1) v += __shfl_sync(peers, score, __ffs(m) - 1);
+                        if (lane == leader) racc[row] = v;
+                    }
+                }
+            }
+        }
+        for (int64_t base = r0; base < (per_beam ? r0 : r1); base += nt) {
             const int64_t r = base + tid;
             uint32_t lkey = kNoKey;
             float score = 0.0f;
@@ -572,7 +615,6 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         const float inv_rmax2 = 1.0f / (S.rmax * S.rmax);
         const float inv_sphi = 1.0f / a.params.sigma_phi;
         const float sig_sa = a.params.sigma_sa, sig_sm = a.params.sigma_sm;
-        int* list = reinterpret_cast<int*>(acc + nbin);
         for (int c = tid; c < cw; c += nt) {
             const float pc = fmaf(small_u2f(U.c0 + c) + 0.5f, da, -0.5f * S.hfov);
             s_pat[c] = 0.5f * expf(-pc * pc * inv_sphi);
@@ -584,13 +626,20 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
         for (int k = tid; k < nbin; k += nt) {
             const uint32_t b = (uint32_t)(row * S.naz + U.c0 + col);
-            const float P = acc[k];
+            float P;
+            if (per_beam) {
+                P = 0.0f;
+                for (int bb = s_b0[col]; bb < s_b0[col + 1]; ++bb) P += accb[bb * S.nr + row];
+            } else {
+                P = acc[k];
+            }
             const U4 x = bin_draws(b, S, K);
             const float w_sa = rayleigh_of(x, sig_sa);
             const float rc = fmaf(small_u2f(row) + 0.5f, dr, S.rmin);
             const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
             if (a.binned) a.binned[S.polar_off + b] = P;
             if (P != 0.0f) {
+                acc[k] = P;
                 list[atomicAdd(&s_count, 1)] = k;
             } else {
                 a.noised[S.polar_off + b] = additive;

@@ -154,6 +154,17 @@ Tune single_tune(const sonar_ctx* ctx, const sonar_sensor& s) {
     return t;
 }
 
+// Most beams a binning unit of this sensor covers (its columns' beams).
+int64_t unit_beams_max(const SensorDev& s) {
+    int64_t most = 0;
+    for (int t = 0; t < s.n_tiles; ++t) {
+        const int64_t c0 = (int64_t)t * s.cols, c1 = std::min<int64_t>(c0 + s.cols, s.naz);
+        most = std::max<int64_t>(most, first_beam_of_col(c1, s.nb, s.naz) - first_beam_of_col(c0, s.nb, s.naz));
+    }
+    return most;
+}
+int64_t unit_rays_max(const SensorDev& s) { return unit_beams_max(s) * (int64_t)s.ne; }
+
 SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, const Tune& t, int fan_w,
                       int fan_h) {
     SensorDev d{};
@@ -186,6 +197,25 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     d.occ = t.occ;
     const int64_t be = 32 / tb;   // ray-cast blocks: one warp on tb beams x be elevations
     d.trace_blocks = (int32_t)(((s.n_beams + tb - 1) / tb) * ((s.n_elev + be - 1) / be));
+    // The per-beam fold when columns hold several beams (n_beams > n_az_bins:
+    // with one beam per column both folds add in the same order, and the
+    // all-warp fold is faster) and its rows fit in shared memory next to the
+    // column block and the list.  The choice depends on the sensor shape alone
+    // (it is made for one column per unit), so every tile shape folds in the
+    // same order; wider units are narrowed until they fit.
+    auto fits = [&](const SensorDev& x) {
+        const int64_t bins = (int64_t)x.nr * x.cols;
+        const int64_t need = bins + unit_beams_max(x) * x.nr + std::min<int64_t>(unit_rays_max(x), bins);
+        return need * (int64_t)sizeof(float) <= (int64_t)kMaxDynSmem;
+    };
+    SensorDev one_col = d;
+    one_col.cols = 1;
+    one_col.n_tiles = s.n_az_bins;
+    d.fold_beams = (s.n_beams > s.n_az_bins && fits(one_col)) ? 1 : 0;
+    while (d.fold_beams && d.cols > 1 && !fits(d)) {
+        d.cols = std::max(1, d.cols / 2);
+        d.n_tiles = (s.n_az_bins + d.cols - 1) / d.cols;
+    }
     return d;
 }
 
@@ -308,22 +338,13 @@ extern "C" sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t id, int64_t ou
 
 namespace {
 
-// Most rays a binning unit of this sensor covers: its columns' beams x elevations.
-int64_t unit_rays_max(const SensorDev& s) {
-    int64_t most = 0;
-    for (int t = 0; t < s.n_tiles; ++t) {
-        const int64_t c0 = (int64_t)t * s.cols, c1 = std::min<int64_t>(c0 + s.cols, s.naz);
-        most = std::max<int64_t>(most, (first_beam_of_col(c1, s.nb, s.naz) - first_beam_of_col(c0, s.nb, s.naz)) *
-                                           (int64_t)s.ne);
-    }
-    return most;
-}
 
 // Shared memory of a binning block: the column block of the unit plus the
 // list of its non-empty bins (no more entries than rays, nor than bins).
 size_t bin_smem(const SensorDev& s) {
     const int64_t bins = (int64_t)s.nr * s.cols;
-    return (size_t)(bins + std::min<int64_t>(unit_rays_max(s), bins)) * sizeof(float);
+    const int64_t beams = s.fold_beams ? unit_beams_max(s) * s.nr : 0;   // per-beam rows of the fold
+    return (size_t)(bins + beams + std::min<int64_t>(unit_rays_max(s), bins)) * sizeof(float);
 }
 
 // Trace, bin and noise of one sensor (polar_off = hits_off = rowmax_off = 0).

@@ -53,8 +53,9 @@ struct SensorDev {
     int32_t cols;        // binning: azimuth columns per work unit
     int32_t n_tiles;     // binning work units of this sensor = ceil(naz / cols)
     int32_t tb;          // trace: beams per warp tile (elevations = 32 / tb)
-    int32_t occ;         // trace: 8 = register budget for 8 blocks of 128 per SM, else none
-    int32_t trace_blocks;  // trace: blocks of 4 warp tiles covering the sensor
+    int32_t occ;         // trace: 8 = register budget for 32 one-warp blocks per SM, else none
+    int32_t trace_blocks;  // trace: one-warp blocks covering the sensor
+    int32_t fold_beams;  // binning: deterministic fold into per-beam rows (fits in shared memory)
     int64_t polar_off, hits_off, fan_off, rowmax_off;
     float4* trig;        // float-float sin/cos of the beam azimuths [nb] and elevations [ne]
     uint4* fan_lut;      // per-pixel fan coordinates shared with same-geometry sensors (nullptr: compute)
