@@ -333,35 +333,37 @@ def measure_configs(son, steps):
     del outs
     for sid in sids:
         son.release(sid)
-    # large: 33.6M triangles, 1024 x 256 rays, 4000 bins, 0.1-60 m; forward + adjoint, hits recomputed
-    t0 = time.perf_counter()
-    mesh, mu, hfn = S.large_scene()
-    gen_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sid = son.upload_mesh(mesh)
-    torch.cuda.synchronize()
-    build_ms = 1000.0 * (time.perf_counter() - t0)
-    base = S.sensor_single(hfn, n_beams=1024, n_elev=256, n_range_bins=4000, r_min=0.1, r_max=60.0,
-                           fan_w=0, fan_h=0)
-    poses = S.trajectory(base, hfn, 256, radius=60.0, seed=7)
-    theta = son.theta(ALPHA, GAIN, mu)
-    b = son.batch([(sid, p, 900 + k, k) for k, p in enumerate(poses)])
-    b.autotune(theta, prm)
-    G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(2)).to(son.device) * 1e-3
-    d = torch.empty_like(theta)
+    # large: 33.6M triangles, 1024 x 256 rays, 4000 bins, 0.1-60 m; forward + adjoint, hits
+    # recomputed; with 64 materials, and with 1024 (the per-material gradient at that scale)
+    for n_mat, name in ((64, "large"), (1024, "large_1024_materials")):
+        t0 = time.perf_counter()
+        mesh, mu, hfn = S.large_scene(n_mat=n_mat)
+        gen_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sid = son.upload_mesh(mesh)
+        torch.cuda.synchronize()
+        build_ms = 1000.0 * (time.perf_counter() - t0)
+        base = S.sensor_single(hfn, n_beams=1024, n_elev=256, n_range_bins=4000, r_min=0.1, r_max=60.0,
+                               fan_w=0, fan_h=0)
+        poses = S.trajectory(base, hfn, 256, radius=60.0, seed=7)
+        theta = son.theta(ALPHA, GAIN, mu)
+        b = son.batch([(sid, p, 900 + k, k) for k, p in enumerate(poses)])
+        b.autotune(theta, prm)
+        G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(2)).to(son.device) * 1e-3
+        d = torch.empty_like(theta)
 
-    def fwd_adj():
-        b.render(theta, prm, hits=False, fan=False)
-        b.backward(theta, prm, G, hits=False, out=d)
-    ms = timed(fwd_adj, max(2, steps // 2), stream)
-    out["large"] = {"tris": mesh.n_tris, "frames": len(poses), "rays_per_frame": base.n_rays,
-                    "fwd_adj_recompute_fps": len(poses) / ms * 1e3,
-                    "Mrays_s": len(poses) * base.n_rays / ms / 1e3, "scene_build_ms": build_ms,
-                    "scene_generation_s": gen_s, "phase_ms": b.timings()}
-    b.close()
-    son.release(sid)
-    del mesh
+        def fwd_adj():
+            b.render(theta, prm, hits=False, fan=False)
+            b.backward(theta, prm, G, hits=False, out=d)
+        ms = timed(fwd_adj, max(2, steps // 2), stream)
+        out[name] = {"tris": mesh.n_tris, "materials": n_mat, "frames": len(poses), "rays_per_frame": base.n_rays,
+                     "fwd_adj_recompute_fps": len(poses) / ms * 1e3,
+                     "Mrays_s": len(poses) * base.n_rays / ms / 1e3, "scene_build_ms": build_ms,
+                     "scene_generation_s": gen_s, "phase_ms": b.timings()}
+        b.close()
+        son.release(sid)
+        del mesh
     # dense rays: 3000 x 460 rays into 350 x 220 bins
     mesh, mu, hfn = S.single_frame_scene()
     sid = son.upload_mesh(mesh)

@@ -11,6 +11,9 @@ batched graph-replayed launch like the bench's:
   large           a 4096^2-cell (33.6M-triangle) seabed, 1024 x 256 rays,
                   4000 range bins, 0.1-60 m: sampled rays and a complete column
                   against the oracle, the adjoint with recomputed hits;
+  large, 1024     the large scene with 1024 materials: the adjoint on a
+  materials       complete column against the oracle, zero gradient for absent
+                  materials, stored = recomputed, and a short fit;
   dense rays      3000 x 460 rays into 350 x 220 bins: sampled rays and the
                   polar total against the scores.
 """
@@ -187,6 +190,69 @@ def test_large_scene(son):
     d_st = b.backward(theta, prm, G, hits=True)
     torch.cuda.synchronize()
     assert torch.equal(d_rc, d_st) and torch.isfinite(d_rc).all()
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+    b.close()
+    son.release(sid)
+
+
+# ---------------------------------------------------------------------------
+# large scene with 1024 materials: per-material gradient at that scale
+# ---------------------------------------------------------------------------
+
+def test_large_scene_1024_materials(son):
+    mesh, mu = cached("large1024", S.large_scene, n_mat=1024)
+    assert mu.size == 1024 and int(mesh.mat.max()) < 1024
+    hfn = S.height_function(400.0, 4.0, 7)
+    base = S.sensor_single(hfn, n_beams=1024, n_elev=256, n_range_bins=4000, r_min=0.1, r_max=60.0,
+                           fan_w=0, fan_h=0)
+    poses = S.trajectory(base, hfn, 4, radius=60.0, seed=11)
+    sid = son.upload_mesh(mesh)
+    theta = son.theta(0.04, 1.5, mu)
+    prm0 = RenderParams(normalise=0)
+    b = son.batch([(sid, p, 40 + k, k) for k, p in enumerate(poses)])
+    b.render(theta, prm0, binned=True, fan=False)
+    torch.cuda.synchronize()
+    spec = poses[1]
+    cols = [300]
+    tv = O.tri_verts(mesh)
+    ref, ids = check_frame(mesh, mu, 0.04, 1.5, spec, b.view(1), 41, 1, cols, 0, tv, O.Params(normalise=0))
+    # upstream gradient on that column of frame 1 only
+    G = torch.zeros(b.n_polar, device=son.device)
+    g1 = np.zeros((spec.n_range_bins, spec.n_az_bins), np.float32)
+    g1[:, cols] = np.random.default_rng(8).normal(size=(spec.n_range_bins, len(cols))).astype(np.float32)
+    p0 = b.layout[1][0]
+    G[p0:p0 + g1.size] = torch.tensor(g1.ravel(), device=son.device)
+    d_st = b.backward(theta, prm0, G, hits=True)
+    d_rc = b.backward(theta, prm0, G, hits=False)
+    torch.cuda.synchronize()
+    assert torch.equal(d_st, d_rc)
+    want = O.grad(mesh, mu, 0.04, 1.5, spec, O.Params(normalise=0), 41, 1, g1.astype(np.float64),
+                  np.zeros(g1.shape), {"hits": {k: v for k, v in ref["hits"].items() if k != "threads"},
+                                       "key": ref["key"]})
+    got = d_st.double().cpu().numpy()
+    scale = np.abs(want).max()
+    assert np.allclose(got, want, rtol=1e-3, atol=2e-4 * scale)
+    # materials no binned return of that column hits get exactly zero
+    hit_mats = set(mesh.mat[ref["hits"]["tri"][(ref["key"] != 0xFFFFFFFF) & (ref["hits"]["tri"] >= 0)]].tolist())
+    absent = [m for m in range(1024) if m not in hit_mats]
+    assert len(absent) > 900 and np.all(got[2 + np.array(absent)] == 0.0)
+    # a short fit of the 1024 reflectivities through autograd lowers the loss
+    from paper_2503_01074_gb300.autograd import sonar_render
+    prm = RenderParams()
+    mu_t = (mu * np.random.default_rng(12).uniform(0.7, 1.3, 1024)).astype(np.float32)
+    target = son.render(sid, spec, son.theta(0.04, 1.5, mu_t), prm, 41, 1)["polar"]
+    mu_p = theta[2:].clone().requires_grad_(True)      # alpha and gain match the target: fit mu only
+    opt = torch.optim.Adam([mu_p], lr=0.005)
+    losses = []
+    for it in range(16):
+        opt.zero_grad()
+        th = torch.cat([theta[:2], mu_p])
+        loss = torch.mean((sonar_render(th, son, sid, spec, prm, 41, 1, save_hits=it % 2 == 0) - target) ** 2)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    assert losses[-1] < 0.8 * losses[0], losses
     st, bits = son.check()
     assert st == 0 and bits == 0
     b.close()
