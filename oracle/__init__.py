@@ -62,6 +62,7 @@ def lib():
         L.oracle_grad.argtypes = [f64, C.c_int, f64, f64, C.c_uint64, C.c_uint64, C.c_double,
                                   C.c_double, C.c_int64, i64, i32, f64, f64, i32, f64, C.c_int,
                                   C.c_double, C.c_double, C.c_int, f64]
+        L.oracle_uw_image.argtypes = [f32, f32, C.c_int64, f64, f64]
         _LIB = L
     return _LIB
 
@@ -240,3 +241,14 @@ def loss_from_hits(mesh, mu, alpha, gain, sensor, params, seed, frame, fwd, targ
     N, _, _ = normalise(sensor, In, params.normalise)
     d = N - np.asarray(target, np.float64).ravel()
     return float(np.mean(d * d)), In
+
+
+def uw_image(J, depth, coef):
+    """Eq. 1 per pixel and channel: J [..., 3] f32, depth [...] f32, coef (9,):
+    beta_attn (RGB), beta_bs (RGB), B_inf (RGB).  Returns I [..., 3] f64."""
+    J = np.ascontiguousarray(J, np.float32)
+    d = np.ascontiguousarray(depth, np.float32)
+    assert J.shape[-1] == 3 and J.shape[:-1] == d.shape
+    out = np.empty(J.shape, np.float64)
+    lib().oracle_uw_image(J.reshape(-1), d.reshape(-1), d.size, np.ascontiguousarray(coef, np.float64), out.reshape(-1))
+    return out

@@ -17,6 +17,7 @@
  *   normalise   range-wise: each range row divided by its maximum (Sec. III-A-2)
  *   fan         Cartesian resample of the polar image (plot style, Sec. III-A-2)
  *   gradient    analytic adjoint of the above w.r.t. (alpha, gain, mu)
+ *   camera      underwater image formation of an in-air image and its depth (Eq. 1)
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
  * Numbers: As Easy as 1, 2, 3", SC'11), written from that paper's description.
@@ -451,4 +452,30 @@ void oracle_grad(const double* sd, int mode, const double* G, const double* In,
         dtheta[2 + m] += g * c * att * gain;
     }
     free(gI);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Underwater image formation (Sec. III-A-1, Eq. 1)                          */
+/* ------------------------------------------------------------------------ */
+
+/* For every pixel k and colour channel c:
+ *   I_c = J_c exp(-beta_attn,c d) + B_inf,c (1 - exp(-beta_bs,c d)).
+ * J: [n][3] (in-air image, pixel-major RGB), d: [n] depth in metres,
+ * coef: beta_attn (R, G, B), beta_bs (R, G, B), B_inf (R, G, B).
+ * A coefficient of 0 means no attenuation at any depth, also d = +inf (the
+ * exponent is taken as 0 rather than 0 * inf). */
+static double uw_transmission(double beta, double d)
+{
+    return beta == 0.0 ? 1.0 : exp(-beta * d);
+}
+
+void oracle_uw_image(const float* J, const float* d, int64_t n, const double coef[9], double* I)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        for (int c = 0; c < 3; ++c) {
+            const double attn = uw_transmission(coef[c], (double)d[k]);
+            const double bs = uw_transmission(coef[3 + c], (double)d[k]);
+            I[3 * k + c] = (double)J[3 * k + c] * attn + coef[6 + c] * (1.0 - bs);   /* Eq. 1 */
+        }
+    }
 }
