@@ -320,6 +320,24 @@ sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t
 /* Adds or replaces cache entries (rows as above), e.g. loaded from a file. */
 sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int32_t count);
 
+/* ---- underwater camera image (Sec. III-A-1, Eq. 1) ---- */
+
+/* Water-column effects on a camera image.  For every pixel k and colour
+ * channel c (R, G, B):
+ *   I_c = J_c exp(-beta_attn,c d) + B_inf,c (1 - exp(-beta_bs,c d)).
+ * d_J      [n_pixels][3] f32, device: the in-air image J (pixel-major RGB).
+ * d_depth  [n_pixels] f32, device: the depth d in metres (+inf where no
+ *          geometry: the pixel then shows the veiling light).
+ * coef     9 floats, host: beta_attn (R, G, B), beta_bs (R, G, B) in 1/m,
+ *          finite and >= 0 (0 = no attenuation at any depth); B_inf (R, G, B),
+ *          finite.
+ * d_I      [n_pixels][3] f32, device, out; may be d_J itself (in place).
+ * All buffers are the caller's; work is enqueued on `stream`.  16-byte aligned
+ * buffers take a vectorised path.  Errors: SONAR_ERR_ARG (NULL buffer with
+ * n_pixels > 0, n_pixels < 0, bad coefficient), before anything is enqueued. */
+sonar_status sonar_uw_image(sonar_ctx_t ctx, const float* d_J, const float* d_depth, int64_t n_pixels,
+                            const float coef[9], float* d_I, void* stream);
+
 /* ---- counters (roofline evidence) ---- */
 
 /* Re-casts the rays of one sensor (with the warp tiles tuned for its shape)

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsonar.so")
-SOURCES = ["render.cu", "bvh_build.cu", "sonar_api.cu"]
+SOURCES = ["render.cu", "bvh_build.cu", "sonar_api.cu", "image.cu"]
 HEADERS = ["sonar_internal.cuh", "sonar_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

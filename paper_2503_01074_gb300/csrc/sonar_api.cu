@@ -1336,6 +1336,28 @@ extern "C" sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int
 // counters
 // ===========================================================================
 
+extern "C" sonar_status sonar_uw_image(sonar_ctx_t ctx, const float* d_J, const float* d_depth, int64_t n_pixels,
+                                       const float coef[9], float* d_I, void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    if (n_pixels < 0) return fail(ctx, SONAR_ERR_ARG, "n_pixels < 0");
+    if (!coef) return fail(ctx, SONAR_ERR_ARG, "coef is NULL");
+    for (int c = 0; c < 9; ++c) {
+        if (!std::isfinite(coef[c])) return fail(ctx, SONAR_ERR_ARG, "coefficients must be finite");
+        if (c < 6 && coef[c] < 0.0f) return fail(ctx, SONAR_ERR_ARG, "attenuation and backscatter must be >= 0");
+    }
+    if (n_pixels == 0) return SONAR_OK;
+    if (!d_J || !d_depth || !d_I) return fail(ctx, SONAR_ERR_ARG, "NULL image buffer");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    UwCoef k;
+    for (int c = 0; c < 3; ++c) {
+        k.b_attn[c] = coef[c];
+        k.b_bs[c] = coef[3 + c];
+        k.b_inf[c] = coef[6 + c];
+    }
+    CU(launch_uw_image(d_J, d_depth, n_pixels, k, d_I, ctx->sm_count, (cudaStream_t)stream), "image launch");
+    return SONAR_OK;
+}
+
 extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
                                           const sonar_params* params, void* stream, int64_t out[6]) {
     if (!ctx || !out) return fail(ctx, SONAR_ERR_ARG, "NULL argument");

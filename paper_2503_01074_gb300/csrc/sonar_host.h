@@ -49,6 +49,8 @@ cudaError_t launch_adjoint(const AdjArgs& a, int grid, int block, size_t smem, f
 int adjoint_blocks_per_sm(int block, size_t smem);
 cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
                          const TraceCounters& tc, uint32_t* err, cudaStream_t st);
+cudaError_t launch_uw_image(const float* J, const float* depth, int64_t n, const UwCoef& k, float* I, int sm_count,
+                            cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out,
                             cudaStream_t st);
 

@@ -229,14 +229,21 @@ struct NormArgs {
     float* polar;
 };
 
-constexpr int kFanTile = 4096;  // fan pixels per block
+constexpr int kFanTile = 4096;  // pixels per coordinate-table block
 constexpr int kFanSide = 64;    // resample blocks are kFanSide x kFanSide pixel squares (compact in polar)
 // Square resample blocks of a w x h fan image.
 __host__ __device__ inline int32_t fan_squares(int32_t w, int32_t h) {
     return ((w + kFanSide - 1) / kFanSide) * ((h + kFanSide - 1) / kFanSide);
 }
 
-// Fan resample: blocks of kFanTile pixels of one sensor, reading the normalised image.
+// Underwater image formation coefficients (Eq. 1), per colour channel R, G, B.
+struct UwCoef {
+    float b_attn[3];   // attenuation
+    float b_bs[3];     // backscatter
+    float b_inf[3];    // veiling light
+};
+
+// Fan resample: kFanSide x kFanSide pixel squares of one sensor, reading the normalised image.
 struct FanArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr
     const int2* block_map;      // batch: per block (sensor, block of that sensor); single: nullptr

@@ -406,3 +406,32 @@ def random_soup(n_tris: int, seed: int, center=(0.0, 6.0, -2.0), spread=4.0,
     tris = np.arange(3 * n_tris, dtype=np.int32).reshape(n_tris, 3)
     mat = rng.integers(0, n_mat, size=n_tris).astype(np.int32)
     return Mesh(verts, tris, mat)
+
+
+# ----------------------------------------------------------------------------
+# camera inputs for the underwater image formation (in-air image and depth)
+# ----------------------------------------------------------------------------
+
+def camera_rgb(height: int, width: int, seed: int) -> np.ndarray:
+    """A seeded in-air RGB image in [0, 1] ([height, width, 3] float32): one
+    value-noise fBm texture per channel, mapped through a logistic."""
+    y, x = np.meshgrid(np.linspace(-0.5, 0.5, height), np.linspace(-0.5, 0.5, width), indexing="ij")
+    ch = [_value_noise_fbm(x, y, 1.0, seed + 31 * c, octaves=5, base_cells=6) for c in range(3)]
+    img = 1.0 / (1.0 + np.exp(-2.5 * np.stack(ch, axis=-1)))
+    return img.astype(np.float32)
+
+
+def camera_seabed_depth(height: int, width: int, hfov_deg=90.0, altitude=4.0, pitch_deg=30.0) -> np.ndarray:
+    """Distance along each pixel's ray from a pinhole camera `altitude` above a
+    flat seabed, pitched `pitch_deg` down ([height, width] float32, +inf for
+    rays that do not reach the seabed)."""
+    f = 0.5 * width / math.tan(math.radians(hfov_deg) / 2.0)
+    v, u = np.meshgrid(np.arange(height) + 0.5 - height / 2.0, np.arange(width) + 0.5 - width / 2.0,
+                       indexing="ij")
+    # camera frame: x right, y down, z forward; pitched down about x
+    p = math.radians(pitch_deg)
+    dz = -(v * math.cos(p) + f * math.sin(p))   # world up component of (u, v, f)
+    norm = np.sqrt(u * u + v * v + f * f)
+    with np.errstate(divide="ignore"):
+        t = np.where(dz < 0.0, altitude * norm / np.maximum(-dz, 1e-30), np.inf)
+    return t.astype(np.float32)

@@ -98,6 +98,8 @@ _SIG = {
     "sonar_tune_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
                                  C.POINTER(C.c_int32)]),
     "sonar_tune_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
+    "sonar_uw_image": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float),
+                                 C.c_void_p, C.c_void_p]),
     "sonar_trace_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Sensor), C.POINTER(Params),
                                     C.c_void_p, C.POINTER(C.c_int64)]),
 }
@@ -291,6 +293,21 @@ class Sonar:
         self._check(self.lib.sonar_trace_stats(self.h, sid, C.byref(sensor), C.byref(prm), _stream(stream), out))
         return dict(zip(("visits", "tests", "nodes_touched", "tris_touched", "rays", "exact_tests"),
                         list(out)))
+
+    def uw_image(self, J, depth, coef, out=None, stream=None):
+        """Underwater image (Eq. 1) of in-air image J [..., 3] and depth [...]
+        (float32 CUDA tensors); coef = beta_attn (RGB), beta_bs (RGB), B_inf
+        (RGB).  Returns I [..., 3] (out may be J itself)."""
+        t = self.torch
+        if J.dtype != t.float32 or depth.dtype != t.float32 or J.shape[-1] != 3 or J.shape[:-1] != depth.shape:
+            raise ValueError("J must be float32 [..., 3] and depth float32 [...] of the same leading shape")
+        J = J.contiguous()
+        depth = depth.contiguous()
+        I = t.empty_like(J) if out is None else out
+        k = (C.c_float * 9)(*[float(x) for x in coef])
+        self._check(self.lib.sonar_uw_image(self.h, _ptr(J), _ptr(depth), depth.numel(), k, _ptr(I),
+                                            _stream(stream)))
+        return I
 
     def tune_get(self):
         cnt = C.c_int32()
