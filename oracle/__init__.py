@@ -24,6 +24,7 @@ conventions (they are pinned against their own closed forms only).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from dataclasses import dataclass
 
@@ -63,6 +64,10 @@ def lib():
                                   C.c_double, C.c_int64, i64, i32, f64, f64, i32, f64, C.c_int,
                                   C.c_double, C.c_double, C.c_int, f64]
         L.oracle_uw_image.argtypes = [f32, f32, C.c_int64, f64, f64]
+        L.oracle_dvl_beams.argtypes = [f64, C.c_int64, C.c_double, f64]
+        L.oracle_dvl_measure.argtypes = [C.c_int64, f64, f64, f64, C.c_double, C.c_double, C.c_double, C.c_int,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64, f64, i32, f64]
+        L.oracle_dvl_schedule.argtypes = [C.c_int64, C.c_int64, f64, C.c_double, i32]
         _LIB = L
     return _LIB
 
@@ -252,3 +257,62 @@ def uw_image(J, depth, coef):
     out = np.empty(J.shape, np.float64)
     lib().oracle_uw_image(J.reshape(-1), d.reshape(-1), d.size, np.ascontiguousarray(coef, np.float64), out.reshape(-1))
     return out
+
+
+@dataclass
+class DvlParams:
+    """DVL readings (the paper fixes none of these): beam tilt off the down axis
+    (rad), valid range [r_min, r_max] (m), beams needed for a velocity, beam
+    velocity noise (m/s), ping period t0 + t1 * farthest valid range (s), and
+    the period after a dropout (s)."""
+    tilt: float = math.radians(30.0)
+    r_min: float = 0.3
+    r_max: float = 50.0
+    min_beams: int = 3
+    sigma_b: float = 0.01
+    t0: float = 0.05
+    t1: float = 4.0 * 2.0 / 1500.0
+    t_lost: float = 1.0
+
+
+def dvl_beams(R, tilt):
+    """World directions [n, 4, 3] of the four beams of poses R [n, 3, 3]."""
+    R = np.ascontiguousarray(R, np.float64).reshape(-1, 9)
+    out = np.empty((R.shape[0], 4, 3), np.float64)
+    lib().oracle_dvl_beams(R.reshape(-1), R.shape[0], float(tilt), out.reshape(-1))
+    return out
+
+
+def dvl_ranges(tv, pos, R, tilt, nthreads=0):
+    """Closest-hit distance of every beam [n, 4] (+inf for a miss), with the
+    hit records (for the edge/tie flags)."""
+    pos = np.asarray(pos, np.float64).reshape(-1, 3)
+    dirs = dvl_beams(R, tilt)
+    t = np.empty((pos.shape[0], 4))
+    recs = []
+    for p in range(pos.shape[0]):
+        h = closest_hits(tv, pos[p], dirs[p], nthreads=nthreads)
+        t[p] = np.where(h["tri"] >= 0, h["t"], np.inf)
+        recs.append(h)
+    return t, recs
+
+
+def dvl_measure(R, v_world, t, params: "DvlParams", seed):
+    R = np.ascontiguousarray(R, np.float64).reshape(-1, 9)
+    n = R.shape[0]
+    vel = np.empty((n, 3))
+    flags = np.empty(n, np.int32)
+    period = np.empty(n)
+    lib().oracle_dvl_measure(n, R.reshape(-1), np.ascontiguousarray(v_world, np.float64).reshape(-1),
+                             np.ascontiguousarray(t, np.float64).reshape(-1), params.tilt, params.r_min,
+                             params.r_max, int(params.min_beams), params.sigma_b, params.t0, params.t1,
+                             params.t_lost, int(seed), vel.reshape(-1), flags, period)
+    return vel, flags, period
+
+
+def dvl_schedule(period, dt):
+    period = np.ascontiguousarray(period, np.float64)
+    n_veh, n_steps = period.shape
+    emit = np.empty((n_veh, n_steps), np.int32)
+    lib().oracle_dvl_schedule(n_veh, n_steps, period.reshape(-1), float(dt), emit.reshape(-1))
+    return emit

@@ -18,6 +18,7 @@
  *   fan         Cartesian resample of the polar image (plot style, Sec. III-A-2)
  *   gradient    analytic adjoint of the above w.r.t. (alpha, gain, mu)
  *   camera      underwater image formation of an in-air image and its depth (Eq. 1)
+ *   DVL         four-beam Janus ranges, least-squares velocity, rate and dropout
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
  * Numbers: As Easy as 1, 2, 3", SC'11), written from that paper's description.
@@ -476,6 +477,139 @@ void oracle_uw_image(const float* J, const float* d, int64_t n, const double coe
             const double attn = uw_transmission(coef[c], (double)d[k]);
             const double bs = uw_transmission(coef[3 + c], (double)d[k]);
             I[3 * k + c] = (double)J[3 * k + c] * attn + coef[6 + c] * (1.0 - bs);   /* Eq. 1 */
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* DVL (Sec. III-A-3): four-beam convex Janus array, range-dependent rate,   */
+/* dropout.  The paper fixes no geometry, rate law or noise; the readings    */
+/* are: beam k (k = 0..3) points tilt off the sensor's down axis at azimuth  */
+/* 45 + 90 k degrees, (sin tilt cos a_k, sin tilt sin a_k, -cos tilt) in the  */
+/* sensor frame; a beam is valid when its closest hit lies in [r_min, r_max]; */
+/* each valid beam measures its radial velocity b_k . v + sigma_b w_k (v the  */
+/* sensor-frame velocity, w_k standard normal); the velocity is the least-    */
+/* squares fit over the valid beams, reported when at least min_beams are     */
+/* valid; the ping period is t0 + t1 * (farthest valid range), or t_lost when */
+/* the velocity is invalid.                                                   */
+/* ------------------------------------------------------------------------ */
+
+static void dvl_beam_sensor(double tilt, int k, double b[3])
+{
+    const double a = M_PI / 4.0 + k * (M_PI / 2.0);
+    b[0] = sin(tilt) * cos(a);
+    b[1] = sin(tilt) * sin(a);
+    b[2] = -cos(tilt);
+}
+
+/* World directions of the four beams of n poses (R: sensor->world, row-major). */
+void oracle_dvl_beams(const double* R, int64_t n, double tilt, double* dirs)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        for (int k = 0; k < 4; ++k) {
+            double b[3];
+            dvl_beam_sensor(tilt, k, b);
+            for (int a = 0; a < 3; ++a)
+                dirs[12 * p + 3 * k + a] = R[9 * p + 3 * a] * b[0] + R[9 * p + 3 * a + 1] * b[1] +
+                                           R[9 * p + 3 * a + 2] * b[2];
+        }
+    }
+}
+
+/* The four standard-normal beam draws of pose p: Philox4x32-10, key = seed,
+ * counter (p lo, p hi, 2, h) for h = 0, 1; words (0, 1) -> beam 2h and words
+ * (2, 3) -> beam 2h + 1, each by the cosine branch of Box-Muller. */
+static void dvl_normals(uint64_t p, uint64_t seed, double w[4])
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 2u, h};
+        uint32_t x[4];
+        oracle_philox4x32_10(ctr, key, x);
+        w[2 * h] = sqrt(-2.0 * log(u01(x[0]))) * cos(2.0 * M_PI * u01(x[1]));
+        w[2 * h + 1] = sqrt(-2.0 * log(u01(x[2]))) * cos(2.0 * M_PI * u01(x[3]));
+    }
+}
+
+/* Solves the 3x3 system A x = y by Gaussian elimination with partial pivoting. */
+static int solve3(double A[3][3], double y[3], double x[3])
+{
+    int piv[3] = {0, 1, 2};
+    for (int c = 0; c < 3; ++c) {
+        int best = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(A[piv[r]][c]) > fabs(A[piv[best]][c])) best = r;
+        const int t = piv[c]; piv[c] = piv[best]; piv[best] = t;
+        const double d = A[piv[c]][c];
+        if (d == 0.0) return 0;
+        for (int r = c + 1; r < 3; ++r) {
+            const double f = A[piv[r]][c] / d;
+            for (int k = c; k < 3; ++k) A[piv[r]][k] -= f * A[piv[c]][k];
+            y[piv[r]] -= f * y[piv[c]];
+        }
+    }
+    for (int c = 2; c >= 0; --c) {
+        double s = y[piv[c]];
+        for (int k = c + 1; k < 3; ++k) s -= A[piv[c]][k] * x[k];
+        x[c] = s / A[piv[c]][c];
+    }
+    return 1;
+}
+
+/* One measurement per pose.  t: [n][4] closest-hit distances along the unit
+ * beams (+inf for a miss); v_world: [n][3].  Out: vel [n][3] (sensor frame, 0
+ * when invalid), flags [n] (bit k: beam k valid; bit 4: velocity valid),
+ * period [n] (s). */
+void oracle_dvl_measure(int64_t n, const double* R, const double* v_world, const double* t, double tilt,
+                        double r_min, double r_max, int min_beams, double sigma_b, double t0, double t1,
+                        double t_lost, uint64_t seed, double* vel, int32_t* flags, double* period)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        double vs[3];
+        for (int a = 0; a < 3; ++a)   /* R^T v: world -> sensor */
+            vs[a] = R[9 * p + a] * v_world[3 * p] + R[9 * p + 3 + a] * v_world[3 * p + 1] +
+                    R[9 * p + 6 + a] * v_world[3 * p + 2];
+        double w[4];
+        dvl_normals((uint64_t)p, seed, w);
+        double A[3][3] = {{0}}, y[3] = {0};
+        int nvalid = 0, f = 0;
+        double far = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            const double r = t[4 * p + k];
+            if (!(r >= r_min && r <= r_max)) continue;
+            f |= 1 << k;
+            ++nvalid;
+            if (r > far) far = r;
+            double b[3];
+            dvl_beam_sensor(tilt, k, b);
+            const double u = b[0] * vs[0] + b[1] * vs[1] + b[2] * vs[2] + sigma_b * w[k];
+            for (int i = 0; i < 3; ++i) {
+                y[i] += b[i] * u;
+                for (int j = 0; j < 3; ++j) A[i][j] += b[i] * b[j];
+            }
+        }
+        double x[3] = {0, 0, 0};
+        if (nvalid >= min_beams && solve3(A, y, x)) f |= 16;
+        else x[0] = x[1] = x[2] = 0.0;
+        for (int a = 0; a < 3; ++a) vel[3 * p + a] = x[a];
+        flags[p] = f;
+        period[p] = (f & 16) ? t0 + t1 * far : t_lost;
+    }
+}
+
+/* Emission schedule of n_veh vehicles of n_steps steps each (period [veh][step],
+ * step dt): a measurement at step 0, then at step s + max(1, ceil(period[s] / dt))
+ * after a measurement at step s.  emit [veh][step] = 1 at measurement steps. */
+void oracle_dvl_schedule(int64_t n_veh, int64_t n_steps, const double* period, double dt, int32_t* emit)
+{
+    for (int64_t v = 0; v < n_veh; ++v) {
+        for (int64_t s = 0; s < n_steps; ++s) emit[v * n_steps + s] = 0;
+        int64_t s = 0;
+        while (s < n_steps) {
+            emit[v * n_steps + s] = 1;
+            double q = ceil(period[v * n_steps + s] / dt);
+            if (q < 1.0) q = 1.0;
+            s += (int64_t)q;
         }
     }
 }
