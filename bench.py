@@ -609,6 +609,38 @@ def run_ours(args):
               "frames_s": F / (u_ms / 1e3),
               "roofline": {"bound": "hbm", "achieved": gbs, "unit": "GB/s", "algorithmic_bytes_per_pixel": 28}}
         del Jg, dg, Ig, J1, d1
+    # DVL: 4096 vehicles x 256 steps of 20 ms on the same scene (1M poses, 4M
+    # beams) per launch, then their measurement schedule
+    dvl = None
+    if not args.no_extras:
+        from paper_2503_01074_gb300.sonar import DvlParams
+        hfn_d = S.height_function(100.0, 2.0, 1)
+        nv, ns, dt = 4096, 256, 0.02
+        dp, dv = S.dvl_trajectories(hfn_d, nv, ns, dt, seed=21)
+        dp = torch.tensor(dp.reshape(-1, 12), device=dev)
+        dv = torch.tensor(dv.reshape(-1, 3), device=dev)
+        prm_d = DvlParams()
+        for _ in range(3):
+            o = son.dvl(sid, dp, dv, prm_d, seed=5)
+            son.dvl_schedule(o["period"].view(nv, ns), dt)
+        e_d = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        dms, sms = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e_d[0].record(stream)
+            o = son.dvl(sid, dp, dv, prm_d, seed=5)
+            e_d[1].record(stream)
+            son.dvl_schedule(o["period"].view(nv, ns), dt)
+            e_d[2].record(stream)
+            torch.cuda.synchronize()
+            dms.append(e_d[0].elapsed_time(e_d[1]))
+            sms.append(e_d[1].elapsed_time(e_d[2]))
+        fl = o["flags"]
+        dvl = {"vehicles": nv, "steps": ns, "poses": nv * ns, "ms_measure": float(np.mean(dms)),
+               "ms_schedule": float(np.mean(sms)), "Mposes_s": nv * ns / float(np.mean(dms)) / 1e3,
+               "Mbeams_s": 4 * nv * ns / float(np.mean(dms)) / 1e3,
+               "valid_fraction": float(((fl & 16) != 0).float().mean().item())}
+        del dp, dv, o
     # algorithmic bytes of one ray-cast launch: per frame, the 4-wide BVH nodes
     # (128 B) and triangles (48 B) its rays touch, plus the 16-byte hit record of
     # every ray; summed over the B frames the launch renders
@@ -664,6 +696,8 @@ def run_ours(args):
         line.update({k: float(v) for k, v in extras.items()})
         if uw is not None:
             line["uw_image"] = uw
+        if dvl is not None:
+            line["dvl"] = dvl
         if configs is not None:
             line["configs"] = configs
         print(json.dumps(line), flush=True)

@@ -338,6 +338,49 @@ sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int32_t count)
 sonar_status sonar_uw_image(sonar_ctx_t ctx, const float* d_J, const float* d_depth, int64_t n_pixels,
                             const float coef[9], float* d_I, void* stream);
 
+/* ---- DVL (Sec. III-A-3) ---- */
+
+/* DVL configuration.  The paper describes a four-beam convex Janus array with
+ * a range-dependent measurement rate and dropout, and fixes no numbers; these
+ * are this library's readings, all adjustable:
+ *   tilt       beam angle off the sensor's down axis (rad), in (0, pi/2);
+ *              beam k points at azimuth 45 + 90 k degrees around that axis
+ *   r_min, r_max  a beam is valid when its closest hit lies in [r_min, r_max] (m)
+ *   min_beams  valid beams needed for a velocity (3 or 4)
+ *   sigma_b    standard deviation of each beam's radial-velocity noise (m/s), >= 0
+ *   t0, t1     ping period t0 + t1 * (farthest valid range) (s, s/m), >= 0
+ *   t_lost     ping period while the velocity is invalid (s), > 0 */
+typedef struct {
+    float tilt, r_min, r_max;
+    int32_t min_beams;
+    float sigma_b, t0, t1, t_lost;
+} sonar_dvl_params;
+
+/* One DVL measurement for each of n poses against scene `scene_id`.
+ * d_poses [n][12] f32: position (3) and sensor->world rotation (9, row-major;
+ *   the sensor looks down its -z axis).  d_vel [n][3] f32: world velocity.
+ * Each beam measures its radial velocity plus noise (Philox4x32-10, key =
+ * seed, counter (pose lo, pose hi, 2, beam / 2); words 0, 1 -> even beams and
+ * 2, 3 -> odd beams by the cosine branch of Box-Muller); the velocity is the
+ * least-squares fit over the valid beams, in the sensor frame.
+ * Out (device, caller-owned): d_ranges [n][4] closest-hit distance per beam
+ * (+inf for a miss); d_vel_out [n][3] (0 when invalid); d_flags [n] (bit k:
+ * beam k valid, bit 4: velocity valid); d_period [n] ping period (s).
+ * Errors: SONAR_ERR_ARG for a bad scene, NULL buffer with n > 0, n < 0 or a
+ * configuration outside the ranges above. */
+sonar_status sonar_dvl(sonar_ctx_t ctx, int32_t scene_id, const float* d_poses, const float* d_vel, int64_t n,
+                       const sonar_dvl_params* params, uint64_t seed, float* d_ranges, float* d_vel_out,
+                       int32_t* d_flags, float* d_period, void* stream);
+
+/* Measurement steps of n_veh vehicles simulated over n_steps steps of dt
+ * seconds (d_period [n_veh][n_steps] from sonar_dvl on poses laid out vehicle
+ * by vehicle): a measurement at step 0, then max(1, ceil(period / dt)) steps
+ * after each one, the period read at that measurement.  d_emit [n_veh][n_steps]
+ * int32 out: 1 at measurement steps, else 0.  Errors: SONAR_ERR_ARG for NULL
+ * buffers with work to do, negative counts, dt <= 0 or not finite. */
+sonar_status sonar_dvl_schedule(sonar_ctx_t ctx, const float* d_period, int64_t n_veh, int64_t n_steps, float dt,
+                                int32_t* d_emit, void* stream);
+
 /* ---- counters (roofline evidence) ---- */
 
 /* Re-casts the rays of one sensor (with the warp tiles tuned for its shape)

@@ -1358,6 +1358,67 @@ extern "C" sonar_status sonar_uw_image(sonar_ctx_t ctx, const float* d_J, const 
     return SONAR_OK;
 }
 
+extern "C" sonar_status sonar_dvl(sonar_ctx_t ctx, int32_t scene_id, const float* d_poses, const float* d_vel,
+                                  int64_t n, const sonar_dvl_params* p, uint64_t seed, float* d_ranges,
+                                  float* d_vel_out, int32_t* d_flags, float* d_period, void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    if (!p) return fail(ctx, SONAR_ERR_ARG, "params is NULL");
+    if (n < 0) return fail(ctx, SONAR_ERR_ARG, "n < 0");
+    sonar_status st;
+    if ((st = check_scene(ctx, scene_id))) return st;
+    const float vals[] = {p->tilt, p->r_min, p->r_max, p->sigma_b, p->t0, p->t1, p->t_lost};
+    for (float v : vals)
+        if (!std::isfinite(v)) return fail(ctx, SONAR_ERR_ARG, "DVL parameters must be finite");
+    if (!(p->tilt > 0.0f && p->tilt < 1.5707963f)) return fail(ctx, SONAR_ERR_ARG, "tilt must lie in (0, pi/2)");
+    if (!(p->r_min >= 0.0f && p->r_max > p->r_min)) return fail(ctx, SONAR_ERR_ARG, "need 0 <= r_min < r_max");
+    if (p->min_beams != 3 && p->min_beams != 4) return fail(ctx, SONAR_ERR_ARG, "min_beams must be 3 or 4");
+    if (p->sigma_b < 0.0f || p->t0 < 0.0f || p->t1 < 0.0f || !(p->t_lost > 0.0f))
+        return fail(ctx, SONAR_ERR_ARG, "need sigma_b, t0, t1 >= 0 and t_lost > 0");
+    if (n == 0) return SONAR_OK;
+    if (!d_poses || !d_vel || !d_ranges || !d_vel_out || !d_flags || !d_period)
+        return fail(ctx, SONAR_ERR_ARG, "NULL buffer");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    DvlArgs a{};
+    a.scene = scene_dev(ctx->scenes[scene_id]);
+    a.pose = d_poses;
+    a.vel_world = d_vel;
+    a.n = n;
+    for (int k = 0; k < 4; ++k) {
+        const double az = M_PI / 4.0 + k * (M_PI / 2.0);
+        a.beam[k][0] = (float)(std::sin((double)p->tilt) * std::cos(az));
+        a.beam[k][1] = (float)(std::sin((double)p->tilt) * std::sin(az));
+        a.beam[k][2] = (float)(-std::cos((double)p->tilt));
+    }
+    a.r_min = p->r_min;
+    a.r_max = p->r_max;
+    a.sigma_b = p->sigma_b;
+    a.t0 = p->t0;
+    a.t1 = p->t1;
+    a.t_lost = p->t_lost;
+    a.min_beams = p->min_beams;
+    a.seed_lo = (uint32_t)seed;
+    a.seed_hi = (uint32_t)(seed >> 32);
+    a.ranges = d_ranges;
+    a.vel = d_vel_out;
+    a.flags = d_flags;
+    a.period = d_period;
+    a.err = ctx->d_err;
+    CU(launch_dvl(a, (cudaStream_t)stream), "DVL launch");
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_dvl_schedule(sonar_ctx_t ctx, const float* d_period, int64_t n_veh, int64_t n_steps,
+                                           float dt, int32_t* d_emit, void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    if (n_veh < 0 || n_steps < 0) return fail(ctx, SONAR_ERR_ARG, "negative count");
+    if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(ctx, SONAR_ERR_ARG, "dt must be finite and > 0");
+    if (n_veh == 0 || n_steps == 0) return SONAR_OK;
+    if (!d_period || !d_emit) return fail(ctx, SONAR_ERR_ARG, "NULL buffer");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CU(launch_dvl_schedule(d_period, n_veh, n_steps, dt, d_emit, (cudaStream_t)stream), "DVL schedule launch");
+    return SONAR_OK;
+}
+
 extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
                                           const sonar_params* params, void* stream, int64_t out[6]) {
     if (!ctx || !out) return fail(ctx, SONAR_ERR_ARG, "NULL argument");

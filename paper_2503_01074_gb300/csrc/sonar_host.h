@@ -51,6 +51,9 @@ cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_par
                          const TraceCounters& tc, uint32_t* err, cudaStream_t st);
 cudaError_t launch_uw_image(const float* J, const float* depth, int64_t n, const UwCoef& k, float* I, int sm_count,
                             cudaStream_t st);
+cudaError_t launch_dvl(const DvlArgs& a, cudaStream_t st);
+cudaError_t launch_dvl_schedule(const float* period, int64_t n_veh, int64_t n_steps, float dt, int32_t* emit,
+                                cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out,
                             cudaStream_t st);
 

@@ -236,6 +236,23 @@ __host__ __device__ inline int32_t fan_squares(int32_t w, int32_t h) {
     return ((w + kFanSide - 1) / kFanSide) * ((h + kFanSide - 1) / kFanSide);
 }
 
+// DVL measurement of n poses (four beams each).
+struct DvlArgs {
+    SceneDev scene;
+    const float* pose;        // [n][12]: position, sensor->world rotation (row-major)
+    const float* vel_world;   // [n][3]
+    int64_t n;
+    float beam[4][3];         // sensor-frame unit beams (from the tilt, in FP64 on the host)
+    float r_min, r_max, sigma_b, t0, t1, t_lost;
+    int32_t min_beams;
+    uint32_t seed_lo, seed_hi;
+    float* ranges;            // [n][4] out
+    float* vel;               // [n][3] out
+    int32_t* flags;           // [n] out
+    float* period;            // [n] out
+    uint32_t* err;
+};
+
 // Underwater image formation coefficients (Eq. 1), per colour channel R, G, B.
 struct UwCoef {
     float b_attn[3];   // attenuation

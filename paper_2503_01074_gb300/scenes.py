@@ -435,3 +435,41 @@ def camera_seabed_depth(height: int, width: int, hfov_deg=90.0, altitude=4.0, pi
     with np.errstate(divide="ignore"):
         t = np.where(dz < 0.0, altitude * norm / np.maximum(-dz, 1e-30), np.inf)
     return t.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# DVL trajectories
+# ----------------------------------------------------------------------------
+
+def dvl_trajectories(height_fn, n_veh: int, n_steps: int, dt: float, seed: int, extent=100.0,
+                     alt_lo=0.5, alt_hi=70.0):
+    """Seeded vehicles crossing a seabed: straight tracks at 0.5-2 m/s, the
+    altitude swinging between alt_lo and alt_hi (so beams leave the DVL's
+    window and come back), small pitch and roll oscillations.  Returns poses
+    [n_veh, n_steps, 12] (position, sensor->world rotation) and world
+    velocities [n_veh, n_steps, 3], float32."""
+    rng = np.random.default_rng(seed)
+    t = (np.arange(n_steps) * dt)[None, :]
+    psi = rng.uniform(0, 2 * math.pi, (n_veh, 1))
+    speed = rng.uniform(0.5, 2.0, (n_veh, 1))
+    x0 = rng.uniform(-0.35 * extent, 0.35 * extent, (n_veh, 1))
+    y0 = rng.uniform(-0.35 * extent, 0.35 * extent, (n_veh, 1))
+    w_alt, ph = rng.uniform(0.05, 0.4, (n_veh, 1)), rng.uniform(0, 2 * math.pi, (n_veh, 1))
+    w_att = rng.uniform(0.2, 1.0, (n_veh, 1))
+    pa, ra = rng.uniform(0.0, 0.15, (n_veh, 1)), rng.uniform(0.0, 0.15, (n_veh, 1))
+    a_mid, a_amp = 0.5 * (alt_lo + alt_hi), 0.5 * (alt_hi - alt_lo)
+    x = x0 + speed * np.cos(psi) * t
+    y = y0 + speed * np.sin(psi) * t
+    z = height_fn(x, y) + a_mid + a_amp * np.sin(w_alt * t + ph)
+    dz = np.gradient(z, dt, axis=1) if n_steps > 1 else np.zeros_like(z)
+    pitch, roll = pa * np.sin(w_att * t), ra * np.cos(w_att * t)
+    cy, sy = np.broadcast_to(np.cos(psi), z.shape), np.broadcast_to(np.sin(psi), z.shape)
+    cp, sp, cr, sr = np.cos(pitch), np.sin(pitch), np.cos(roll), np.sin(roll)
+    # R = Rz(psi) Rx(pitch) Ry(roll), row-major
+    R = np.stack([cy * cr - sy * sp * sr, -sy * cp, cy * sr + sy * sp * cr,
+                  sy * cr + cy * sp * sr, cy * cp, sy * sr - cy * sp * cr,
+                  -cp * sr, sp, cp * cr], axis=-1)
+    poses = np.concatenate([np.stack([x, y, z], axis=-1), R], axis=-1)
+    vels = np.stack([np.broadcast_to(speed * np.cos(psi), z.shape), np.broadcast_to(speed * np.sin(psi), z.shape),
+                     dz], axis=-1)
+    return poses.astype(np.float32), vels.astype(np.float32)

@@ -7,6 +7,7 @@ library is missing or fails to load, the first call raises.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from dataclasses import dataclass
 
@@ -58,6 +59,16 @@ class BatchOutputs(C.Structure):
                 ("hits", C.c_void_p), ("fan", C.c_void_p)]
 
 
+class DvlParams(C.Structure):
+    """DVL configuration (include/sonar.h: sonar_dvl_params)."""
+    _fields_ = [("tilt", C.c_float), ("r_min", C.c_float), ("r_max", C.c_float), ("min_beams", C.c_int32),
+                ("sigma_b", C.c_float), ("t0", C.c_float), ("t1", C.c_float), ("t_lost", C.c_float)]
+
+    def __init__(self, tilt=math.radians(30.0), r_min=0.3, r_max=50.0, min_beams=3, sigma_b=0.01, t0=0.05,
+                 t1=4.0 * 2.0 / 1500.0, t_lost=1.0):
+        super().__init__(tilt, r_min, r_max, min_beams, sigma_b, t0, t1, t_lost)
+
+
 HIT_DTYPE = np.dtype([("key", "<u4"), ("tri", "<u4"), ("r", "<f4"), ("cos", "<f4")])
 
 # name -> (restype, argtypes); every symbol declared in include/sonar.h
@@ -100,6 +111,10 @@ _SIG = {
     "sonar_tune_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
     "sonar_uw_image": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float),
                                  C.c_void_p, C.c_void_p]),
+    "sonar_dvl": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(DvlParams),
+                            C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sonar_dvl_schedule": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_float, C.c_void_p,
+                                     C.c_void_p]),
     "sonar_trace_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Sensor), C.POINTER(Params),
                                     C.c_void_p, C.POINTER(C.c_int64)]),
 }
@@ -308,6 +323,34 @@ class Sonar:
         self._check(self.lib.sonar_uw_image(self.h, _ptr(J), _ptr(depth), depth.numel(), k, _ptr(I),
                                             _stream(stream)))
         return I
+
+    def dvl(self, sid, poses, vel_world, params=None, seed=0, stream=None):
+        """DVL measurements of poses [n, 12] (position, sensor->world rotation)
+        with world velocities [n, 3] (float32 CUDA tensors).  Returns a dict of
+        ranges [n, 4], vel [n, 3] (sensor frame), flags [n] (int32; bit k beam k
+        valid, bit 4 velocity valid), period [n]."""
+        t = self.torch
+        params = params or DvlParams()
+        poses = poses.contiguous()
+        vel_world = vel_world.contiguous()
+        n = poses.shape[0]
+        if poses.shape != (n, 12) or vel_world.shape != (n, 3) or poses.dtype != t.float32:
+            raise ValueError("poses must be float32 [n, 12] and vel_world [n, 3]")
+        out = {"ranges": t.empty(n, 4, device=self.device), "vel": t.empty(n, 3, device=self.device),
+               "flags": t.empty(n, dtype=t.int32, device=self.device), "period": t.empty(n, device=self.device)}
+        self._check(self.lib.sonar_dvl(self.h, sid, _ptr(poses), _ptr(vel_world), n, C.byref(params),
+                                       C.c_uint64(seed), _ptr(out["ranges"]), _ptr(out["vel"]), _ptr(out["flags"]),
+                                       _ptr(out["period"]), _stream(stream)))
+        return out
+
+    def dvl_schedule(self, period, dt, stream=None):
+        """Measurement steps [n_veh, n_steps] (int32 0/1) of periods [n_veh, n_steps]."""
+        period = period.contiguous()
+        n_veh, n_steps = period.shape
+        emit = self.torch.empty(n_veh, n_steps, dtype=self.torch.int32, device=self.device)
+        self._check(self.lib.sonar_dvl_schedule(self.h, _ptr(period), n_veh, n_steps, C.c_float(dt), _ptr(emit),
+                                                _stream(stream)))
+        return emit
 
     def tune_get(self):
         cnt = C.c_int32()
