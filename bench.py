@@ -379,7 +379,8 @@ def measure_configs(son, steps):
     return out
 
 
-RAY_CAST_SOURCES = ("paper_2503_01074_gb300/csrc/render.cu", "paper_2503_01074_gb300/csrc/sonar_internal.cuh")
+RAY_CAST_SOURCES = ("paper_2503_01074_gb300/csrc/trace.cu", "paper_2503_01074_gb300/csrc/devmath.cuh",
+                    "paper_2503_01074_gb300/csrc/sonar_internal.cuh")
 
 
 def ray_cast_sources_sha():
@@ -389,21 +390,48 @@ def ray_cast_sources_sha():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile():
-    """Per-frame DRAM bytes (read + write) of the ray-cast kernel from the
-    committed ncu summary, if it was taken on the current kernel sources
-    (else None: the counters no longer describe the kernel)."""
+def traffic_from_profile(tb: int, occ: int):
+    """Per-frame counters of the ray-cast kernel for warp tile `tb` (beams per
+    warp) and occupancy variant `occ` from the committed ncu summary, if they
+    were taken on the current kernel sources (else None: the counters no
+    longer describe the kernel): {"dram": DRAM bytes read + written, "l2": L2
+    bytes (lts__t_bytes)}."""
     path = os.path.join(ROOT, "profiles", "k_trace_dram.txt")
     if not os.path.exists(path):
         return None
     kv = {}
     for line in open(path):
-        if ":" in line:
+        if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("ray_cast_sources_sha256_16") != ray_cast_sources_sha() or "dram_bytes_per_frame" not in kv:
+    pre = f"tb{tb}_occ{occ}_"
+    if kv.get("ray_cast_sources_sha256_16") != ray_cast_sources_sha() or pre + "dram_bytes_per_frame" not in kv:
         return None
-    return float(kv["dram_bytes_per_frame"])
+    return {"dram": float(kv[pre + "dram_bytes_per_frame"]), "l2": float(kv[pre + "l2_bytes_per_frame"])}
+
+
+def l2_read_peak(son, dev, stream):
+    """Measured L2 read rate (GB/s): the library's probe reads a 32 MiB buffer
+    (a quarter of L2) 40 times per launch with L2-cached 16-byte loads on 4
+    blocks of 512 per SM; best of 5 launches after 2 warm-ups."""
+    import torch
+    buf = torch.ones(8 << 20, dtype=torch.float32, device=dev)
+    blocks = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    passes = 40
+    best = None
+    with torch.cuda.stream(stream):
+        for r in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            son.probe_l2_read(buf, passes, blocks, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if r >= 2:
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+    del buf
+    return {"gbs": (8 << 20) * 4 * passes / (best / 1000.0) / 1e9, "buffer_mib": 32, "passes": passes,
+            "blocks": blocks, "how": "sonar_probe_l2_read: 16-byte ld.global.cg loads, best of 5 launches"}
 
 
 def run_ours(args):
@@ -659,11 +687,24 @@ def run_ours(args):
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    tb = traffic_from_profile()
+    tune_row = [r for r in son.tune_get().tolist() if r[:4] == [base.n_beams, base.n_elev, base.n_range_bins,
+                                                                 base.n_az_bins]]
+    tb = traffic_from_profile(tune_row[0][5], tune_row[0][7]) if tune_row else None
     if uw is not None:
         uw["roofline"].update({"peak": peak, "frac": uw["roofline"]["achieved"] / peak})
+    l2 = None
+    if rank == 0:
+        l2p = l2_read_peak(son, dev, stream)
+        l2 = {"peak": l2p["gbs"], "unit": "GB/s", "peak_source": l2p, "achieved": None, "frac": None,
+              "traffic": None}
+        if tb is not None:
+            l2["traffic"] = tb["l2"] * B
+            l2["achieved"] = l2["traffic"] / (trace_ms / 1000.0) / 1e9
+            l2["frac"] = l2["achieved"] / l2["peak"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tb * B if tb is not None else None),
+                "traffic": (tb["dram"] * B if tb is not None else None), "l2": l2,
+                "warp_tile": (f"{tune_row[0][5]} beams x {32 // tune_row[0][5]} elevations, occupancy variant "
+                              f"{tune_row[0][7]}" if tune_row else None),
                 "kernel": "k_trace (ray generation + LBVH walk + Moller-Trumbore + bin key)",
                 "avg_launch_ms": trace_ms, "algorithmic_bytes_per_launch": int(alg),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}

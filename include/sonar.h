@@ -392,6 +392,18 @@ sonar_status sonar_dvl_schedule(sonar_ctx_t ctx, const float* d_period, int64_t 
 sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
                                const sonar_params* params, void* stream, int64_t out[6]);
 
+/* L2 read bandwidth: reads the caller's buffer `passes` times over with
+ * 16-byte loads that are cached in L2 but not in L1, on n_blocks blocks of
+ * 512 threads, and writes each block's sum of the values it read (FP32) to
+ * d_block_sums[n_blocks].  A buffer well below the L2 size (e.g. 32 MiB)
+ * stays resident after the first pass, so bytes * passes / duration measures
+ * the L2 read rate that the ray cast's node and triangle fetches draw on.
+ * d_buf 16-byte aligned device memory of `bytes` (a multiple of 16, > 0);
+ * passes >= 1; 1 <= n_blocks <= 65535.  Errors: SONAR_ERR_ARG, before
+ * anything is enqueued. */
+sonar_status sonar_probe_l2_read(sonar_ctx_t ctx, const void* d_buf, int64_t bytes, int32_t passes,
+                                 float* d_block_sums, int32_t n_blocks, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

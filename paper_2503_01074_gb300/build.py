@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsonar.so")
-SOURCES = ["render.cu", "bvh_build.cu", "sonar_api.cu", "image.cu"]
-HEADERS = ["sonar_internal.cuh", "sonar_host.h"]
+SOURCES = ["trace.cu", "render.cu", "bvh_build.cu", "sonar_api.cu", "image.cu", "dvl.cu", "probe.cu"]
+HEADERS = ["sonar_internal.cuh", "devmath.cuh", "sonar_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

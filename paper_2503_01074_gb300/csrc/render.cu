@@ -1,8 +1,5 @@
-// Sonar rendering kernels (OceanSim, arXiv 2503.01074, Sec. III-A-2).
+// Sonar post-processing kernels (OceanSim, arXiv 2503.01074, Sec. III-A-2).
 //
-// k_trace             one ray per thread, warps on compact beam x elevation
-//                     patches: ray generation -> closest hit (LBVH walk,
-//                     Moller-Trumbore) -> range/azimuth bin -> 16-byte hit record.
 // k_bin               one work unit = whole azimuth columns of one sensor: the
 //                     units' hit records -> intensity (Eq. 2, two-way) -> polar
 //                     binning into a shared-memory column block -> Eq. 3-6 noise
@@ -11,462 +8,22 @@
 //                     memset of the image.
 // k_norm_rows         range-wise normalisation: one warp per range row takes the
 //                     row maximum of I~ and writes N = I~ / max.
-// k_fan_tiles         fan resample of the normalised image, tiles of pixels.
+// k_fan_*             fan resample of the normalised image: per-pixel polar
+//                     coordinate tables, then bilinear gathers for up to 8
+//                     frames per table read.
 // adjoint             per-group (row) Jacobian terms, then a per-ray gather of
 //                     dL/dP into (dalpha, dgain, dmu) over ray chunks, and a
 //                     fixed-order final reduction (deterministic).
-//
-// Ray casting precision: the walk and the triangle tests run in FP32.  A test
-// whose barycentric or distance outcome lies inside a certified FP32 error
-// bound, and any two candidates within 2e-5 t of each other, are re-decided
-// exactly in float-float arithmetic (about 48 significant bits, on the FP32
-// pipes) against the exact ray, whose direction comes from per-sensor sin/cos
-// tables computed in FP64 once; hit decisions therefore agree with an FP64
-// reference except for genuinely ambiguous rays.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
 
 #include "sonar_host.h"
 #include "sonar_internal.cuh"
+#include "devmath.cuh"
 
 namespace sonar {
 namespace {
-
-__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
-__device__ __forceinline__ float3 sub(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float l1(float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); }
-
-// ---------------------------------------------------------------------------
-// rays
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float3 ray_dir32(const SensorDev& s, int i, int j) {
-    const float phi = fmaf((float)i + 0.5f, s.hfov / (float)s.nb, -0.5f * s.hfov);
-    const float th = fmaf((float)j + 0.5f, s.vfov / (float)s.ne, -0.5f * s.vfov);
-    float sp, cp, st, ct;
-    sincosf(phi, &sp, &cp);
-    sincosf(th, &st, &ct);
-    const float dx = sp * ct, dy = cp * ct, dz = st;
-    const float3 w = f3(fmaf(s.rot[0], dx, fmaf(s.rot[1], dy, s.rot[2] * dz)),
-                        fmaf(s.rot[3], dx, fmaf(s.rot[4], dy, s.rot[5] * dz)),
-                        fmaf(s.rot[6], dx, fmaf(s.rot[7], dy, s.rot[8] * dz)));
-    const float inv = 1.0f / sqrtf(dot3(w, w));
-    return f3(w.x * inv, w.y * inv, w.z * inv);
-}
-
-// ---- float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2 ----
-// Error-free transforms (Knuth's two-sum, FMA-based two-product) carried out
-// with explicit round-to-nearest operations so that no contraction or
-// reassociation can change them.  About 48 significand bits, all on the FP32
-// pipes.
-struct ff {
-    float hi, lo;
-};
-
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ ff ff_quick(float a, float b) {   // requires |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    ff s = ff_two_sum(a.hi, b.hi);
-    const ff t = ff_two_sum(a.lo, b.lo);
-    s = ff_quick(s.hi, __fadd_rn(s.lo, t.hi));
-    return ff_quick(s.hi, __fadd_rn(s.lo, t.lo));
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return ff_quick(p, e);
-}
-__device__ __forceinline__ ff ff_mulf(ff a, float b) {
-    const float p = __fmul_rn(a.hi, b);
-    const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
-    return ff_quick(p, e);
-}
-__device__ __forceinline__ int ff_sign(ff a) {
-    return a.hi > 0.0f ? 1 : a.hi < 0.0f ? -1 : (a.lo > 0.0f ? 1 : a.lo < 0.0f ? -1 : 0);
-}
-__device__ __forceinline__ ff ff_dot(const ff a[3], const ff b[3]) {
-    return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
-}
-
-// The exact ray of (i, j) in float-float, unnormalised: w = R ds with ds from
-// the sensor's float-float sine/cosine tables (beam i, elevation j).  The hit
-// decisions below only use signs and ratios, which a positive scale leaves
-// unchanged.
-__device__ __forceinline__ void ray_dir_ff(const SensorDev& s, int i, int j, ff w[3]) {
-    const float4 bp = __ldg(s.trig + i), el = __ldg(s.trig + s.nb + j);
-    const ff sp{bp.x, bp.y}, cp{bp.z, bp.w}, st{el.x, el.y}, ct{el.z, el.w};
-    const ff ds[3] = {ff_mul(sp, ct), ff_mul(cp, ct), st};
-    for (int a = 0; a < 3; ++a)
-        w[a] = ff_add(ff_add(ff_mulf(ds[0], s.rot[3 * a]), ff_mulf(ds[1], s.rot[3 * a + 1])),
-                      ff_mulf(ds[2], s.rot[3 * a + 2]));
-}
-
-// ---------------------------------------------------------------------------
-// ray / triangle
-// ---------------------------------------------------------------------------
-
-// FP32 Moller-Trumbore with a certified error bound.  Returns 0 for a certain
-// miss, 1 for a certain hit (t set), 2 when FP32 cannot decide.  Each bound is
-// g * (product of the magnitudes entering the numerator) / |det|, with
-// g = 2^-19 (32 unit roundoffs), which covers the rounding of the edge vectors,
-// of the FP32 direction against the exact one, and of the cross and dot
-// products.
-__device__ __forceinline__ int mt32(float3 o, float3 d, float4 a, float4 b, float4 c, float& t) {
-    const float3 v0 = f3(a.x, a.y, a.z);
-    const float3 e1 = sub(f3(b.x, b.y, b.z), v0), e2 = sub(f3(c.x, c.y, c.z), v0);
-    const float3 p = cross3(d, e2);
-    const float det = dot3(e1, p);
-    const float3 s = sub(o, v0);
-    const float3 q = cross3(s, e1);
-    const float un = dot3(s, p), vn = dot3(d, q), tn = dot3(e2, q);
-    const float g = 0x1p-19f;
-    const float ad = l1(d), as = l1(s), ae1 = l1(e1), ae2 = l1(e2);
-    const float Edet = g * ae1 * ad * ae2;
-    const float adet = fabsf(det);
-    if (adet <= Edet) return 2;   // near-parallel: decided exactly
-    const float inv = 1.0f / det;
-    const float u = un * inv, v = vn * inv, w = 1.0f - u - v;
-    t = tn * inv;
-    const float ia = 1.0f / adet;
-    const float eu = (g * as * ad * ae2 + fabsf(u) * Edet) * ia;
-    const float ev = (g * ad * as * ae1 + fabsf(v) * Edet) * ia;
-    const float ew = eu + ev + 0x1p-22f;
-    const float et = (g * ae2 * as * ae1 + fabsf(t) * Edet) * ia;
-    if (u < -eu || v < -ev || w < -ew || t < -et) return 0;
-    if (u > eu && v > ev && w > ew && t > et) return 1;
-    return 2;
-}
-
-// Moller-Trumbore on the exact ray in float-float, without division: with
-// D = |det| and U, V, T the u, v, t numerators times sign(det), the test
-// "det != 0, u >= 0, v >= 0, u + v <= 1, t > 0" becomes
-// "D != 0, U >= 0, V >= 0, D - U - V >= 0, T > 0"; t = T / D along w.
-// Edge vectors and s = o - v0 are exact (two-sum of FP32 inputs).
-__device__ __forceinline__ bool mt_ff(const float o[3], const ff d[3], float4 a, float4 b, float4 c, ff& D,
-                                      ff& T) {
-    const ff e1[3] = {ff_two_sum(b.x, -a.x), ff_two_sum(b.y, -a.y), ff_two_sum(b.z, -a.z)};
-    const ff e2[3] = {ff_two_sum(c.x, -a.x), ff_two_sum(c.y, -a.y), ff_two_sum(c.z, -a.z)};
-    const ff sv[3] = {ff_two_sum(o[0], -a.x), ff_two_sum(o[1], -a.y), ff_two_sum(o[2], -a.z)};
-    const ff p[3] = {ff_sub(ff_mul(d[1], e2[2]), ff_mul(d[2], e2[1])),
-                     ff_sub(ff_mul(d[2], e2[0]), ff_mul(d[0], e2[2])),
-                     ff_sub(ff_mul(d[0], e2[1]), ff_mul(d[1], e2[0]))};
-    const ff det = ff_dot(e1, p);
-    const int sg = ff_sign(det);
-    if (sg == 0) return false;
-    ff u = ff_dot(sv, p);
-    const ff q[3] = {ff_sub(ff_mul(sv[1], e1[2]), ff_mul(sv[2], e1[1])),
-                     ff_sub(ff_mul(sv[2], e1[0]), ff_mul(sv[0], e1[2])),
-                     ff_sub(ff_mul(sv[0], e1[1]), ff_mul(sv[1], e1[0]))};
-    ff v = ff_dot(d, q);
-    ff t = ff_dot(e2, q);
-    D = det;
-    if (sg < 0) { D = ff_neg(det); u = ff_neg(u); v = ff_neg(v); t = ff_neg(t); }
-    if (ff_sign(u) < 0 || ff_sign(v) < 0 || ff_sign(ff_sub(ff_sub(D, u), v)) < 0 || ff_sign(t) <= 0) return false;
-    T = t;
-    return true;
-}
-
-// ---------------------------------------------------------------------------
-// closest hit: LBVH walk with a short stack
-// ---------------------------------------------------------------------------
-
-// The exact decisions, out of line (rarely needed; they would otherwise add
-// registers to the FP32 walk) and in float-float on the FP32 pipes.
-//
-// exact_hit: does the exact ray of (i, j) hit the triangle?  *t = the hit
-// distance in FP32.
-__device__ __noinline__ bool exact_hit(const SensorDev& s, int i, int j, float4 a, float4 b, float4 c, float* t) {
-    ff w[3];
-    ray_dir_ff(s, i, j, w);
-    const float o[3] = {s.pos[0], s.pos[1], s.pos[2]};
-    ff D, T;
-    if (!mt_ff(o, w, a, b, c, D, T)) return false;
-    const float len = sqrtf(w[0].hi * w[0].hi + w[1].hi * w[1].hi + w[2].hi * w[2].hi);
-    *t = (T.hi / D.hi) * len;
-    return true;
-}
-
-// exact_closer: along the exact ray of (i, j), is triangle `p` (index id_p) the
-// closest-hit choice over triangle `q` (index id_q)?  Nearer exact distance
-// first (T_p / D_p < T_q / D_q, compared as T_p D_q < T_q D_p), then the lower
-// index; a triangle the exact ray misses never wins.
-__device__ __noinline__ bool exact_closer(const SensorDev& s, int i, int j, const float4* p, uint32_t id_p,
-                                          const float4* q, uint32_t id_q) {
-    ff w[3];
-    ray_dir_ff(s, i, j, w);
-    const float o[3] = {s.pos[0], s.pos[1], s.pos[2]};
-    ff Dp, Tp, Dq, Tq;
-    if (!mt_ff(o, w, __ldg(p), __ldg(p + 1), __ldg(p + 2), Dp, Tp)) return false;
-    if (!mt_ff(o, w, __ldg(q), __ldg(q + 1), __ldg(q + 2), Dq, Tq)) return true;
-    const int c = ff_sign(ff_sub(ff_mul(Tp, Dq), ff_mul(Tq, Dp)));
-    return c < 0 || (c == 0 && id_p < id_q);
-}
-
-// Float-float sine and cosine tables of the sensor's beam azimuths
-// phi_i = -H/2 + (i + 1/2) H / N_b and elevations theta_j = -V/2 + (j + 1/2) V / N_e
-// (computed in FP64 once per sensor, split into hi + lo floats): trig[i] for
-// beams, trig[N_b + j] for elevations, each (sin hi, sin lo, cos hi, cos lo).
-__global__ void k_trig(const SensorDev* sensors, SensorDev one) {
-    const SensorDev& s = sensors ? sensors[blockIdx.y] : one;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= s.nb + s.ne) return;
-    double a;
-    if (k < s.nb) {
-        const double H = s.hfov;
-        a = -H / 2.0 + (k + 0.5) * H / s.nb;
-    } else {
-        const double V = s.vfov;
-        a = -V / 2.0 + (k - s.nb + 0.5) * V / s.ne;
-    }
-    double sn, cs;
-    sincos(a, &sn, &cs);
-    const float sh = (float)sn, ch = (float)cs;
-    s.trig[k] = make_float4(sh, (float)(sn - (double)sh), ch, (float)(cs - (double)ch));
-}
-
-// Range bin of a hit, or -1 when r is outside [r_min, r_max).
-__device__ __forceinline__ int range_bin(const SensorDev& s, float r) {
-    if (!(r >= s.rmin && r < s.rmax)) return -1;
-    const int br = (int)floorf((r - s.rmin) * s.inv_dr);
-    return br < s.nr - 1 ? br : s.nr - 1;
-}
-
-// Azimuth bin of beam i: floor((2i + 1) naz / (2 nb)), in 32-bit integers when
-// the product fits (it does whenever nb * naz < 2^30).
-__device__ __forceinline__ int az_bin(const SensorDev& s, int i) {
-    if ((int64_t)s.nb * s.naz < (1ll << 30)) return (int)(((2u * i + 1u) * (uint32_t)s.naz) / (2u * (uint32_t)s.nb));
-    return (int)(((2ll * i + 1) * s.naz) / (2ll * s.nb));
-}
-
-// Exact uint -> float for v < 2^23 without a conversion instruction.
-__device__ __forceinline__ float small_u2f(uint32_t v) {
-    return __uint_as_float(0x4B000000u | v) - 8388608.0f;
-}
-
-// ---------------------------------------------------------------------------
-// trace: one ray per thread, hit record out
-// ---------------------------------------------------------------------------
-
-// Each block is one warp on a tile of tb beams x (32 / tb) elevations of one
-// sensor: lane l traces beam i0 + l % tb, elevation j0 + l / tb, so that the
-// warp's rays sample a compact patch of the field of view.  (One-warp blocks
-// free their slot as soon as their rays are done.)  Records go to their
-// canonical index i * n_elev + j.
-//
-// The walk over the 4-wide hierarchy is a while-while loop: a lane descends
-// nearest child first, pushing the other entered children; a lane that
-// reaches a leaf parks it and keeps descending until every active lane of the
-// warp holds one, so that the triangle tests run together.  A lane whose ray
-// is finished writes its record at once and idles until the warp is done.
-// With STATS the kernel also counts node visits and triangle tests and marks
-// the nodes and triangles it touches (records are then not written).
-template <int MINB, bool STATS>
-__global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
-    __shared__ SensorDev S;
-    __shared__ SceneDev SC;
-    __shared__ int s_tile;
-    if (threadIdx.x == 0) {
-        if (a.sensors) {
-            const int2 m = a.block_map[blockIdx.x];
-            S = a.sensors[m.x];
-            SC = a.scenes[S.scene];
-            s_tile = m.y;
-        } else {
-            S = a.one;
-            SC = a.one_scene;
-            s_tile = blockIdx.x;
-        }
-    }
-    __syncthreads();
-    const int tb = S.tb, te = 32 / S.tb;
-    const int tiles_b = (S.nb + tb - 1) / tb;
-    const int ty = s_tile / tiles_b, tx = s_tile - ty * tiles_b;
-    const int lane = threadIdx.x;
-    const int ri = tx * tb + (lane % tb);
-    const int rj = ty * te + lane / tb;
-    const SceneDev& sc = SC;
-    const sonar_params& p = a.params;
-    const float tlimit = p.clip_tmax ? S.rmax : CUDART_INF_F;
-    const float3 o = f3(S.pos[0], S.pos[1], S.pos[2]);
-    const bool inside = ri < S.nb && rj < S.ne;
-    const float3 d = inside ? ray_dir32(S, ri, rj) : f3(0.0f, 0.0f, 1.0f);
-    const float tiny = 1e-20f;
-    const float3 inv = f3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
-                          1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
-                          1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
-    const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
-    int32_t stack[kStackMax];
-    int sp = 0, best = -1;
-    uint32_t best_id = 0xFFFFFFFFu;
-    float best_t = tlimit;
-    uint64_t visits = 0, tests = 0, exact_n = 0;
-    // `node`: the internal node to visit next (or kEmpty); `leaf`: a parked
-    // leaf whose triangles wait to be tested (0 = none; leaf handles are negative)
-    int32_t node = inside ? sc.root : kEmpty, leaf = 0;
-    if (node < 0 && node != kEmpty) { leaf = node; node = kEmpty; }
-    bool live = inside;
-    for (;;) {
-        if (live) {
-            while (node >= 0) {
-                const float4* pn = sc.nodes + 8 * (int64_t)node;
-                const float4 lx = __ldg(pn), hx = __ldg(pn + 1), ly = __ldg(pn + 2), hy = __ldg(pn + 3);
-                const float4 lz = __ldg(pn + 4), hz = __ldg(pn + 5);
-                const int4 ch = __ldg(reinterpret_cast<const int4*>(pn + 6));
-                if (STATS) {
-                    ++visits;
-                    atomicOr(a.tc.node_bits + (node >> 5), 1u << (node & 31));
-                }
-                const float tcut = best_t * 1.00002f;
-                const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
-                const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
-                const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
-                const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
-                // sort key per child: entry distance bits (>= 0, so integer order
-                // is distance order) with the child slot in the two low bits; a
-                // missed child sorts last as 0xFFFFFFFF
-                uint32_t key[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
-                    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-                    t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
-                    lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
-                    t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
-                    lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
-                    const bool hit = hs[c] != kEmpty && lo <= hi * 1.0000005f;
-                    key[c] = hit ? ((__float_as_uint(lo) & ~3u) | (uint32_t)c) : 0xFFFFFFFFu;
-                }
-#define SONAR_USORT(x, y)                                    \
-                {                                            \
-                    const uint32_t mn = min(key[x], key[y]); \
-                    key[y] = max(key[x], key[y]);            \
-                    key[x] = mn;                             \
-                }
-                SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
-#undef SONAR_USORT
-                const int nhit = (key[0] != 0xFFFFFFFFu) + (key[1] != 0xFFFFFFFFu) + (key[2] != 0xFFFFFFFFu) +
-                                 (key[3] != 0xFFFFFFFFu);
-                if (nhit == 0) {
-                    node = sp > 0 ? stack[--sp] : kEmpty;
-                } else {
-                    if (sp + nhit - 1 > kStackMax) {   // cannot happen for a checked height: give up the ray
-                        atomicOr(a.err, SONAR_DEVERR_STACK);
-                        node = kEmpty;
-                        leaf = 0;
-                        sp = 0;
-                        best = -1;
-                        break;
-                    }
-#pragma unroll
-                    for (int c = 3; c >= 1; --c) {
-                        if (c < nhit) {
-                            const uint32_t k = key[c] & 3u;
-                            stack[sp++] = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-                        }
-                    }
-                    const uint32_t k = key[0] & 3u;
-                    node = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-                }
-                if (node < 0 && node != kEmpty && leaf == 0) {   // park the leaf, keep descending
-                    leaf = node;
-                    node = sp > 0 ? stack[--sp] : kEmpty;
-                }
-                if (!__any_sync(__activemask(), leaf == 0)) break;
-            }
-            while (leaf != 0) {
-                // a run of triangles in leaf order
-                const int32_t x = ~leaf;
-                const int32_t first = x >> 3, count = (x & 7) + 1;
-                for (int k = 0; k < count; ++k) {
-                    const int32_t f = first + k;
-                    if (f >= sc.n_tris) {
-                        atomicOr(a.err, SONAR_DEVERR_INDEX);
-                        break;
-                    }
-                    const float4* tp = sc.tris + 3 * (int64_t)f;
-                    const float4 va = __ldg(tp), vb = __ldg(tp + 1), vc = __ldg(tp + 2);
-                    if (STATS) {
-                        ++tests;
-                        atomicOr(a.tc.tri_bits + (f >> 5), 1u << (f & 31));
-                    }
-                    float t;
-                    const int r = mt32(o, d, va, vb, vc, t);
-                    if (r == 0) continue;
-                    if (r == 2) {
-                        if (STATS) ++exact_n;
-                        if (!exact_hit(S, ri, rj, va, vb, vc, &t)) continue;
-                    }
-                    if (!(t < tlimit)) continue;
-                    const uint32_t id = __float_as_uint(vb.w);
-                    bool take;
-                    if (best < 0) {
-                        take = true;
-                    } else if (fabsf(t - best_t) <= 2e-5f * fmaxf(t, best_t)) {
-                        // near tie: decide on the exact distances, then on the caller's index
-                        if (STATS) ++exact_n;
-                        take = exact_closer(S, ri, rj, tp, id, sc.tris + 3 * (int64_t)best, best_id);
-                    } else {
-                        take = t < best_t;
-                    }
-                    if (take) {
-                        best = f;
-                        best_id = id;
-                        best_t = t;
-                    }
-                }
-                leaf = 0;
-                if (node < 0 && node != kEmpty) {   // the next stacked entry is a leaf too
-                    leaf = node;
-                    node = sp > 0 ? stack[--sp] : kEmpty;
-                }
-            }
-        }
-        if (live && node == kEmpty) {
-            // the ray is finished: its hit record (bin key, triangle, range, incidence)
-            live = false;
-            if (!STATS) {
-                uint32_t key = kNoKey, orig = 0xFFFFFFFFu, cosb = 0u;
-                float tr = CUDART_INF_F;
-                if (best >= 0) {
-                    const float4* tp = sc.tris + 3 * (int64_t)best;
-                    const float4 va = __ldg(tp), vb = __ldg(tp + 1), vc = __ldg(tp + 2);
-                    const float3 v0 = f3(va.x, va.y, va.z);
-                    const float3 n = cross3(sub(f3(vb.x, vb.y, vb.z), v0), sub(f3(vc.x, vc.y, vc.z), v0));
-                    const float dn = dot3(d, n) / sqrtf(dot3(n, n));
-                    orig = __float_as_uint(vb.w);
-                    tr = best_t;
-                    cosb = __float_as_uint(p.two_sided ? fabsf(dn) : fmaxf(-dn, 0.0f));
-                    const int br = range_bin(S, best_t);
-                    if (br >= 0) key = (uint32_t)(br * S.naz + az_bin(S, ri));
-                }
-                *reinterpret_cast<uint4*>(a.hits + S.hits_off + (int64_t)ri * S.ne + rj) =
-                    make_uint4(key, orig, __float_as_uint(tr), cosb);
-            }
-        }
-        if (__ballot_sync(0xFFFFFFFFu, live) == 0u) break;
-    }
-    if (STATS) {
-        atomicAdd(a.tc.visits, (unsigned long long)visits);
-        atomicAdd(a.tc.tests, (unsigned long long)tests);
-        atomicAdd(a.tc.exact, (unsigned long long)exact_n);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // bin + noise: one work unit = whole azimuth columns of one sensor
@@ -1120,218 +677,6 @@ __global__ void __launch_bounds__(256) k_adj_final(const double* partials, int n
     }
     if (threadIdx.x == 0) dtheta[q] = (float)red[0];
 }
-
-// ---------------------------------------------------------------------------
-// counters
-// ---------------------------------------------------------------------------
-
-__global__ void k_popcount(const uint32_t* bits, int64_t words, unsigned long long* out) {
-    unsigned long long c = 0;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x)
-        c += __popc(bits[w]);
-    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
-}
-
-// ---------------------------------------------------------------------------
-// DVL (Sec. III-A-3): four-beam Janus ranges, least-squares velocity, rate
-// ---------------------------------------------------------------------------
-
-// Closest hit along one ray (any origin and direction) by a per-thread walk
-// of the 4-wide hierarchy: certified FP32 Moller-Trumbore, undecided tests
-// decided exactly in float-float on the FP32 direction; ties go to the lower
-// caller index.  Returns the distance (+inf for a miss).
-__device__ float closest_distance(const SceneDev& sc, float3 o, float3 d, float tmax, uint32_t* err) {
-    if (sc.root == kEmpty) return CUDART_INF_F;
-    const float tiny = 1e-20f;
-    const float3 inv = f3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
-                          1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
-                          1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
-    const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
-    const float of[3] = {o.x, o.y, o.z};
-    const ff dff[3] = {ff{d.x, 0.0f}, ff{d.y, 0.0f}, ff{d.z, 0.0f}};
-    int32_t stack[kStackMax];
-    int sp = 0;
-    float best_t = tmax;
-    uint32_t best_id = 0xFFFFFFFFu;
-    int32_t node = sc.root;
-    while (node != kEmpty) {
-        if (node < 0) {
-            const int32_t x = ~node;
-            const int32_t first = x >> 3, count = (x & 7) + 1;
-            for (int k = 0; k < count; ++k) {
-                const int32_t f = first + k;
-                if (f >= sc.n_tris) {
-                    atomicOr(err, SONAR_DEVERR_INDEX);
-                    break;
-                }
-                const float4* tp = sc.tris + 3 * (int64_t)f;
-                const float4 va = __ldg(tp), vb = __ldg(tp + 1), vc = __ldg(tp + 2);
-                float t;
-                const int r = mt32(o, d, va, vb, vc, t);
-                if (r == 0) continue;
-                if (r == 2) {
-                    ff D, T;
-                    if (!mt_ff(of, dff, va, vb, vc, D, T)) continue;
-                    t = T.hi / D.hi;
-                }
-                const uint32_t id = __float_as_uint(vb.w);
-                if (t < best_t || (t == best_t && id < best_id)) {
-                    best_t = t;
-                    best_id = id;
-                }
-            }
-            node = sp > 0 ? stack[--sp] : kEmpty;
-            continue;
-        }
-        const float4* pn = sc.nodes + 8 * (int64_t)node;
-        const float4 lx = __ldg(pn), hx = __ldg(pn + 1), ly = __ldg(pn + 2), hy = __ldg(pn + 3);
-        const float4 lz = __ldg(pn + 4), hz = __ldg(pn + 5);
-        const int4 ch = __ldg(reinterpret_cast<const int4*>(pn + 6));
-        const float tcut = best_t * 1.00002f;
-        const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
-        const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
-        const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
-        uint32_t key[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
-            float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-            t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
-            lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
-            t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
-            lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
-            const bool hit = hs[c] != kEmpty && lo <= hi * 1.0000005f;
-            key[c] = hit ? ((__float_as_uint(lo) & ~3u) | (uint32_t)c) : 0xFFFFFFFFu;
-        }
-#define SONAR_USORT(x, y)                                \
-        {                                                \
-            const uint32_t mn = min(key[x], key[y]);     \
-            key[y] = max(key[x], key[y]);                \
-            key[x] = mn;                                 \
-        }
-        SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
-#undef SONAR_USORT
-        const int nhit = (key[0] != 0xFFFFFFFFu) + (key[1] != 0xFFFFFFFFu) + (key[2] != 0xFFFFFFFFu) +
-                         (key[3] != 0xFFFFFFFFu);
-        if (nhit == 0) {
-            node = sp > 0 ? stack[--sp] : kEmpty;
-            continue;
-        }
-        if (sp + nhit - 1 > kStackMax) {   // cannot happen for a checked depth: give up the ray
-            atomicOr(err, SONAR_DEVERR_STACK);
-            return CUDART_INF_F;
-        }
-        for (int c = nhit - 1; c >= 1; --c) {
-            const uint32_t k = key[c] & 3u;
-            stack[sp++] = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-        }
-        const uint32_t k = key[0] & 3u;
-        node = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-    }
-    return best_id == 0xFFFFFFFFu ? CUDART_INF_F : best_t;
-}
-
-// A standard normal from two Philox words: the cosine branch of Box-Muller.
-__device__ __forceinline__ float normal_of(uint32_t a, uint32_t b) {
-    const float u2 = fmaf((float)b, 0x1p-32f, 0x1p-32f);
-    return sqrt_nonneg(neg2log_u(a)) * cospif(2.0f * u2);
-}
-
-// Four lanes per pose, lane k casting beam k; the group's first lane fits the
-// velocity by least squares over the valid beams (Cramer's rule on the 3 x 3
-// normal equations) and writes the pose's outputs.
-__global__ void __launch_bounds__(128) k_dvl(DvlArgs a) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t p = g >> 2;
-    const int k = (int)(g & 3);
-    const int lane = threadIdx.x & 31, base = lane & ~3;
-    const unsigned grp = 0xFu << base;
-    const bool live = p < a.n;
-    float range = CUDART_INF_F, u = 0.0f;
-    bool valid = false;
-    if (live) {
-        const float* q = a.pose + 12 * p;
-        const float3 o = f3(q[0], q[1], q[2]);
-        const float* R = q + 3;
-        const float bx = a.beam[k][0], by = a.beam[k][1], bz = a.beam[k][2];
-        float3 d = f3(fmaf(R[0], bx, fmaf(R[1], by, R[2] * bz)), fmaf(R[3], bx, fmaf(R[4], by, R[5] * bz)),
-                      fmaf(R[6], bx, fmaf(R[7], by, R[8] * bz)));
-        range = closest_distance(a.scene, o, d, CUDART_INF_F, a.err);
-        valid = range >= a.r_min && range <= a.r_max;
-        // sensor-frame velocity R^T v and this beam's radial velocity with noise
-        const float* vw = a.vel_world + 3 * p;
-        const float vs0 = fmaf(R[0], vw[0], fmaf(R[3], vw[1], R[6] * vw[2]));
-        const float vs1 = fmaf(R[1], vw[0], fmaf(R[4], vw[1], R[7] * vw[2]));
-        const float vs2 = fmaf(R[2], vw[0], fmaf(R[5], vw[1], R[8] * vw[2]));
-        const U4 x = philox10(U4{(uint32_t)p, (uint32_t)((uint64_t)p >> 32), 2u, (uint32_t)(k >> 1)},
-                              a.seed_lo, a.seed_hi);
-        const float w = (k & 1) ? normal_of(x.z, x.w) : normal_of(x.x, x.y);
-        u = fmaf(bx, vs0, fmaf(by, vs1, bz * vs2)) + a.sigma_b * w;
-        a.ranges[4 * p + k] = range;
-    }
-    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
-    float rr[4], uu[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        rr[j] = __shfl_sync(0xFFFFFFFFu, range, base + j);
-        uu[j] = __shfl_sync(0xFFFFFFFFu, u, base + j);
-    }
-    if (!live || k != 0) return;
-    const unsigned bits = (vm & grp) >> base;
-    const int nvalid = __popc(bits);
-    float A[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, y[3] = {0.f, 0.f, 0.f};
-    float far = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (!((bits >> j) & 1u)) continue;
-        far = fmaxf(far, rr[j]);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            y[r] = fmaf(a.beam[j][r], uu[j], y[r]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) A[r][c] = fmaf(a.beam[j][r], a.beam[j][c], A[r][c]);
-        }
-    }
-    int32_t flags = (int32_t)bits;
-    float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
-    const float det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
-                      A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-                      A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-    if (nvalid >= a.min_beams && det != 0.0f) {
-        const float id = 1.0f / det;
-        v0 = (y[0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (y[1] * A[2][2] - A[1][2] * y[2]) +
-              A[0][2] * (y[1] * A[2][1] - A[1][1] * y[2])) * id;
-        v1 = (A[0][0] * (y[1] * A[2][2] - A[1][2] * y[2]) - y[0] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-              A[0][2] * (A[1][0] * y[2] - y[1] * A[2][0])) * id;
-        v2 = (A[0][0] * (A[1][1] * y[2] - y[1] * A[2][1]) - A[0][1] * (A[1][0] * y[2] - y[1] * A[2][0]) +
-              y[0] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) * id;
-        flags |= 16;
-    }
-    a.vel[3 * p] = v0;
-    a.vel[3 * p + 1] = v1;
-    a.vel[3 * p + 2] = v2;
-    a.flags[p] = flags;
-    a.period[p] = (flags & 16) ? fmaf(a.t1, far, a.t0) : a.t_lost;
-}
-
-// Emission schedule: one thread per vehicle walks its steps (a measurement at
-// step 0, then max(1, ceil(period / dt)) steps after each measurement).
-__global__ void k_dvl_schedule(const float* period, int64_t n_veh, int64_t n_steps, float dt, int32_t* emit) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n_veh) return;
-    const float* P = period + v * n_steps;
-    int32_t* E = emit + v * n_steps;
-    for (int64_t s = 0; s < n_steps; ++s) E[s] = 0;
-    int64_t s = 0;
-    while (s < n_steps) {
-        E[s] = 1;
-        const float q = ceilf(P[s] / dt);
-        s += q >= 1.0f ? (int64_t)q : 1;
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1342,21 +687,6 @@ void set_kernel_attributes() {
     cudaFuncSetAttribute(k_bin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_bin<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-}
-
-cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_sensors, int max_angles,
-                        cudaStream_t st) {
-    const dim3 grid((unsigned)((max_angles + 127) / 128), (unsigned)n_sensors);
-    k_trig<<<grid, 128, 0, st>>>(sensors, one);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st) {
-    if (blocks > 0) {
-        if (occupancy >= 8) k_trace<32, false><<<blocks, 32, 0, st>>>(a);
-        else k_trace<4, false><<<blocks, 32, 0, st>>>(a);
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_bin(const BinArgs& a, int det, int grid, int block, size_t smem, cudaStream_t st) {
@@ -1419,35 +749,6 @@ int adjoint_blocks_per_sm(int block, size_t smem) {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k_adjoint, block, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
-}
-
-cudaError_t launch_dvl(const DvlArgs& a, cudaStream_t st) {
-    if (a.n > 0) k_dvl<<<(unsigned)((4 * a.n + 127) / 128), 128, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_dvl_schedule(const float* period, int64_t n_veh, int64_t n_steps, float dt, int32_t* emit,
-                                cudaStream_t st) {
-    if (n_veh > 0 && n_steps > 0) k_dvl_schedule<<<(unsigned)((n_veh + 127) / 128), 128, 0, st>>>(period, n_veh, n_steps, dt, emit);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,
-                         const TraceCounters& tc, uint32_t* err, cudaStream_t st) {
-    TraceArgs a{};
-    a.one = s;
-    a.one_scene = sc;
-    a.n_sensors = 1;
-    a.params = p;
-    a.err = err;
-    a.tc = tc;
-    if (s.trace_blocks > 0) k_trace<4, true><<<s.trace_blocks, 32, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out, cudaStream_t st) {
-    k_popcount<<<1024, 256, 0, st>>>(bits, words, out);
-    return cudaGetLastError();
 }
 
 }  // namespace sonar

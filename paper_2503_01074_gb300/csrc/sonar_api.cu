@@ -1,6 +1,6 @@
 // C ABI of libsonar: contexts, scenes, single-frame and batched rendering,
 // the adjoint, the autotuner and the counter mode.  Host code only; kernels
-// live in bvh_build.cu and render.cu.
+// live in bvh_build.cu, trace.cu, render.cu, image.cu and dvl.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1066,10 +1066,10 @@ namespace {
 
 sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
                                      const float* grad, const float* noised, const sonar_hit* hits, float* dtheta,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, bool events = false) {
     sonar_ctx* ctx = b->ctx;
     CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
-    CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
     if (!hits) {   // recompute the hit records with the ray-cast kernel into the batch scratch
         CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
         TraceArgs tr{};
@@ -1088,7 +1088,7 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
                            grad, b->d_rowinfo, s),
            "batch adjoint rows");
-    CU(cudaEventRecordWithFlags(b->ev[4], s, cudaEventRecordExternal), "cudaEventRecord");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[4], s, cudaEventRecordExternal), "cudaEventRecord");
     AdjArgs a{};
     a.sensors = b->d_sens;
     a.units = b->d_adj_units;
@@ -1109,7 +1109,7 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->adj_units.size(),
                                                                     (int64_t)ctx->sm_count * per_sm));
     CU(launch_adjoint(a, grid, b->block, smem, dtheta, s), "batch adjoint launch");
-    CU(cudaEventRecordWithFlags(b->ev[5], s, cudaEventRecordExternal), "cudaEventRecord");
+    if (events) CU(cudaEventRecordWithFlags(b->ev[5], s, cudaEventRecordExternal), "cudaEventRecord");
     return SONAR_OK;
 }
 
@@ -1149,7 +1149,7 @@ extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar
         if (b->bwd) cudaGraphExecDestroy(b->bwd);
         b->bwd = nullptr;
         CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
-        st = batch_backward_launches(b, p, d_theta, n_mat, d_grad, d_noised, d_hits, d_dtheta, b->cap);
+        st = batch_backward_launches(b, p, d_theta, n_mat, d_grad, d_noised, d_hits, d_dtheta, b->cap, true);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -1219,22 +1219,36 @@ extern "C" sonar_status sonar_batch_destroy(sonar_batch_t b) {
 
 namespace {
 
-// Times the batch's phase-1 + phase-2 launches (no graph) over `reps` runs.
+// Times the batch's forward launches, and its adjoint launches when `grad` is
+// given (no graph): the best over `rounds` of the mean of `reps` back-to-back
+// passes, after one warm-up pass; 1e30 when a launch sequence fails.
 float time_batch(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
-                 const sonar_batch_outputs* out, cudaStream_t s, int reps) {
+                 const sonar_batch_outputs* out, const float* grad, float* dtheta, cudaStream_t s, int reps,
+                 int rounds) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    batch_forward_launches(b, p, d_theta, n_mat, out, s);   // warm-up
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < reps; ++r) batch_forward_launches(b, p, d_theta, n_mat, out, s);
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    bool ok = true;
+    auto pass = [&] {
+        ok = ok && batch_forward_launches(b, p, d_theta, n_mat, out, s) == SONAR_OK;
+        if (grad)
+            ok = ok && batch_backward_launches(b, p, d_theta, n_mat, grad, out->noised, out->hits, dtheta, s) ==
+                           SONAR_OK;
+    };
+    pass();
+    float best = 1e30f;
+    for (int k = 0; k < rounds && ok; ++k) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r) pass();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms / reps);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return ms / reps;
+    return ok ? best : 1e30f;   // a candidate whose launches failed is never chosen
 }
 
 }  // namespace
@@ -1257,6 +1271,19 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
         if (std::find(shapes.begin(), shapes.end(), k) == shapes.end()) shapes.push_back(k);
     }
     const std::vector<sonar_batch_item> all = b->items;
+    // an upstream gradient for timing the adjoint: every element the float
+    // with bytes 0x3A (about 7e-4)
+    float* adj_grad = nullptr;
+    float* adj_dtheta = nullptr;
+    if (out->hits && out->noised) {
+        if (cudaMalloc(&adj_grad, sizeof(float) * std::max<int64_t>(1, b->total_polar)) != cudaSuccess ||
+            cudaMalloc(&adj_dtheta, sizeof(float) * (n_mat + 2)) != cudaSuccess ||
+            cudaMemsetAsync(adj_grad, 0x3A, sizeof(float) * std::max<int64_t>(1, b->total_polar), s) != cudaSuccess) {
+            if (adj_grad) cudaFree(adj_grad);
+            if (adj_dtheta) cudaFree(adj_dtheta);
+            return fail(ctx, SONAR_ERR_OOM, "autotune scratch");
+        }
+    }
     // per shape, timed on that shape's items alone
     for (const ShapeKey& k : shapes) {
         std::vector<sonar_batch_item> sub;
@@ -1274,12 +1301,15 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
                 ctx->tune[k] = Tune{0, tb, 128, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
                 if (batch_scratch(b, out) != cudaSuccess) { st = fail(ctx, SONAR_ERR_OOM, "batch scratch"); goto restore; }
-                const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
+                const float ms = time_batch(b, p, d_theta, n_mat, out, nullptr, nullptr, s, 3, 3);
                 if (cudaGetLastError() != cudaSuccess) continue;
                 if (ms < best_ms) { best_ms = ms; best.tb = tb; best.occ = occ; }
             }
         }
-        // then columns per binning unit and the binning block size
+        // then columns per binning unit and the binning block size (which also
+        // sets the adjoint's block and ray chunks): forward and, when the caller's
+        // outputs hold the hit records and I~, the adjoint of a constant
+        // upstream gradient too
         best_ms = 1e30f;
         const int tb = best.tb, occ = best.occ;
         for (int block : {64, 128, 256}) {
@@ -1288,7 +1318,16 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
                 ctx->tune[k] = Tune{cols, tb, block, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
                 if (batch_scratch(b, out) != cudaSuccess) { st = fail(ctx, SONAR_ERR_OOM, "batch scratch"); goto restore; }
-                const float ms = time_batch(b, p, d_theta, n_mat, out, s, 3);
+                const float* g = nullptr;
+                if (adj_grad) {
+                    if (cudaMalloc(&b->d_partials, sizeof(double) * b->adj_units.size() * (n_mat + 2)) != cudaSuccess) {
+                        st = fail(ctx, SONAR_ERR_OOM, "batch scratch");
+                        goto restore;
+                    }
+                    b->n_mat_cap = n_mat;
+                    g = adj_grad;
+                }
+                const float ms = time_batch(b, p, d_theta, n_mat, out, g, adj_dtheta, s, 3, 3);
                 if (cudaGetLastError() != cudaSuccess) continue;
                 if (ms < best_ms) { best_ms = ms; best = Tune{cols, tb, block, occ}; }
             }
@@ -1297,6 +1336,8 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
     }
 restore:
     b->items = all;
+    if (adj_grad) cudaFree(adj_grad);
+    if (adj_dtheta) cudaFree(adj_dtheta);
     {
         const sonar_status st2 = batch_plan(b);
         if (st == SONAR_OK) st = st2;
@@ -1463,6 +1504,19 @@ extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, con
     out[3] = (int64_t)h[4];
     out[4] = (int64_t)S.nb * S.ne;
     out[5] = (int64_t)h[2];
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_probe_l2_read(sonar_ctx_t ctx, const void* d_buf, int64_t bytes, int32_t passes,
+                                            float* d_block_sums, int32_t n_blocks, void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    if (!d_buf || !d_block_sums) return fail(ctx, SONAR_ERR_ARG, "NULL buffer");
+    if (bytes <= 0 || bytes % 16 != 0) return fail(ctx, SONAR_ERR_ARG, "bytes must be a positive multiple of 16");
+    if (reinterpret_cast<uintptr_t>(d_buf) % 16 != 0) return fail(ctx, SONAR_ERR_ARG, "buffer not 16-byte aligned");
+    if (passes < 1) return fail(ctx, SONAR_ERR_ARG, "passes < 1");
+    if (n_blocks < 1 || n_blocks > 65535) return fail(ctx, SONAR_ERR_ARG, "n_blocks outside [1, 65535]");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CU(launch_l2_read(d_buf, bytes, passes, d_block_sums, n_blocks, (cudaStream_t)stream), "probe launch");
     return SONAR_OK;
 }
 

@@ -30,7 +30,9 @@ inline SceneDev scene_dev(const SceneStore& s) {
     return SceneDev{s.nodes, s.tris, s.mat_orig, s.root, (int32_t)s.n_tris};
 }
 
-// Kernel launchers (render.cu).
+// Kernel launchers (trace.cu: ray cast and counters; render.cu: binning, noise,
+// normalisation, fan and adjoint; image.cu: Eq. 1 camera; dvl.cu: DVL;
+// probe.cu: L2 read-bandwidth probe).
 void set_kernel_attributes();
 cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_sensors, int max_angles,
                         cudaStream_t st);
@@ -56,5 +58,7 @@ cudaError_t launch_dvl_schedule(const float* period, int64_t n_veh, int64_t n_st
                                 cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t* bits, int64_t words, unsigned long long* out,
                             cudaStream_t st);
+cudaError_t launch_l2_read(const void* buf, int64_t bytes, int passes, float* block_sums, int n_blocks,
+                           cudaStream_t st);
 
 }  // namespace sonar

@@ -117,6 +117,8 @@ _SIG = {
                                      C.c_void_p]),
     "sonar_trace_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Sensor), C.POINTER(Params),
                                     C.c_void_p, C.POINTER(C.c_int64)]),
+    "sonar_probe_l2_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32,
+                                      C.c_void_p]),
 }
 
 _LIB = None
@@ -351,6 +353,15 @@ class Sonar:
         self._check(self.lib.sonar_dvl_schedule(self.h, _ptr(period), n_veh, n_steps, C.c_float(dt), _ptr(emit),
                                                 _stream(stream)))
         return emit
+
+    def probe_l2_read(self, buf, passes, n_blocks, stream=None):
+        """Reads the CUDA tensor `buf` (16-byte aligned, size a multiple of 16
+        bytes) `passes` times with L2-cached, L1-bypassing loads on n_blocks
+        blocks; returns the per-block sums (float32 [n_blocks])."""
+        sums = self.torch.empty(n_blocks, dtype=self.torch.float32, device=self.device)
+        self._check(self.lib.sonar_probe_l2_read(self.h, _ptr(buf), buf.numel() * buf.element_size(), passes,
+                                                 _ptr(sums), n_blocks, _stream(stream)))
+        return sums
 
     def tune_get(self):
         cnt = C.c_int32()

@@ -231,6 +231,23 @@ def test_trace_stats(son, tiny, tiny_sid):
     assert st["visits"] >= st["nodes_touched"] and st["tests"] >= st["tris_touched"]
 
 
+def test_l2_read_probe_reads_every_byte(son):
+    # a buffer of ones with a ragged length: the block sums add up to the
+    # number of floats times the passes, exactly (every partial sum is an
+    # integer below 2^24)
+    n = (1 << 20) + 12
+    buf = torch.ones(n, dtype=torch.float32, device=son.device)
+    for passes, blocks in ((1, 1), (3, 608), (2, 37)):
+        sums = son.probe_l2_read(buf, passes, blocks)
+        torch.cuda.synchronize()
+        assert sums.double().sum().item() == n * passes
+    for bad in ((buf[:3], 1, 4), (buf, 0, 4), (buf, 1, 0), (buf, 1, 70000), (buf[1:5], 1, 4)):
+        with pytest.raises(SonarError):
+            son.probe_l2_read(*bad)
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+
+
 def batch_items(son, tiny, tiny_sid):
     mesh, mu = tiny
     soup = S.random_soup(500, 9)
@@ -355,12 +372,29 @@ def test_autotune_keeps_results(son, tiny, tiny_sid):
     b.autotune(theta, prm)
     rows = son.tune_get()
     assert len(rows) >= 3
+    # both stages chose a measured candidate (a stage whose every candidate
+    # failed would leave the derived defaults, 0)
+    assert all(r[4] > 0 and r[5] > 0 for r in rows.tolist()), rows
     b.render(theta, prm)
     torch.cuda.synchronize()
     for k, (sid, spec, seed, frame) in enumerate(items):
         single = son.render(sid, spec, theta, prm, seed, frame)
         # elevation-lane mapping keeps the canonical fold order: any tile shape gives the same bits
         assert torch.equal(b.view(k)["polar"], single["polar"]), k
+    # the tuner timed the adjoint on its own scratch: the tuned batch's adjoint
+    # still equals the sum of the single-frame adjoints
+    G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(3)).to(son.device)
+    d_b = b.backward(theta, prm, G, hits=True)
+    total = torch.zeros_like(theta, dtype=torch.float64)
+    for k, (sid, spec, seed, frame) in enumerate(items):
+        v = b.view(k)
+        p0 = b.layout[k][0]
+        g = G[p0:p0 + spec.n_range_bins * spec.n_az_bins].view(spec.n_range_bins, spec.n_az_bins)
+        total += son.backward(sid, spec, theta, prm, seed, frame, g, v["noised"], v["hits"]).double()
+    torch.cuda.synchronize()
+    assert torch.allclose(d_b.double(), total, rtol=1e-5, atol=1e-6 * float(total.abs().max()))
+    st, bits = son.check()
+    assert st == 0 and bits == 0
     b.close()
 
 
