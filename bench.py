@@ -303,8 +303,27 @@ def timed(fn, steps, stream):
     return float(np.mean(ms))
 
 
-def measure_configs(son, steps):
-    """Throughput of the other workload configurations (not the headline line)."""
+def trace_roofline(son, items, trace_ms, peak, scale=1.0):
+    """The ray-cast launch's HBM roofline for a batch: algorithmic bytes (per
+    item, the distinct 128-byte nodes and 48-byte triangles its rays touch
+    plus a 16-byte record per ray, from the counter mode) over the launch's
+    in-graph time.  `items` may be a sample of the batch, `scale` the batch
+    size over the sample size."""
+    from paper_2503_01074_gb300.sonar import RenderParams
+    alg = 0
+    for sid, spec in items:
+        st = son.trace_stats(sid, spec, RenderParams())
+        alg += st["nodes_touched"] * 128 + st["tris_touched"] * 48 + spec.n_rays * 16
+    alg *= scale
+    gbs = alg / (trace_ms / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "algorithmic_bytes_per_launch": int(alg), "avg_launch_ms": trace_ms,
+            "sample": f"{len(items)} of {int(round(len(items) * scale))} items"}
+
+
+def measure_configs(son, steps, peak):
+    """Throughput of the other workload configurations (not the headline line),
+    each with its ray-cast launch's HBM roofline."""
     import torch
     from paper_2503_01074_gb300 import scenes as S
     from paper_2503_01074_gb300.sonar import RenderParams
@@ -326,9 +345,13 @@ def measure_configs(son, steps):
         for (sid, spec, seed, fr), o in zip(items, outs):
             son.render(sid, spec, theta, prm, seed, fr, hits=True, fan=True, outputs=o)
     ms_s = timed(singles, max(2, steps // 2), stream)
+    b.render(theta, prm, hits=True, fan=True)
+    ph = b.timings()
     out["heterogeneous_batch"] = {"sensors": len(items), "rays": rays, "batched_fwd_fps": len(items) / ms_b * 1e3,
                                   "single_fwd_fps": len(items) / ms_s * 1e3,
-                                  "batched_Mrays_s": rays / ms_b / 1e3, "speedup": ms_s / ms_b}
+                                  "batched_Mrays_s": rays / ms_b / 1e3, "speedup": ms_s / ms_b, "phase_ms": ph,
+                                  "roofline": trace_roofline(son, [(sid, spec) for sid, spec, _, _ in items],
+                                                             ph["trace"], peak)}
     b.close()
     del outs
     for sid in sids:
@@ -357,10 +380,13 @@ def measure_configs(son, steps):
             b.render(theta, prm, hits=False, fan=False)
             b.backward(theta, prm, G, hits=False, out=d)
         ms = timed(fwd_adj, max(2, steps // 2), stream)
+        ph = b.timings()
         out[name] = {"tris": mesh.n_tris, "materials": n_mat, "frames": len(poses), "rays_per_frame": base.n_rays,
                      "fwd_adj_recompute_fps": len(poses) / ms * 1e3,
                      "Mrays_s": len(poses) * base.n_rays / ms / 1e3, "scene_build_ms": build_ms,
-                     "scene_generation_s": gen_s, "phase_ms": b.timings()}
+                     "scene_generation_s": gen_s, "phase_ms": ph,
+                     "roofline": trace_roofline(son, [(sid, p) for p in poses[::32]], ph["trace"], peak,
+                                                scale=len(poses) / len(poses[::32]))}
         b.close()
         son.release(sid)
         del mesh
@@ -372,8 +398,10 @@ def measure_configs(son, steps):
     b = son.batch([(sid, spec, 3, 3)])
     b.autotune(theta, prm)
     ms = timed(lambda: b.render(theta, prm, hits=True, fan=True), steps, stream)
+    ph = b.timings()
     out["dense_rays"] = {"rays_per_frame": spec.n_rays, "bins": 350 * 220, "fwd_fps": 1e3 / ms,
-                         "Mrays_s": spec.n_rays / ms / 1e3, "phase_ms": b.timings()}
+                         "Mrays_s": spec.n_rays / ms / 1e3, "phase_ms": ph,
+                         "roofline": trace_roofline(son, [(sid, spec)], ph["trace"], peak)}
     b.close()
     son.release(sid)
     return out
@@ -715,7 +743,7 @@ def run_ours(args):
     extras["tri_tests_per_ray"] = tests / (B * base.n_rays)
     extras["fp64_tests_per_ray"] = exact / (B * base.n_rays)
 
-    configs = measure_configs(son, args.steps) if (args.configs and rank == 0) else None
+    configs = measure_configs(son, args.steps, peak) if (args.configs and rank == 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
