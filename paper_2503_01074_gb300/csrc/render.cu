@@ -631,12 +631,18 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
                     }
                 }
             }
-            // material sums of this warp: one leader per material, lanes in order
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, valid ? mat : -1);
-            if (valid) {
-                float sum = 0.0f;
-                for (uint32_t m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v_mu, __ffs(m) - 1);
-                if (lane == __ffs(peers) - 1) slab[warp * nm + mat] += sum;
+            // material sums of this warp: one butterfly reduction (a fixed order,
+            // so deterministic) per distinct material among the valid lanes,
+            // added to the slab by the material's lowest lane
+            uint32_t todo = __ballot_sync(0xFFFFFFFFu, valid);
+            while (todo) {
+                const int leader = __ffs(todo) - 1;
+                const int m = __shfl_sync(0xFFFFFFFFu, mat, leader);
+                const bool mine = valid && mat == m;
+                float x = mine ? v_mu : 0.0f;
+                for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+                if (lane == leader) slab[warp * nm + m] += x;
+                todo &= ~__ballot_sync(0xFFFFFFFFu, mine);
             }
         }
         ff da{acc_a, 0.0f}, dg{acc_g, 0.0f};
