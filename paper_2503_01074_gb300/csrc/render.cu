@@ -425,24 +425,31 @@ __global__ void __launch_bounds__(256) k_fan_group(FanGroupArgs a) {
     }
 }
 
-// Fills the coordinate table of each owner sensor (one block = kFanTile pixels).
+// Fills the coordinate table of each owner sensor (one block = kFanTile
+// pixels).  A block whose stamp already holds the owner's fan_version has
+// nothing to do: the table depends on the fan geometry only, and the host bumps
+// the version whenever an update changes it.
 __global__ void __launch_bounds__(256) k_fan_lut(FanLutArgs a) {
     __shared__ SensorDev S;
-    __shared__ int64_t s_base;
+    __shared__ int s_blk;
     __shared__ uint4* s_lut;
     if (threadIdx.x == 0) {
         const int2 m = a.block_map[blockIdx.x];
         S = a.sensors[m.x];
-        s_base = (int64_t)m.y * kFanTile;
+        s_blk = m.y;
         s_lut = a.luts[m.x];
     }
     __syncthreads();
+    if (S.fan_stamp && S.fan_stamp[s_blk] == S.fan_version) return;   // block-uniform
+    const int64_t base = (int64_t)s_blk * kFanTile;
     const int64_t n = (int64_t)S.fan_w * S.fan_h;
 #pragma unroll 1
     for (int k = 0; k < kFanTile / 256; ++k) {
-        const int64_t pix = s_base + k * 256 + threadIdx.x;
+        const int64_t pix = base + k * 256 + threadIdx.x;
         if (pix < n) s_lut[pix] = fan_coord(S, pix);
     }
+    // the entries are read by later launches only, which see both them and the stamp
+    if (threadIdx.x == 0 && S.fan_stamp) S.fan_stamp[s_blk] = S.fan_version;
 }
 
 // ---------------------------------------------------------------------------

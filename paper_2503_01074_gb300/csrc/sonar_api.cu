@@ -563,6 +563,7 @@ struct sonar_batch {
     int2* d_lut_map = nullptr;        // per table block: (owner, block)
     int4* d_group_map = nullptr;      // per grouped fan block: (owner, pixel block, users [m0, m1))
     int32_t* d_members = nullptr;     // users of each table, by owner
+    uint32_t* d_fan_stamp = nullptr;  // per table block: the owner's fan_version it was built for
     int lut_blocks = 0, group_blocks = 0;
     int fan_blocks = 0;               // blocks of the per-sensor fan launch
     sonar_hit* d_hits = nullptr;      // hit records when the caller asks for none
@@ -598,13 +599,14 @@ void batch_free_device(sonar_batch* b) {
                     (void*)b->d_rowmax,
                     (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters,
                     (void*)b->d_fan_lut, (void*)b->d_luts, (void*)b->d_lut_map, (void*)b->d_group_map,
-                    (void*)b->d_members})
+                    (void*)b->d_members, (void*)b->d_fan_stamp})
         if (p) cudaFree(p);
     b->d_fan_lut = nullptr;
     b->d_luts = nullptr;
     b->d_lut_map = nullptr;
     b->d_group_map = nullptr;
     b->d_members = nullptr;
+    b->d_fan_stamp = nullptr;
     b->lut_blocks = b->group_blocks = b->fan_blocks = 0;
     b->d_trace_prefix = nullptr;
     b->d_trace_map = nullptr;
@@ -741,13 +743,14 @@ sonar_status batch_plan(sonar_batch* b) {
         if (b->lut_owner[k] < 0) { owners.push_back(k); b->lut_owner[k] = k; members[k] = 1; }
     }
     int64_t lut_px = 0;
-    std::vector<int64_t> lut_at(n, -1);
+    std::vector<int64_t> lut_at(n, -1), stamp_at(n, -1);
     std::vector<int2> lmap;
     for (int o : owners) {
         if (members[o] < 2) continue;
         const int64_t px = (int64_t)b->hs[o].fan_w * b->hs[o].fan_h;
         lut_at[o] = lut_px;
         lut_px += px;
+        stamp_at[o] = (int64_t)lmap.size();
         for (int64_t t = 0; t < (px + kFanTile - 1) / kFanTile; ++t) lmap.push_back(make_int2(o, (int)t));
     }
     for (int k = 0; k < n; ++k)
@@ -774,6 +777,8 @@ sonar_status batch_plan(sonar_batch* b) {
         alloc((void**)&b->d_lut_map, sizeof(int2) * lmap.size());
         alloc((void**)&b->d_group_map, sizeof(int4) * gmap.size());
         alloc((void**)&b->d_members, sizeof(int32_t) * mem.size());
+        alloc((void**)&b->d_fan_stamp, sizeof(uint32_t) * lmap.size());
+        if (e == cudaSuccess) e = cudaMemset(b->d_fan_stamp, 0, sizeof(uint32_t) * lmap.size());
         if (e == cudaSuccess) {
             std::vector<uint4*> own(n, nullptr);
             for (int k = 0; k < n; ++k) {
@@ -781,7 +786,11 @@ sonar_status batch_plan(sonar_batch* b) {
                 if (o < 0) continue;
                 b->lut_of[k] = b->d_fan_lut + lut_at[o];
                 b->hs[k].fan_lut = b->lut_of[k];
-                if (o == k) own[k] = b->lut_of[k];
+                if (o == k) {
+                    own[k] = b->lut_of[k];
+                    b->hs[k].fan_stamp = b->d_fan_stamp + stamp_at[o];   // stamps 0: every block builds once
+                    b->hs[k].fan_version = 1;
+                }
             }
             e = cudaMemcpy(b->d_luts, own.data(), sizeof(uint4*) * n, cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
@@ -1008,6 +1017,8 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
         S.inv_dr = fresh.inv_dr; S.fan_scale = fresh.fan_scale;
         S.seed_lo = fresh.seed_lo; S.seed_hi = fresh.seed_hi; S.frame_lo = fresh.frame_lo; S.frame_hi = fresh.frame_hi;
         S.scene = it.scene_id;
+        // an owner's table is rebuilt (inside the graph) once its fan geometry changes
+        if (S.fan_stamp && !same_fan_geometry(S, b->hs[k]) && ++S.fan_version == 0) S.fan_version = 1;   // 0: never built
         b->hs[k] = S;
         b->items[k] = it;
     }

@@ -59,6 +59,9 @@ struct SensorDev {
     int64_t polar_off, hits_off, fan_off, rowmax_off;
     float4* trig;        // float-float sin/cos of the beam azimuths [nb] and elevations [ne]
     uint4* fan_lut;      // per-pixel fan coordinates shared with same-geometry sensors (nullptr: compute)
+    uint32_t* fan_stamp;   // table owners: per table block, the fan_version it was last built for
+    uint32_t fan_version;  // table owners: bumped whenever an update changes the fan geometry
+    uint32_t pad_;
 };
 
 // A work unit: the azimuth columns [c0, c1) of one sensor, i.e. every ray

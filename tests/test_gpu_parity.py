@@ -291,8 +291,10 @@ def test_batch_equals_single_renders(son, tiny, tiny_sid):
     b.render(theta, prm)
     torch.cuda.synchronize()
     for k, (sid, spec, seed, frame) in enumerate(new):
-        single = son.render(sid, spec, theta, prm, seed, frame, hits=True)
+        single = son.render(sid, spec, theta, prm, seed, frame, hits=True, fan=True)
         assert torch.equal(b.view(k)["polar"], single["polar"]), k
+        if spec.fan_w:   # the fan tables were kept (same geometry): still the single render's fan
+            assert torch.equal(b.view(k)["fan"], single["fan"]), k
     assert b.info()["graphs"] == 1
     b.close()
 
