@@ -124,7 +124,42 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
                 }
             }
         }
-        for (int64_t base = r0; base < (per_beam ? r0 : r1); base += nt) {
+        // With at most one beam per column (n_beams <= n_az_bins) a beam's bins
+        // are its column's own: warp w folds beams w, w + nw, ... straight into
+        // the unit's accumulator, each in elevation order (the canonical order of
+        // that column's rays, so the same sums as the turn-taking fold below),
+        // with no barriers between warps.
+        const bool col_fold = DET && !per_beam && S.nb <= S.naz;
+        if (col_fold) {
+            const uint32_t naz = (uint32_t)S.naz;
+            for (int bb = warp; bb < nbeam; bb += nw) {
+                const sonar_hit* Hb = H + (int64_t)(i0 + bb) * S.ne;
+                for (int jb = 0; jb < S.ne; jb += 32) {
+                    const int j = jb + lane;
+                    uint32_t lkey = kNoKey;
+                    float score = 0.0f;
+                    if (j < S.ne) {
+                        const uint4 h = __ldg(reinterpret_cast<const uint4*>(Hb + j));
+                        if (h.x != kNoKey) {
+                            const uint32_t br = h.x / naz, ba = h.x - br * naz;
+                            lkey = br * (uint32_t)cw + (ba - (uint32_t)U.c0);
+                            int m = SC.mat_orig[h.y];
+                            m = m < a.n_mat ? m : a.n_mat - 1;
+                            score = __ldg(a.theta + 2 + m) * __uint_as_float(h.w) *
+                                    expf(-2.0f * alpha * __uint_as_float(h.z)) * gain;
+                        }
+                    }
+                    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, lkey);
+                    if (lkey != kNoKey) {
+                        const int leader = __ffs(peers) - 1;
+                        float v = lane == leader ? acc[lkey] : 0.0f;
+                        for (uint32_t m = peers; m; m &= m - 1) v += __shfl_sync(peers, score, __ffs(m) - 1);
+                        if (lane == leader) acc[lkey] = v;
+                    }
+                }
+            }
+        }
+        for (int64_t base = r0; base < (per_beam || col_fold ? r0 : r1); base += nt) {
             const int64_t r = base + tid;
             uint32_t lkey = kNoKey;
             float score = 0.0f;
