@@ -284,9 +284,13 @@ __device__ __forceinline__ float norm_value(float In, float m, int mode) {
 }
 
 __global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // rows from the last to the first: the binning kernel wrote the last
+    // sensors' I~ last, so the first rows read here are still in L2, and the
+    // first sensors' N, written last, are in L2 when the fan starts on them
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (g >= a.total_rows) return;
+    if (t >= a.total_rows) return;
+    const int64_t g = a.total_rows - 1 - t;
     const SensorDev& s = a.sensors ? a.sensors[a.row_map[g]] : a.one;
     const int row = (int)(g - s.rowmax_off);
     const int naz = s.naz;
