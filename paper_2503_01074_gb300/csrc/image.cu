@@ -7,6 +7,8 @@
 //              pixel; each thread takes 4 pixels as 16-byte loads and stores
 //              (three float4 of RGB, one float4 of depth) when the arrays are
 //              16-byte aligned, and single pixels otherwise and for the tail.
+//              The grid is one resident wave, and each thread's grid-stride
+//              loop is unrolled four times so that 16 loads are in flight.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,6 +41,7 @@ __global__ void __launch_bounds__(256) k_uw_image(const float* J, const float* d
         const float4* J4 = reinterpret_cast<const float4*>(J);
         const float4* d4 = reinterpret_cast<const float4*>(depth);
         float4* I4 = reinterpret_cast<float4*>(I);
+#pragma unroll 4
         for (int64_t q = t0; q < quads; q += stride) {
             const float4 a = J4[3 * q], b = J4[3 * q + 1], c = J4[3 * q + 2];
             const float4 d = d4[q];
@@ -68,10 +71,15 @@ cudaError_t launch_uw_image(const float* J, const float* depth, int64_t n, const
     if (n <= 0) return cudaSuccess;
     const bool vec = ((reinterpret_cast<uintptr_t>(J) | reinterpret_cast<uintptr_t>(depth) |
                        reinterpret_cast<uintptr_t>(I)) & 15u) == 0;
-    // enough threads to keep every SM streaming, a multiple of the SM count
+    // one resident wave: every SM streams from start to end, with no partly
+    // occupied second round of the grid-stride loop
+    static int per_sm = 0;
+    if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uw_image, 256, 0) != cudaSuccess ||
+                        per_sm < 1))
+        per_sm = 1;
     const int64_t work = vec ? (n + 3) / 4 : n;
     const int64_t want = (work + 255) / 256;
-    const int64_t cap = (int64_t)sm_count * 8;
+    const int64_t cap = (int64_t)sm_count * per_sm;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min(want, cap));
     k_uw_image<<<blocks, 256, 0, st>>>(J, depth, n, k, I, vec ? 1 : 0);
     return cudaGetLastError();
