@@ -283,14 +283,8 @@ __device__ __forceinline__ float norm_value(float In, float m, int mode) {
     return (mode != 0 && m > 0.0f) ? In / m : In;
 }
 
-__global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
-    // rows from the last to the first: the binning kernel wrote the last
-    // sensors' I~ last, so the first rows read here are still in L2, and the
-    // first sensors' N, written last, are in L2 when the fan starts on them
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (t >= a.total_rows) return;
-    const int64_t g = a.total_rows - 1 - t;
+// One row: its maximum over azimuth and N = I~ / max (any alignment and width).
+__device__ __forceinline__ void norm_row(const NormArgs& a, int64_t g, int lane) {
     const SensorDev& s = a.sensors ? a.sensors[a.row_map[g]] : a.one;
     const int row = (int)(g - s.rowmax_off);
     const int naz = s.naz;
@@ -334,6 +328,73 @@ __global__ void __launch_bounds__(256) k_norm_rows(NormArgs a) {
         m = ord_dec(a.gmax[s.rowmax_off]);
     }
     for (int j = lane; j < naz; j += 32) out[j] = norm_value(In[j], m, a.normalise);
+}
+
+// One warp per pair of adjacent range rows, the pairs from the last to the
+// first: the binning kernel wrote the last sensors' I~ last, so the first rows
+// read here are still in L2, and the first sensors' N, written last, are in L2
+// when the fan starts on them.  A row of 16-byte-aligned bins, at most 512 of
+// them, stays in registers between its maximum and the division, and both rows'
+// loads are issued before either reduction (4 KB in flight per warp); other
+// rows go one at a time (in registers up to 1024 aligned bins, else in two
+// passes).
+__global__ void __launch_bounds__(256, 4) k_norm_rows(NormArgs a) {
+    constexpr int kV = 4;   // float4 per lane: rows of up to 512 bins
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t pairs = (a.total_rows + 1) >> 1;
+    if (t >= pairs) return;
+    const int64_t g0 = 2 * (pairs - 1 - t);
+    float4 v[2][kV];
+    float4* out4[2] = {nullptr, nullptr};
+    int n4[2] = {0, 0};
+    bool fast[2] = {false, false};
+    int64_t rowmax_off[2] = {0, 0};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int64_t g = g0 + r;
+        if (g >= a.total_rows) continue;
+        const SensorDev& s = a.sensors ? a.sensors[a.row_map[g]] : a.one;
+        const int naz = s.naz;
+        if (((s.polar_off | naz) & 3) != 0 || naz > 32 * 4 * kV) continue;
+        const int64_t off = s.polar_off + (int64_t)(g - s.rowmax_off) * naz;
+        const float4* In4 = reinterpret_cast<const float4*>(a.noised + off);
+        out4[r] = reinterpret_cast<float4*>(a.polar + off);
+        n4[r] = naz >> 2;
+        fast[r] = true;
+        rowmax_off[r] = s.rowmax_off;
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            const int q = lane + 32 * k;
+            v[r][k] = q < n4[r] ? __ldg(In4 + q)
+                                : make_float4(-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int64_t g = g0 + r;
+        if (g >= a.total_rows) continue;
+        if (!fast[r]) {
+            norm_row(a, g, lane);
+            continue;
+        }
+        float m = 0.0f;
+        if (a.normalise == 1) {
+            m = -CUDART_INF_F;
+#pragma unroll
+            for (int k = 0; k < kV; ++k) m = fmaxf(fmaxf(m, fmaxf(v[r][k].x, v[r][k].y)), fmaxf(v[r][k].z, v[r][k].w));
+            for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        } else if (a.normalise == 2) {
+            m = ord_dec(a.gmax[rowmax_off[r]]);
+        }
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            const int q = lane + 32 * k;
+            if (q < n4[r])
+                out4[r][q] = make_float4(norm_value(v[r][k].x, m, a.normalise), norm_value(v[r][k].y, m, a.normalise),
+                                         norm_value(v[r][k].z, m, a.normalise), norm_value(v[r][k].w, m, a.normalise));
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -755,7 +816,7 @@ int bin_blocks_per_sm(int det, int block, size_t smem) {
 }
 
 cudaError_t launch_norm(const NormArgs& a, cudaStream_t st) {
-    const int64_t threads = a.total_rows * 32;
+    const int64_t threads = ((a.total_rows + 1) / 2) * 32;   // a warp per pair of rows
     k_norm_rows<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
