@@ -520,6 +520,7 @@ def run_ours(args):
         phase.append(batch.timings())       # in-graph events of this step's replays
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    kern = batch.kernels()                 # our kernels per replayed step (graph kernel nodes)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(float(sum(step_ms)), dev)
     if world > 1:
@@ -761,7 +762,7 @@ def run_ours(args):
                 "phase_ms": {k: float(np.mean([p[k] for p in phase])) for k in phase[0]},
                 "batch": info, "tune": son.tune_get().tolist(),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 7 * args.steps}
+                "gpu_launches": (kern["forward"] + kern["adjoint"]) * args.steps}
         line.update({k: float(v) for k, v in extras.items()})
         if uw is not None:
             line["uw_image"] = uw

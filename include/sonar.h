@@ -287,6 +287,11 @@ sonar_status sonar_render_batch_backward(sonar_batch_t batch, const sonar_params
  * grid size, out[3] block size, out[4] graphs captured so far. */
 sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
 
+/* Kernel launches per replay: out[0] kernel nodes of the current forward
+ * graph, out[1] of the current adjoint graph (0 for a graph not captured yet;
+ * -1 if the graph could not be inspected).  Host only, no synchronisation. */
+sonar_status sonar_batch_kernels(sonar_batch_t batch, int32_t out[2]);
+
 /* Device durations, in milliseconds, of the phases of the most recent
  * sonar_render_batch and sonar_render_batch_backward replays, measured by CUDA
  * events captured inside their graphs: ms[0] the ray-cast launch, ms[1] the

@@ -588,6 +588,7 @@ struct sonar_batch {
     bool ran_fwd = false, ran_bwd = false;
     std::vector<unsigned char> fwd_key, bwd_key;
     int graphs = 0;
+    int fwd_kernels = 0, bwd_kernels = 0;   // kernel nodes of the current graphs
 };
 
 namespace {
@@ -869,6 +870,21 @@ int persistent_grid(const sonar_batch* b, int det) {
     return (int)std::max<int64_t>(1, g);
 }
 
+// Kernel nodes of a captured graph (-1 if the graph cannot be inspected).
+int kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n > 0 && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int k = 0;
+    for (cudaGraphNode_t v : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(v, &t) != cudaSuccess) return -1;
+        k += t == cudaGraphNodeTypeKernel;
+    }
+    return k;
+}
+
 template <class T>
 void append_bytes(std::vector<unsigned char>& v, const T& x) {
     const unsigned char* p = (const unsigned char*)&x;
@@ -1062,6 +1078,7 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
         const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
         CU(e, "graph capture");
+        b->fwd_kernels = kernel_nodes(g);
         const cudaError_t e2 = cudaGraphInstantiate(&b->fwd, g, 0);
         cudaGraphDestroy(g);
         CU(e2, "graph instantiation");
@@ -1165,6 +1182,7 @@ extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar
         const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
         CU(e, "graph capture");
+        b->bwd_kernels = kernel_nodes(g);
         const cudaError_t e2 = cudaGraphInstantiate(&b->bwd, g, 0);
         cudaGraphDestroy(g);
         CU(e2, "graph instantiation");
@@ -1185,6 +1203,13 @@ extern "C" sonar_status sonar_batch_info(sonar_batch_t b, int64_t out[5]) {
     out[2] = persistent_grid(b, 1);
     out[3] = b->block;
     out[4] = b->graphs;
+    return SONAR_OK;
+}
+
+extern "C" sonar_status sonar_batch_kernels(sonar_batch_t b, int32_t out[2]) {
+    if (!b || !out) return SONAR_ERR_ARG;
+    out[0] = b->fwd ? b->fwd_kernels : 0;
+    out[1] = b->bwd ? b->bwd_kernels : 0;
     return SONAR_OK;
 }
 

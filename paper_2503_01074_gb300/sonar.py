@@ -102,6 +102,7 @@ _SIG = {
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p]),
     "sonar_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "sonar_batch_kernels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "sonar_batch_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "sonar_batch_destroy": (C.c_int, [C.c_void_p]),
     "sonar_autotune": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_int32,
@@ -467,6 +468,12 @@ class Batch:
         prm = params.c()
         self.sonar._check(self.lib.sonar_autotune(self.h, C.byref(prm), _ptr(theta), theta.shape[0] - 2,
                                                   C.byref(out), _stream(stream)))
+
+    def kernels(self):
+        """Kernel launches per replay of the current forward and adjoint graphs."""
+        out = (C.c_int32 * 2)()
+        self.sonar._check(self.lib.sonar_batch_kernels(self.h, out))
+        return {"forward": out[0], "adjoint": out[1]}
 
     def info(self):
         out = (C.c_int64 * 5)()

@@ -352,7 +352,11 @@ def test_batch_backward_equals_sum_of_singles(son, tiny, tiny_sid):
     b.render(theta, prm)
     G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(2)).to(son.device)
     d_b = b.backward(theta, prm, G, hits=True)
+    # kernels per replay: the row terms, the gather and the final sum (stored hits)
+    k = b.kernels()
+    assert 4 <= k["forward"] <= 7 and k["adjoint"] == 3, k
     d_r = b.backward(theta, prm, G, hits=False)
+    assert b.kernels()["adjoint"] == 5       # + the sin/cos tables and the ray cast (recomputed hits)
     torch.cuda.synchronize()
     assert torch.equal(d_b, d_r)
     total = torch.zeros_like(theta, dtype=torch.float64)
