@@ -73,9 +73,8 @@ cudaError_t launch_uw_image(const float* J, const float* depth, int64_t n, const
                        reinterpret_cast<uintptr_t>(I)) & 15u) == 0;
     // one resident wave: every SM streams from start to end, with no partly
     // occupied second round of the grid-stride loop
-    static int per_sm = 0;
-    if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uw_image, 256, 0) != cudaSuccess ||
-                        per_sm < 1))
+    int per_sm = 0;   // a host-side calculation, no device work
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uw_image, 256, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int64_t work = vec ? (n + 3) / 4 : n;
     const int64_t want = (work + 255) / 256;
