@@ -305,12 +305,16 @@ sonar_status sonar_batch_destroy(sonar_batch_t batch);
 
 /* ---- autotuner ---- */
 
-/* Times candidate tile shapes (beams x elevations per ray-cast warp, columns
- * per binning work unit, binning block size) on the batch's own sensors and records the fastest per sensor
- * shape (n_beams, n_elev, n_range_bins, n_az_bins) in the context's tuning
- * cache; later sonar_batch_create and sonar_render calls use it.  Runs
- * renders on `stream` and synchronises it.  Outputs of `out` are
- * overwritten. */
+/* Times candidate tile shapes on the batch's own sensors and records the
+ * fastest per sensor shape (n_beams, n_elev, n_range_bins, n_az_bins) in the
+ * context's tuning cache; later sonar_batch_create and sonar_render calls use
+ * it.  Stage 1 times the forward launches over the ray-cast warp tiles (beams
+ * x elevations per warp) and register variants; stage 2 times the columns per
+ * binning work unit and the block size, which also shape the adjoint, on the
+ * forward launches plus, when `out` holds hit records and I~, the adjoint of
+ * a constant upstream gradient.  Each candidate scores the best of 3 rounds
+ * of 3 passes.  Runs on `stream` and synchronises it; allocates and frees its
+ * own scratch (a polar-sized gradient).  Outputs of `out` are overwritten. */
 sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
                             const float* d_theta, int32_t n_mat,
                             const sonar_batch_outputs* out, void* stream);
