@@ -275,7 +275,7 @@ struct FanArgs {
 
 // Fan of the users of a shared coordinate table: per block (owner, block of
 // its pixels, users members[m0 .. m1)); one thread serves up to kFanGroup frames.
-constexpr int kFanGroup = 8;
+constexpr int kFanGroup = 2;     // frames per grouped fan block (more frames per thread evict lines that neighbouring pixels reuse)
 struct FanGroupArgs {
     const SensorDev* sensors;
     const int4* block_map;
