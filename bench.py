@@ -120,7 +120,7 @@ def workload(rank: int, world: int, frames: int, small: bool):
 class Clocks:
     """SM clock and throttle reasons sampled while the timed region runs.
 
-    A poller thread reads the driver's NVML library (through ctypes, read-only
+    A poller thread reads the NVIDIA driver's NVML library (through ctypes, read-only
     queries) every millisecond, since the timed region can be shorter than
     nvidia-smi's sampling period; where NVML does not load, nvidia-smi samples
     every 200 ms instead."""
