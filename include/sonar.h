@@ -401,6 +401,16 @@ sonar_status sonar_dvl_schedule(sonar_ctx_t ctx, const float* d_period, int64_t 
 sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor* sensor,
                                const sonar_params* params, void* stream, int64_t out[6]);
 
+/* The noise stream (Sec. III-A-2, Eq. 3-6 draws): Philox4x32-10 (Salmon et al.,
+ * SC'11) of n counters under the key (seed lo 32 bits, seed hi 32 bits), by the
+ * round function the render, adjoint and DVL kernels use.  A bin's draws come
+ * from counter (bin index, frame lo, 0, frame hi): word 0 the Rayleigh draw,
+ * words 1 and 2 the Gaussian one.  d_counters [n][4] and d_out [n][4] uint32,
+ * device, 16-byte aligned; d_out may equal d_counters.  Errors: SONAR_ERR_ARG
+ * (n < 0, NULL or unaligned buffers with n > 0), before anything is enqueued. */
+sonar_status sonar_philox(sonar_ctx_t ctx, const uint32_t* d_counters, int64_t n, uint64_t seed, uint32_t* d_out,
+                          void* stream);
+
 /* L2 read bandwidth: reads the caller's buffer `passes` times over with
  * 16-byte loads that are cached in L2 but not in L1, on n_blocks blocks of
  * 512 threads, and writes each block's sum of the values it read (FP32) to

@@ -279,6 +279,17 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
 // phase 2a: range-wise normalisation, one warp per (sensor, range row)
 // ---------------------------------------------------------------------------
 
+// The noise stream itself: Philox4x32-10 of n counters under one key, the
+// same round function the binning, adjoint and DVL kernels draw from.
+__global__ void __launch_bounds__(256) k_philox_words(const uint4* ctr, int64_t n, uint32_t k0, uint32_t k1,
+                                                      uint4* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = ctr[i];
+    const U4 x = philox10(U4{c.x, c.y, c.z, c.w}, philox_key(k0, k1));
+    out[i] = make_uint4(x.x, x.y, x.z, x.w);
+}
+
 __device__ __forceinline__ float norm_value(float In, float m, int mode) {
     return (mode != 0 && m > 0.0f) ? In / m : In;
 }
@@ -813,6 +824,13 @@ int bin_blocks_per_sm(int det, int block, size_t smem) {
     const void* f = det ? (const void*)k_bin<1> : (const void*)k_bin<0>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
+}
+
+cudaError_t launch_philox(const void* ctr, int64_t n, uint32_t k0, uint32_t k1, void* out, cudaStream_t st) {
+    if (n > 0)
+        k_philox_words<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(static_cast<const uint4*>(ctr), n, k0, k1,
+                                                                      static_cast<uint4*>(out));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_norm(const NormArgs& a, cudaStream_t st) {

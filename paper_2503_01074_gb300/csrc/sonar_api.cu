@@ -1543,6 +1543,19 @@ extern "C" sonar_status sonar_trace_stats(sonar_ctx_t ctx, int32_t scene_id, con
     return SONAR_OK;
 }
 
+extern "C" sonar_status sonar_philox(sonar_ctx_t ctx, const uint32_t* d_counters, int64_t n, uint64_t seed,
+                                     uint32_t* d_out, void* stream) {
+    if (!ctx) return SONAR_ERR_ARG;
+    if (n < 0) return fail(ctx, SONAR_ERR_ARG, "n < 0");
+    if (n == 0) return SONAR_OK;
+    if (!d_counters || !d_out) return fail(ctx, SONAR_ERR_ARG, "NULL buffer");
+    if (!aligned16(d_counters) || !aligned16(d_out)) return fail(ctx, SONAR_ERR_ARG, "buffers must be 16-byte aligned");
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CU(launch_philox(d_counters, n, (uint32_t)seed, (uint32_t)(seed >> 32), d_out, (cudaStream_t)stream),
+       "philox launch");
+    return SONAR_OK;
+}
+
 extern "C" sonar_status sonar_probe_l2_read(sonar_ctx_t ctx, const void* d_buf, int64_t bytes, int32_t passes,
                                             float* d_block_sums, int32_t n_blocks, void* stream) {
     if (!ctx) return SONAR_ERR_ARG;

@@ -40,6 +40,7 @@ cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStre
 cudaError_t launch_bin(const BinArgs& a, int det, int grid, int block, size_t smem, cudaStream_t st);
 int bin_blocks_per_sm(int det, int block, size_t smem);
 constexpr size_t kMaxDynSmem = 200 * 1024;
+cudaError_t launch_philox(const void* ctr, int64_t n, uint32_t k0, uint32_t k1, void* out, cudaStream_t st);
 cudaError_t launch_norm(const NormArgs& a, cudaStream_t st);
 cudaError_t launch_fan_tiles(const FanArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_fan_lut(const FanLutArgs& a, int blocks, cudaStream_t st);

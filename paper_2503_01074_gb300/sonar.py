@@ -120,6 +120,7 @@ _SIG = {
                                     C.c_void_p, C.POINTER(C.c_int64)]),
     "sonar_probe_l2_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32,
                                       C.c_void_p]),
+    "sonar_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p]),
 }
 
 _LIB = None
@@ -354,6 +355,17 @@ class Sonar:
         self._check(self.lib.sonar_dvl_schedule(self.h, _ptr(period), n_veh, n_steps, C.c_float(dt), _ptr(emit),
                                                 _stream(stream)))
         return emit
+
+    def philox(self, counters, seed, stream=None):
+        """Philox4x32-10 words of counters [n, 4] (an int32 CUDA tensor holding
+        the uint32 bits) under key = seed; returns [n, 4] int32 (the bits)."""
+        counters = counters.contiguous()
+        if counters.dtype != self.torch.int32 or counters.dim() != 2 or counters.shape[1] != 4:
+            raise ValueError("counters must be an int32 tensor [n, 4]")
+        out = self.torch.empty_like(counters)
+        self._check(self.lib.sonar_philox(self.h, _ptr(counters), counters.shape[0], C.c_uint64(seed), _ptr(out),
+                                          _stream(stream)))
+        return out
 
     def probe_l2_read(self, buf, passes, n_blocks, stream=None):
         """Reads the CUDA tensor `buf` (16-byte aligned, size a multiple of 16

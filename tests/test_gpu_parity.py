@@ -231,6 +231,31 @@ def test_trace_stats(son, tiny, tiny_sid):
     assert st["visits"] >= st["nodes_touched"] and st["tests"] >= st["tris_touched"]
 
 
+def test_philox_stream_bitwise(son):
+    """The kernels' Philox4x32-10 against the oracle's (itself pinned to a
+    library implementation), word for word: random counters, the extremes and
+    the counters of a frame's bins (bin, frame lo, 0, frame hi)."""
+    rng = np.random.default_rng(8)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    frame = (5 << 32) | 77
+    ctr[2:2050, 0] = np.arange(2048, dtype=np.uint32)
+    ctr[2:2050, 1] = frame & 0xFFFFFFFF
+    ctr[2:2050, 2] = 0
+    ctr[2:2050, 3] = frame >> 32
+    d_ctr = torch.tensor(ctr.view(np.int32), device=son.device)
+    for seed in (0, 1, 0x0123456789ABCDEF):
+        got = son.philox(d_ctr, seed).cpu().numpy().view(np.uint32)
+        want = O.philox(ctr, np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32))
+        assert np.array_equal(got, want), seed
+    unaligned = torch.zeros(20, dtype=torch.int32, device=son.device)[1:17].view(4, 4)
+    with pytest.raises(SonarError):
+        son.philox(unaligned, 0)
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+
+
 def test_l2_read_probe_reads_every_byte(son):
     # a buffer of ones with a ragged length: the block sums add up to the
     # number of floats times the passes, exactly (every partial sum is an
