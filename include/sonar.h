@@ -85,7 +85,8 @@ typedef struct {
     int32_t normalise;   /* 0 none, 1 range-row maximum (default), 2 global maximum */
     int32_t two_sided;   /* 1: incidence factor |d.n| (default); 0: max(0, -d.n) */
     int32_t clip_tmax;   /* 1: only hits with r < r_max count; 0: trace to infinity */
-    int32_t accumulate;  /* 0: deterministic sort-by-bin segmented fold (default);
+    int32_t accumulate;  /* 0: deterministic fold of each bin's returns in canonical
+                               ray order (default; bitwise reproducible);
                             1: warp-aggregated shared-memory atomics */
     int32_t reserved;
 } sonar_params;
@@ -255,16 +256,21 @@ typedef struct {
 sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_item* items,
                                 int32_t n_items, sonar_batch_t* out);
 
-/* Replaces poses, seeds and frames (and scene ids) of a planned batch.  Item
- * count, shapes and offsets must match the plan.  Enqueued on `stream` from
+/* Replaces poses, seeds and frames (and scene ids, fields of view and range
+ * windows) of a planned batch.  Item count, shapes (beams, elevations, bins,
+ * fan size) and offsets must match the plan.  A shared fan coordinate table
+ * is rebuilt by the next render once its owner's fan geometry has changed;
+ * items whose geometry no longer matches their table's compute their own.  Enqueued on `stream` from
  * host staging memory owned by the batch; `items` may be reused at once. */
 sonar_status sonar_batch_update(sonar_batch_t batch, const sonar_batch_item* items,
                                 int32_t n_items, void* stream);
 
-/* Renders every item of the batch: one launch casts every ray of every
- * sensor, one persistent launch bins and adds noise for all column work units
- * (dynamic work list), one normalises every range row and one resamples every
- * fan.  The first call for a given (params, theta, outputs)
+/* Renders every item of the batch: one launch builds the exact-ray sin/cos
+ * tables, one casts every ray of every sensor, one persistent launch bins and
+ * adds noise for all column work units (dynamic work list), one normalises
+ * every range row, and the fans are resampled by one launch for the items
+ * that share a fan geometry (after refreshing any coordinate table whose
+ * geometry changed) and one for the others.  The first call for a given (params, theta, outputs)
  * captures the launches in a CUDA graph; later calls with the same arguments
  * replay it.  Results per item equal sonar_render's for the same item and
  * tile shape (bitwise, in deterministic accumulation). */
@@ -322,7 +328,7 @@ sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
 /* Tuning cache entries: writes up to `cap` rows of 8 int32
  * (n_beams, n_elev, n_range_bins, n_az_bins, cols, tb, block, occ), tb =
  * beams per ray-cast warp (a power of two <= 32; elevations = 32 / tb), occ =
- * 8 to cap the ray-cast registers for 8 blocks of 128 per SM, else 0
+ * 8 to cap the ray-cast registers at 64 (32 one-warp blocks per SM), else 0
  * and returns the number of entries in *count. */
 sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count);
 
