@@ -24,7 +24,7 @@ struct Tune {
     int cols = 0;     // binning: azimuth columns per work unit (0: derive)
     int tb = 0;       // tracing: beams per warp tile, elevations = 32 / tb (0: derive)
     int block = 128;  // binning: threads per block
-    int occ = 0;      // tracing: 8 = cap registers for 8 blocks per SM, 0 = no cap
+    int occ = 0;      // tracing: 8 = cap registers at 64 for 32 one-warp blocks per SM, 0 = no cap
 };
 
 using ShapeKey = std::array<int, 4>;   // n_beams, n_elev, n_range_bins, n_az_bins
