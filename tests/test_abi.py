@@ -77,3 +77,39 @@ def test_product_path_has_no_cpu_fallback(tmp_path, monkeypatch):
             if f.endswith(".py"):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", txt, flags=re.M), f
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/sonar.h compiles as C99 (no C++ in the boundary) and a C program
+    links against libsonar.so and calls it (only calls that need no GPU: the
+    version string and argument errors)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "sonar.h"
+int main(void) {
+    const char* v = sonar_version();
+    if (!v || strncmp(v, "libsonar", 8) != 0) return 1;
+    if (sonar_create(0, NULL) != SONAR_ERR_ARG) return 2;          /* NULL out */
+    if (sonar_check(NULL, NULL) != SONAR_ERR_ARG) return 3;        /* NULL context */
+    if (sonar_philox(NULL, NULL, 0, 0, NULL, NULL) != SONAR_ERR_ARG) return 4;
+    if (sizeof(sonar_hit) != 16) return 5;
+    puts(v);
+    return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    libdir = os.path.join(ROOT, "paper_2503_01074_gb300")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe), "-L", libdir, "-lsonar", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.startswith("libsonar")
