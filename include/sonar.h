@@ -52,7 +52,7 @@ typedef enum {
     SONAR_ERR_ARG = 1,      /* invalid argument; nothing was enqueued */
     SONAR_ERR_CUDA = 2,     /* a CUDA runtime call failed */
     SONAR_ERR_OOM = 3,      /* device allocation failed */
-    SONAR_ERR_TIMEOUT = 4,  /* a bounded device wait gave up */
+    SONAR_ERR_TIMEOUT = 4,  /* reserved: no call returns it (no kernel waits on another) */
     SONAR_ERR_DEVICE = 5,   /* the sticky device error word was set */
     SONAR_ERR_STATE = 6     /* call not valid in the object's current state */
 } sonar_status;
@@ -60,7 +60,7 @@ typedef enum {
 /* Sticky device error bits (sonar_check reports their OR in *bits). */
 #define SONAR_DEVERR_STACK 0x1u    /* BVH traversal stack overflow */
 #define SONAR_DEVERR_INDEX 0x2u    /* an index read from memory was out of range */
-#define SONAR_DEVERR_TIMEOUT 0x4u  /* a bounded spin-wait ran out */
+#define SONAR_DEVERR_TIMEOUT 0x4u  /* reserved: never set (no kernel spin-waits) */
 
 /* Sonar geometry and pose.  rot is the sensor->world rotation, row-major:
  * d_world[a] = sum_b rot[3a + b] d_sensor[b].  hfov, vfov in radians, in
@@ -188,8 +188,10 @@ sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const sonar_sensor*
  *     SONAR_ERR_ARG before anything is enqueued (pass out->hits and
  *     out->noised to need only the small fixed parts).
  *   - The first call on a device looks up the array's device address (which
- *     may load the library's device code) and caches it; make that first call
- *     before any stream capture on that device.
+ *     may load the library's device code) and caches it for that device's
+ *     current context; make that first call before any stream capture on
+ *     that device.  After cudaDeviceReset the next call is a first call again
+ *     (the new context loads the device code anew and the array may move).
  *   - All calls on a device share the one array, and it keeps the last
  *     call's contents (each call clears what it needs cleared): calls whose
  *     work can overlap on the GPU (different streams, or different contexts

@@ -1582,19 +1582,55 @@ namespace {
 static __device__ __align__(256) float g_noalloc_scratch[SONAR_NOALLOC_SCRATCH_WORDS];
 
 std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[256] = {};
+std::map<unsigned long long, void*> g_noalloc_addr;   // by context id (unique for the process)
 
-// Device address of the scratch array on `device` (current), looked up once.
-cudaError_t noalloc_scratch(int device, void** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
-    if (!g_noalloc_addr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[device] = p;
+// The unique id of the calling thread's current context (cuCtxGetCurrent and
+// cuCtxGetId, through the runtime's driver entry points); false when the
+// driver does not offer them.
+bool current_context_id(unsigned long long* id) {
+    typedef int (*get_current_t)(void**);
+    typedef int (*get_id_t)(void*, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        void* g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (get_current_t)f;
+            get_id = (get_id_t)g;
+        }
+        looked_up = true;
     }
-    *out = g_noalloc_addr[device];
+    void* ctx = nullptr;
+    return get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current context (the caller has
+// made the context's device current).  Looked up once per context: a context
+// that is destroyed and created again (cudaDeviceReset) reloads the library's
+// device code, the array may move, and the new context has a new id.  Where
+// the driver cannot name the context, the address is looked up on every call
+// (a host-side lookup once the device code is loaded).
+cudaError_t noalloc_scratch(void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    unsigned long long id = 0;
+    const bool keyed = current_context_id(&id);
+    if (keyed) {
+        auto it = g_noalloc_addr.find(id);
+        if (it != g_noalloc_addr.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (keyed) g_noalloc_addr[id] = p;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -1631,7 +1667,7 @@ extern "C" sonar_status sonar_render_noalloc(sonar_ctx_t ctx, int32_t scene_id, 
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device), "cudaSetDevice");
     void* base = nullptr;
-    CU(noalloc_scratch(ctx->device, &base), "cudaGetSymbolAddress of the fixed scratch");
+    CU(noalloc_scratch(&base), "cudaGetSymbolAddress of the fixed scratch");
     uint32_t* rowmax = (uint32_t*)base;
     sonar_hit* hits = out->hits ? out->hits : (sonar_hit*)((float*)base + hits_at);
     float* noised = out->noised ? out->noised : (float*)base + noised_at;

@@ -178,6 +178,16 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _keep(tmp, orig, stream):
+    """A contiguous copy `tmp` of `orig` that a call reads on `stream`: when it
+    is a new tensor and the stream is not torch's current one, the caching
+    allocator is told that the stream uses it, so that its memory is not
+    handed to other work before the queued kernels have read it."""
+    if stream is not None and tmp.data_ptr() != orig.data_ptr():
+        tmp.record_stream(stream)
+    return tmp
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -290,7 +300,8 @@ class Sonar:
         t = self.torch
         F = t.empty((fan_h, fan_w), dtype=t.float32, device=self.device)
         sensor = to_sensor(spec)
-        self._check(self.lib.sonar_fan_resample(self.h, C.byref(sensor), _ptr(polar.contiguous()), fan_w,
+        src = _keep(polar.contiguous(), polar, stream)
+        self._check(self.lib.sonar_fan_resample(self.h, C.byref(sensor), _ptr(src), fan_w,
                                                 fan_h, _ptr(F), _stream(stream)))
         return F
 
@@ -300,9 +311,10 @@ class Sonar:
         d = t.empty_like(theta)
         sensor = to_sensor(spec)
         prm = params.c()
+        g = _keep(grad_polar.contiguous(), grad_polar, stream)
         self._check(self.lib.sonar_render_backward(
             self.h, sid, C.byref(sensor), C.byref(prm), _ptr(theta), theta.shape[0] - 2, seed, frame,
-            _ptr(grad_polar.contiguous()), _ptr(noised), _ptr(hits), _ptr(d), _stream(stream)))
+            _ptr(g), _ptr(noised), _ptr(hits), _ptr(d), _stream(stream)))
         return d
 
     def trace_stats(self, sid, spec, params: RenderParams = RenderParams(), stream=None):

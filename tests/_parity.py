@@ -61,8 +61,6 @@ def excluded_bins(spec, ref, h):
                     mask[kk - naz] = True
                 if kk + naz < nr * naz:
                     mask[kk + naz] = True
-        if f["binedge"][k] and ref["key"][k] < 0 and key[k] < 0:
-            continue
     return mask.reshape(nr, naz)
 
 

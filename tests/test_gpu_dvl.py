@@ -42,7 +42,9 @@ def ambiguous_beams(recs, t, P):
     for p, h in enumerate(recs):
         hit = h["tri"] >= 0
         bary = np.minimum(np.minimum(h["u"], h["v"]), 1.0 - h["u"] - h["v"])
-        amb[p] = hit & ((bary < 1e-6) | (h["t2"] - h["t"] < 1e-6 * h["t"]) | (np.abs(h["dn"]) < 1e-6))
+        with np.errstate(invalid="ignore"):      # a miss has t = t2 = inf
+            tie = h["t2"] - h["t"] < 1e-6 * h["t"]
+        amb[p] = hit & ((bary < 1e-6) | tie | (np.abs(h["dn"]) < 1e-6))
     amb |= (np.abs(t - P.r_min) < 1e-4) | (np.abs(t - P.r_max) < 1e-4)
     return amb
 

@@ -162,6 +162,51 @@ def test_flat_seabed_closed_form(n_az):
     assert np.isclose(r["P"].sum(), r["score"][r["key"] >= 0].sum(), rtol=1e-12)
 
 
+def test_accumulate_per_bin_closed_form():
+    """oracle_accumulate bin by bin: on a flat seabed every ray's range, score,
+    range bin and azimuth bin have closed forms, so the polar image P is the
+    closed-form scores summed at the closed-form keys (np.add.at).  Several
+    beams share a column (N_b = 3 N_az + 1) and several elevations share range
+    bins, so a transposed index, a dropped or doubled score or a misplaced
+    column fails here even though the image total would still agree."""
+    h = 4.0
+    mesh = S.quad(-h, 500.0, 0)
+    s = S.SensorSpec(np.zeros(3, np.float32), S.pose_matrix(0.3, math.radians(25.0)), 97, 24, 60, 32,
+                     math.radians(120.0), math.radians(18.0), 0.5, 25.0)
+    mu, alpha, gain = float(np.float32(0.45)), 0.03, 2.0     # the reflectivity table is FP32
+    r = O.render(mesh, np.array([mu], np.float32), alpha, gain, s, O.Params(), fan=False)
+    H, V = float(np.float32(s.hfov)), float(np.float32(s.vfov))
+    i = np.arange(s.n_beams).repeat(s.n_elev)
+    j = np.tile(np.arange(s.n_elev), s.n_beams)
+    phi = -H / 2 + (i + 0.5) * H / s.n_beams
+    th = -V / 2 + (j + 0.5) * V / s.n_elev
+    R = s.rot.astype(np.float64)
+    ds = np.stack([np.sin(phi) * np.cos(th), np.cos(phi) * np.cos(th), np.sin(th)], axis=1)
+    dw = ds @ R.T
+    sin_dep = -dw[:, 2] / np.linalg.norm(dw, axis=1)
+    rr = h / sin_dep
+    score = mu * (h / rr) * np.exp(-2 * alpha * rr) * gain
+    rmin, rmax = 0.5, float(np.float32(25.0))
+    dr = (rmax - rmin) / s.n_range_bins
+    br = np.floor((rr - rmin) / dr).astype(np.int64)
+    ba = ((2 * i + 1) * s.n_az_bins) // (2 * s.n_beams)
+    inside = (rr >= rmin) & (rr < rmax)
+    key = br * s.n_az_bins + ba
+    expect = np.zeros(s.n_range_bins * s.n_az_bins)
+    np.add.at(expect, key[inside], score[inside])
+    # bins a return within 1e-4 m of a range-bin edge may reach are not compared
+    near = np.abs(rr - (rmin + np.round((rr - rmin) / dr) * dr)) < 1e-4
+    skip = np.zeros_like(expect, bool)
+    for k in np.flatnonzero(near & (rr > rmin - 1e-3) & (rr < rmax + 1e-3)):
+        for kk in (key[k] - s.n_az_bins, key[k], key[k] + s.n_az_bins):
+            if 0 <= kk < skip.size:
+                skip[kk] = True
+    P = r["P"].ravel()
+    assert inside.sum() > 0.5 * s.n_rays and (expect > 0).sum() > 300     # not vacuous
+    assert np.allclose(P[~skip], expect[~skip], rtol=1e-11, atol=0)
+    assert (np.bincount(ba, minlength=s.n_az_bins) > s.n_elev).any()      # columns hold several beams
+
+
 # --------------------------------------------------------------------------
 # closest hit: icosphere vs analytic sphere bounds
 # --------------------------------------------------------------------------
