@@ -2,12 +2,17 @@
 rays, 1000 x 512 bins, 1024 x 576 fan) in the launch configuration bench.py
 times: a batch of 64 poses, autotuned, graph-replayed.
 
-The oracle cannot brute-force whole frames here, so it checks
+One whole frame is compared with the oracle's brute force over all 32,768
+rays (about half a minute of FP64 work on 16 host cores): hit triangles,
+ranges and bin keys of every ray; the binned image P, the noised image I~ and
+the range-normalised image N bin by bin; the fan; and the gradient with
+respect to (alpha, gain, mu) in the row and whole-image normalisation modes.
+Other frames are checked on
   - sampled rays, one by one (hit triangle, range, bin, incidence);
   - complete azimuth columns: every ray of the beams that fall into a column,
     so the column's binned and noised values can be compared bin by bin;
-and properties that hold at any size check the rest (the polar total equals
-the sum of the binned scores; N = I~ / row max; single render = batch frame).
+and by properties that hold at any size (the polar total equals the sum of
+the binned scores; N = I~ / row max; single render = batch frame).
 """
 import numpy as np
 import pytest
@@ -94,6 +99,69 @@ def test_sampled_rays_and_complete_columns(setup, frame):
     mat = d["mesh"].mat[tri[key >= 0]]
     s = d["mu"][mat].astype(np.float64) * cs[key >= 0] * np.exp(-2 * ALPHA * r[key >= 0]) * GAIN
     assert np.isclose(gP.sum(), s.sum(), rtol=1e-5)
+
+
+def test_whole_frame_against_oracle(setup):
+    """Frame 0 of the bench's batch against the oracle's full render."""
+    d = setup
+    spec = d["poses"][0]
+    v = d["batch"].view(0)
+    h = hits_numpy(v["hits"])
+    ref = O.render(d["mesh"], d["mu"], ALPHA, GAIN, spec, O.Params(), seed=0, frame=0, tv=d["tv"])
+    excl = hit_parity(ref, h)
+    assert (ref["key"] >= 0).mean() > 0.5 and excl.mean() < 0.05          # not vacuous
+    mask = excluded_bins(spec, ref, h)
+    gP = v["binned"].double().cpu().numpy()
+    gI = v["noised"].double().cpu().numpy()
+    gN = v["polar"].double().cpu().numpy()
+    assert_bins_close(gP, ref["P"], mask, what="binned image")
+    assert_bins_close(gI, ref["noised"], mask, what="noised image")
+    # range-wise normalisation (the default mode): rows whose maximum lies in
+    # a compared bin
+    nr, naz = spec.n_range_bins, spec.n_az_bins
+    am = ref["argmax"]
+    good_row = ~mask[np.arange(nr), am]
+    assert good_row.mean() > 0.9
+    rowmask = mask | ~good_row[:, None]
+    assert_bins_close(gN, ref["polar"], rowmask, what="normalised image")
+    # the fan: against the oracle's fan of the GPU's own N (the resampler
+    # alone), and against the oracle's own fan wherever every bin a pixel
+    # blends was compared above
+    gF = v["fan"].double().cpu().numpy()
+    fr, flag = O.fan_image(spec, gN, spec.fan_w, spec.fan_h)
+    assert np.allclose(gF[~flag], fr[~flag], rtol=1e-4, atol=1e-5)
+    probe, _ = O.fan_image(spec, np.where(rowmask, np.nan, 0.0), spec.fan_w, spec.fan_h)
+    ok = ~flag & np.isfinite(probe)
+    assert ok.mean() > 0.3 and (gF[ok] != 0).mean() > 0.5
+    bad = ok & ~np.isclose(gF, ref["fan"], rtol=1e-4, atol=1e-5)
+    assert not bad.any(), f"fan: {bad.sum()} of {ok.sum()} pixels out of tolerance"
+    # gradient in modes 1 and 2 through the batch adjoint: both sides take
+    # the oracle's I~ in FP32 and the same upstream gradient, which is zero on
+    # every bin a flagged ray may reach and on rows (mode 1) whose maximum is
+    # such a bin, so that rays the two sides may bin differently add nothing
+    b = d["batch"]
+    In32 = ref["noised"].astype(np.float32)
+    G = np.random.default_rng(11).normal(size=(nr, naz)).astype(np.float32) * 1e-3
+    G[rowmask] = 0.0
+    saved = b.noised.clone()
+    try:
+        b.noised[:nr * naz] = torch.tensor(In32.ravel(), device=d["son"].device)
+        Gd = torch.zeros(b.n_polar, device=d["son"].device)
+        Gd[:nr * naz] = torch.tensor(G.ravel(), device=d["son"].device)
+        for mode in (1, 2):
+            if mode == 2:
+                gmax = int(np.argmax(In32.ravel()))
+                assert not mask.ravel()[gmax]
+            prm = RenderParams(normalise=mode)
+            got = b.backward(d["theta"], prm, Gd, hits=True).double().cpu().numpy()
+            want = O.grad(d["mesh"], d["mu"], ALPHA, GAIN, spec, O.Params(normalise=mode), 0, 0,
+                          G.astype(np.float64), In32.astype(np.float64), ref)
+            scale = np.abs(want).max()
+            assert scale > 0
+            assert np.allclose(got, want, rtol=1e-3, atol=1e-4 * scale), (mode, got, want)
+    finally:
+        b.noised.copy_(saved)
+        torch.cuda.synchronize()
 
 
 def test_single_render_equals_batch_frame(setup):
