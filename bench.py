@@ -52,15 +52,17 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--frames", type=int, default=64, help="frames (sensor poses) per step and rank")
-    p.add_argument("--cpu-rays", type=int, default=8192, help="rays in the oracle's CPU-baseline sample")
+    p.add_argument("--ref-rays", type=int, default=4096, help="rays the reference arm (the oracle) casts per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the single-frame and e2e legs")
     p.add_argument("--small", action="store_true", help="a small case for profiler captures")
     p.add_argument("--tune", default=None, metavar="COLS,TB,BLOCK,OCC",
                    help="fixed launch configuration instead of autotuning (profiler captures, whose "
                         "replays distort the autotuner's timings)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other configurations (differentiable fit, heterogeneous batch, large, dense rays)")
     p.add_argument("--configs", action="store_true",
-                   help="also measure the heterogeneous-batch, large and dense-ray configurations")
+                   help="also measure the large scene with 1024 materials")
     return p.parse_args()
 
 
@@ -228,57 +230,78 @@ class Clocks:
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
 
-def oracle_frame_time(mesh, mu, spec, n_rays, seed=0, tv=None):
-    """Seconds per full frame, extrapolated from casting `n_rays` sampled rays
-    plus the full per-bin pipeline (binning, noise, normalisation, fan)."""
+def oracle_pass(mesh, mu, spec, n_rays, seed=0, tv=None):
+    """One pass of the oracle over `n_rays` sampled rays of the frame (all of
+    them when n_rays = the frame's rays): brute-force FP64 ray casting, then
+    the whole per-bin pipeline on the full image (binning, noise,
+    normalisation, fan).  Returns (seconds casting, seconds per-bin, threads,
+    the per-ray results)."""
     import oracle as O
     tv = O.tri_verts(mesh) if tv is None else tv
-    ids = np.sort(np.random.default_rng(seed).choice(spec.n_rays, n_rays, replace=False))
+    ids = None if n_rays >= spec.n_rays else \
+        np.sort(np.random.default_rng(seed).choice(spec.n_rays, n_rays, replace=False))
     t0 = time.perf_counter()
-    r = O.render(mesh, mu, ALPHA, GAIN, spec, O.Params(), ray_ids=ids, tv=tv)
+    r = O.render(mesh, mu, ALPHA, GAIN, spec, O.Params(),
+                 ray_ids=ids if ids is not None else np.arange(spec.n_rays), tv=tv)
     t1 = time.perf_counter()
-    # per-bin stages on a full-size image built from the sampled returns
     P = np.zeros(spec.n_range_bins * spec.n_az_bins)
-    O.lib().oracle_accumulate(len(ids), r["key"], r["score"], P.size, P)
+    O.lib().oracle_accumulate(len(r["key"]), r["key"], r["score"], P.size, P)
     In = O.noise(spec, P.reshape(spec.n_range_bins, spec.n_az_bins), 0, 0, O.Params())
     N, _, _ = O.normalise(spec, In, 1)
     O.fan_image(spec, N, spec.fan_w, spec.fan_h)
     t2 = time.perf_counter()
-    per_frame = (t1 - t0) * spec.n_rays / n_rays + (t2 - t1)
-    return per_frame, r["hits"]["threads"], (t1 - t0), (t2 - t1)
+    return t1 - t0, t2 - t1, int(r["hits"]["threads"]), r
 
 
-def cpu_baseline(mesh, mu, spec, n_rays):
-    per_frame, threads, t_rays, t_bins = oracle_frame_time(mesh, mu, spec, n_rays)
-    return {"value": 1.0 / per_frame, "unit": UNIT, "cores": int(threads), "kind": "oracle",
-            "sample": (f"{n_rays} of {spec.n_rays} rays of one frame cast by brute force in FP64 "
-                       f"({t_rays:.1f} s, scaled to the full frame) + the full per-bin pipeline "
-                       f"({t_bins:.2f} s)")}
+def cpu_baseline(mesh, mu, spec):
+    """The oracle on one whole frame of the workload (every ray cast by brute
+    force in FP64, then the per-bin pipeline), timed on this host's cores."""
+    t_rays, t_bins, threads, r = oracle_pass(mesh, mu, spec, spec.n_rays)
+    total = t_rays + t_bins
+    return {"value": 1.0 / total, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "Mrays_s": spec.n_rays / total / 1e6,
+            "sample": (f"one whole frame: all {spec.n_rays} rays cast by brute force in FP64 ({t_rays:.1f} s) "
+                       f"+ binning, noise, normalisation and fan of the full image ({t_bins:.2f} s)")}, r, total
+
+
+def arm_config(frames, rays_per_frame, world):
+    """The workload description both arms print."""
+    return {"workload": WORKLOAD, "frames_per_step": frames, "rays_per_frame": rays_per_frame,
+            "step": "batched forward (graph) + batched adjoint (graph)",
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world}"}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step casts a seeded sample of
+    `--ref-rays` rays of one frame of the workload by brute force in FP64 and
+    runs the per-bin pipeline on the full image; the step counts as that
+    share of a frame, so ms_per_step is the step's wall time and value the
+    frames per second it sustains."""
     rank, world, _ = rank_info()
     if rank != 0:
         return 0
     mesh, mu, base, poses, _ = workload(0, 1, max(args.frames, 1), args.small)
     import oracle as O
     tv = O.tri_verts(mesh)
-    n = min(args.cpu_rays, 2048)
+    n = min(args.ref_rays, base.n_rays)
     for k in range(args.warmup):
-        oracle_frame_time(mesh, mu, poses[k % len(poses)], 256, seed=k, tv=tv)
-    times = []
-    threads = 0
+        oracle_pass(mesh, mu, poses[k % len(poses)], 256, seed=k, tv=tv)
+    walls, threads = [], 0
     for k in range(args.steps):
-        pf, threads, _, _ = oracle_frame_time(mesh, mu, poses[k % len(poses)], n, seed=100 + k, tv=tv)
-        times.append(pf)
-    value = 1.0 / float(np.mean(times))
+        t0 = time.perf_counter()
+        _, _, threads, _ = oracle_pass(mesh, mu, poses[k % len(poses)], n, seed=100 + k, tv=tv)
+        walls.append(time.perf_counter() - t0)
+    share = n / base.n_rays
+    value = share * args.steps / float(np.sum(walls))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(walls)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "frames_per_step": 1},
+            "data": "synthetic", "config": arm_config(args.frames, base.n_rays, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(threads), "kind": "oracle",
-                             "sample": f"each step: {n} of {base.n_rays} rays of one frame in FP64 brute "
-                                       f"force, scaled to the frame, + the full per-bin pipeline"},
+                             "sample": f"each step: {n} of the {base.n_rays} rays of one frame ({share:.3f} "
+                                       f"of the frame) cast by brute force in FP64, then binning, noise, "
+                                       f"normalisation and fan of the full image; a step counts as "
+                                       f"{share:.3f} frames"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -321,15 +344,112 @@ def trace_roofline(son, items, trace_ms, peak, scale=1.0):
             "sample": f"{len(items)} of {int(round(len(items) * scale))} items"}
 
 
-def measure_configs(son, steps, peak):
-    """Throughput of the other workload configurations (not the headline line),
-    each with its ray-cast launch's HBM roofline."""
+def oracle_subset(mesh, mu, spec, frac, seed, params=None, grad=False, fan=True, tv=None):
+    """Seconds per frame of the oracle, estimated from a seeded subset of
+    `frac` of the frame's rays (cast by brute force in FP64; the time scaled by
+    the frame's rays over the subset's) plus the per-bin pipeline of the full
+    image (binning, noise, normalisation, fan when the sensor has one) and,
+    with `grad`, the analytic gradient (its per-ray part scaled likewise)."""
+    import oracle as O
+    params = params or O.Params()
+    tv = O.tri_verts(mesh) if tv is None else tv
+    n = max(32, int(round(frac * spec.n_rays)))
+    ids = np.sort(np.random.default_rng(seed).choice(spec.n_rays, n, replace=False))
+    t0 = time.perf_counter()
+    r = O.render(mesh, mu, ALPHA, GAIN, spec, params, ray_ids=ids, tv=tv)
+    t1 = time.perf_counter()
+    nb = spec.n_range_bins * spec.n_az_bins
+    P = np.zeros(nb)
+    O.lib().oracle_accumulate(n, r["key"], r["score"], nb, P)
+    In = O.noise(spec, P.reshape(spec.n_range_bins, spec.n_az_bins), 0, 0, params)
+    N, _, _ = O.normalise(spec, In, params.normalise)
+    if fan and spec.fan_w > 0:
+        O.fan_image(spec, N, spec.fan_w, spec.fan_h)
+    t2 = time.perf_counter()
+    t_grad = 0.0
+    if grad:
+        G = np.random.default_rng(seed + 1).normal(size=nb) * 1e-3
+        t3 = time.perf_counter()
+        O.grad(mesh, mu, ALPHA, GAIN, spec, params, 0, 0, G, In, r)
+        t_grad = time.perf_counter() - t3
+    per_frame = (t1 - t0) * spec.n_rays / n + (t2 - t1) + t_grad
+    return per_frame, {"rays_cast": n, "of_rays": spec.n_rays, "cast_s": t1 - t0, "per_bin_s": t2 - t1,
+                       "grad_s": t_grad, "threads": int(r["hits"]["threads"])}
+
+
+def measure_configs(son, args, peak, oracle_frame):
+    """The other workload configurations (not the headline line), each with
+    its ray-cast launch's HBM roofline and the oracle's estimate from a ray
+    subset: the differentiable fit, the heterogeneous batch against single
+    renders, the large scene forward + adjoint with recomputed hits, and the
+    dense-ray frame (and, with --configs, the large scene with 1024
+    materials)."""
     import torch
+    import oracle as O
     from paper_2503_01074_gb300 import scenes as S
+    from paper_2503_01074_gb300.autograd import sonar_render
     from paper_2503_01074_gb300.sonar import RenderParams
     stream = torch.cuda.current_stream()
     prm = RenderParams()
+    steps = args.steps
     out = {}
+
+    # differentiable: 64 materials, a target rendered with perturbed parameters,
+    # MSE loss, 32 sequential fit iterations (forward + adjoint each) through
+    # the autograd function on the single-sensor path
+    mesh, mu, hfn = S.single_frame_scene(n_mat=64, mu_lo=0.05, mu_hi=0.95)
+    sid = son.upload_mesh(mesh)
+    spec = S.sensor_single(hfn)
+    mu_t = (mu * np.random.default_rng(5).uniform(0.8, 1.2, 64)).astype(np.float32)
+    target = son.render(sid, spec, son.theta(0.06, 1.2, mu_t), prm, 1, 1, fan=False)["polar"].clone()
+
+    def fit(n_it):
+        th = son.theta(ALPHA, GAIN, mu).requires_grad_(True)
+        opt = torch.optim.Adam([th], lr=0.02)
+        losses = []
+        for _ in range(n_it):
+            opt.zero_grad()
+            loss = torch.mean((sonar_render(th, son, sid, spec, prm, 1, 1, save_hits=True) - target) ** 2)
+            loss.backward()
+            opt.step()
+            losses.append(loss.detach())
+        return [float(x) for x in losses]
+    fit(4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = fit(32)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    b1 = son.batch([(sid, spec, 1, 1)])
+    theta = son.theta(ALPHA, GAIN, mu)
+    for _ in range(3):
+        b1.render(theta, prm, hits=True, fan=False)
+    tr = []
+    for _ in range(steps):
+        b1.render(theta, prm, hits=True, fan=False)
+        tr.append(b1.timings()["trace"])
+    b1.close()
+    ent = {"materials": 64, "iterations": 32, "fwd_bwd_fps": 32 / fit_s, "ms_per_iteration": 1e3 * fit_s / 32,
+           "loss_first": losses[0], "loss_last": losses[-1],
+           "roofline": trace_roofline(son, [(sid, spec)], float(np.mean(tr)), peak)}
+    if oracle_frame is not None:
+        # the oracle's forward is the headline's whole-frame time (same seabed
+        # geometry, so the same brute-force cost), plus its analytic gradient
+        r, t_frame, ospec, omesh, omu = oracle_frame
+        nb = ospec.n_range_bins * ospec.n_az_bins
+        P = np.zeros(nb)
+        O.lib().oracle_accumulate(len(r["key"]), r["key"], r["score"], nb, P)
+        In = O.noise(ospec, P.reshape(ospec.n_range_bins, ospec.n_az_bins), 0, 0, O.Params())
+        G = np.random.default_rng(9).normal(size=nb) * 1e-3
+        t0 = time.perf_counter()
+        O.grad(omesh, omu, ALPHA, GAIN, ospec, O.Params(), 0, 0, G, In, r)
+        t_g = time.perf_counter() - t0
+        ent["oracle"] = {"fwd_bwd_fps": 1.0 / (t_frame + t_g), "kind": "oracle",
+                         "sample": f"one whole frame cast by brute force ({t_frame:.1f} s, the headline baseline's) "
+                                   f"+ the analytic gradient ({t_g:.2f} s)"}
+    out["differentiable_fit"] = ent
+    son.release(sid)
+
     # heterogeneous batch: 4 scenes, 128 sensors of three shapes, vs 128 single renders
     scenes, mu, sensors = S.batched_workload()
     sids = [son.upload_mesh(m) for m, _ in scenes]
@@ -347,18 +467,32 @@ def measure_configs(son, steps, peak):
     ms_s = timed(singles, max(2, steps // 2), stream)
     b.render(theta, prm, hits=True, fan=True)
     ph = b.timings()
-    out["heterogeneous_batch"] = {"sensors": len(items), "rays": rays, "batched_fwd_fps": len(items) / ms_b * 1e3,
-                                  "single_fwd_fps": len(items) / ms_s * 1e3,
-                                  "batched_Mrays_s": rays / ms_b / 1e3, "speedup": ms_s / ms_b, "phase_ms": ph,
-                                  "roofline": trace_roofline(son, [(sid, spec) for sid, spec, _, _ in items],
-                                                             ph["trace"], peak)}
+    ent = {"sensors": len(items), "rays": rays, "batched_fwd_fps": len(items) / ms_b * 1e3,
+           "single_fwd_fps": len(items) / ms_s * 1e3, "batched_Mrays_s": rays / ms_b / 1e3,
+           "speedup": ms_s / ms_b, "phase_ms": ph,
+           "roofline": trace_roofline(son, [(sid, spec) for sid, spec, _, _ in items], ph["trace"], peak)}
+    if oracle_frame is not None:
+        est, shapes = {}, {}
+        for si, spec in sensors:
+            key = (spec.n_beams, spec.n_elev, spec.n_range_bins)
+            if key not in est:
+                est[key], shapes[str(key)] = oracle_subset(scenes[si][0], mu, spec, 0.01, 31)
+        per_frame = [est[(spec.n_beams, spec.n_elev, spec.n_range_bins)] for _, spec in sensors]
+        ent["oracle"] = {"fwd_fps": len(per_frame) / float(np.sum(per_frame)), "kind": "oracle",
+                         "sample": "1% of the rays of one sensor of each shape (beams, elevations, range bins), "
+                                   "scaled to its frame, + its per-bin pipeline; weighted by the batch's mix",
+                         "shapes": shapes}
+    out["heterogeneous_batch"] = ent
     b.close()
     del outs
     for sid in sids:
         son.release(sid)
-    # large: 33.6M triangles, 1024 x 256 rays, 4000 bins, 0.1-60 m; forward + adjoint, hits
-    # recomputed; with 64 materials, and with 1024 (the per-material gradient at that scale)
+
+    # large: 33.6M triangles, 1024 x 256 rays, 4000 bins, 0.1-60 m; 256 poses,
+    # forward + adjoint with recomputed hits (and with 1024 materials: --configs)
     for n_mat, name in ((64, "large"), (1024, "large_1024_materials")):
+        if n_mat == 1024 and not args.configs:
+            continue
         t0 = time.perf_counter()
         mesh, mu, hfn = S.large_scene(n_mat=n_mat)
         gen_s = time.perf_counter() - t0
@@ -381,12 +515,18 @@ def measure_configs(son, steps, peak):
             b.backward(theta, prm, G, hits=False, out=d)
         ms = timed(fwd_adj, max(2, steps // 2), stream)
         ph = b.timings()
-        out[name] = {"tris": mesh.n_tris, "materials": n_mat, "frames": len(poses), "rays_per_frame": base.n_rays,
-                     "fwd_adj_recompute_fps": len(poses) / ms * 1e3,
-                     "Mrays_s": len(poses) * base.n_rays / ms / 1e3, "scene_build_ms": build_ms,
-                     "scene_generation_s": gen_s, "phase_ms": ph,
-                     "roofline": trace_roofline(son, [(sid, p) for p in poses[::32]], ph["trace"], peak,
-                                                scale=len(poses) / len(poses[::32]))}
+        ent = {"tris": mesh.n_tris, "materials": n_mat, "frames": len(poses), "rays_per_frame": base.n_rays,
+               "fwd_adj_recompute_fps": len(poses) / ms * 1e3,
+               "Mrays_s": len(poses) * base.n_rays / ms / 1e3, "scene_build_ms": build_ms,
+               "scene_generation_s": gen_s, "phase_ms": ph,
+               "roofline": trace_roofline(son, [(sid, p) for p in poses[::32]], ph["trace"], peak,
+                                          scale=len(poses) / len(poses[::32]))}
+        if oracle_frame is not None and n_mat == 64:
+            pf, info = oracle_subset(mesh, mu, poses[0], 0.002, 41, grad=True, fan=False)
+            ent["oracle"] = {"fwd_adj_fps": 1.0 / pf, "kind": "oracle", "detail": info,
+                             "sample": "0.2% of one frame's rays cast by brute force and differentiated, scaled "
+                                       "to the frame, + the per-bin pipeline and gradient terms of the full image"}
+        out[name] = ent
         b.close()
         son.release(sid)
         del mesh
@@ -399,9 +539,15 @@ def measure_configs(son, steps, peak):
     b.autotune(theta, prm)
     ms = timed(lambda: b.render(theta, prm, hits=True, fan=True), steps, stream)
     ph = b.timings()
-    out["dense_rays"] = {"rays_per_frame": spec.n_rays, "bins": 350 * 220, "fwd_fps": 1e3 / ms,
-                         "Mrays_s": spec.n_rays / ms / 1e3, "phase_ms": ph,
-                         "roofline": trace_roofline(son, [(sid, spec)], ph["trace"], peak)}
+    ent = {"rays_per_frame": spec.n_rays, "bins": 350 * 220, "fwd_fps": 1e3 / ms,
+           "Mrays_s": spec.n_rays / ms / 1e3, "phase_ms": ph,
+           "roofline": trace_roofline(son, [(sid, spec)], ph["trace"], peak)}
+    if oracle_frame is not None:
+        pf, info = oracle_subset(mesh, mu, spec, 0.005, 51)
+        ent["oracle"] = {"fwd_fps": 1.0 / pf, "kind": "oracle", "detail": info,
+                         "sample": "0.5% of the frame's rays cast by brute force, scaled to the frame, + the "
+                                   "per-bin pipeline of the full image"}
+    out["dense_rays"] = ent
     b.close()
     son.release(sid)
     return out
@@ -535,10 +681,42 @@ def run_ours(args):
 
     extras = {}
     e2e = None
+    # algorithmic bytes per frame (the per-kernel figures of the design notes):
+    # the ray cast reads the 4-wide nodes (128 B) and triangles (48 B) its rays
+    # touch and writes a 16-byte record per ray; binning reads the records and
+    # writes I~; the normalisation + fan reads I~, writes N and the fan image
+    # and reads the shared coordinate table (16 B a pixel, once per launch);
+    # the adjoint reads I~ and G per bin, the records and a G gather per ray
+    alg = 0
+    visits = tests = exact = 0
+    for p in poses:
+        st = son.trace_stats(sid, p, prm)
+        alg += st["nodes_touched"] * 128 + st["tris_touched"] * 48 + p.n_rays * 16
+        visits += st["visits"]
+        tests += st["tests"]
+        exact += st["exact_tests"]
+    nbin, npx, nray = base.n_range_bins * base.n_az_bins, base.fan_w * base.fan_h, base.n_rays
+    bytes_frame = {"trace": alg / B, "bin_noise": nray * 16 + nbin * 4,
+                   "normalise_fan": nbin * 8 + npx * 4 + npx * 16 / B,
+                   "adjoint_rows": nbin * 8, "adjoint_gather": nray * 20}
+    fwd_bytes = bytes_frame["trace"] + bytes_frame["bin_noise"] + bytes_frame["normalise_fan"]
+    adj_bytes = bytes_frame["adjoint_rows"] + bytes_frame["adjoint_gather"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    def leg_roofline(bytes_per_frame, ms_per_frame):
+        gbs = bytes_per_frame / (ms_per_frame / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "algorithmic_bytes_per_frame": int(bytes_per_frame), "device_ms_per_frame": ms_per_frame}
+
     if not args.no_extras:
-        # batched forward only
+        # batched forward only (the forward graph), its phases from in-graph events
         e_f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        fwd_ms = []
+        fwd_ms, fwd_ph = [], []
         for k in range(args.steps):
             flush.zero_()
             e_f[0].record(stream)
@@ -546,8 +724,20 @@ def run_ours(args):
             e_f[1].record(stream)
             torch.cuda.synchronize()
             fwd_ms.append(e_f[0].elapsed_time(e_f[1]))
-        extras["batched_fwd_fps"] = B / (np.mean(fwd_ms) / 1000.0)
-        # the plain single-sensor path: one sonar_render call per frame (no batching, no graph)
+            fwd_ph.append(batch.timings())
+        fms = float(np.mean(fwd_ms))
+        extras["batched_fwd"] = {
+            "fps": B / (fms / 1e3), "device_ms_per_step": fms,
+            "phase_ms": {k: float(np.mean([q[k] for q in fwd_ph])) for k in ("trace", "bin_noise", "normalise_fan")},
+            "roofline": leg_roofline(fwd_bytes, fms / B),
+            "phase_frac": {k: bytes_frame[k] * B / (float(np.mean([q[k] for q in fwd_ph])) / 1e3) / 1e9 / peak
+                           for k in ("trace", "bin_noise", "normalise_fan")}}
+        extras["batched_fwd_fps"] = extras["batched_fwd"]["fps"]
+        # the plain single-sensor path: one sonar_render (and sonar_render_backward)
+        # call per frame, no batching, no graph.  Host loop: the Python loop as a
+        # caller runs it.  Device: the same calls queued behind a long sleep
+        # kernel, so that the host is ahead and the frames' kernels run back to
+        # back (their device time without host launch gaps).
         out = {"polar": torch.empty(base.n_range_bins, base.n_az_bins, device=dev),
                "noised": torch.empty(base.n_range_bins, base.n_az_bins, device=dev),
                "hits": torch.empty(base.n_rays, 4, dtype=torch.int32, device=dev),
@@ -555,20 +745,46 @@ def run_ours(args):
         g1 = G[: base.n_range_bins * base.n_az_bins].view(base.n_range_bins, base.n_az_bins)
         for p in poses[:4]:
             son.render(sid, p, theta, prm, 0, 0, hits=True, fan=True, outputs=out)
+            son.backward(sid, p, theta, prm, 0, 0, g1, out["noised"], out["hits"])
         torch.cuda.synchronize()
+
+        def frames(with_adj):
+            for j, p in enumerate(poses):
+                son.render(sid, p, theta, prm, SEED, fids[j], hits=True, fan=True, outputs=out)
+                if with_adj:
+                    son.backward(sid, p, theta, prm, SEED, fids[j], g1, out["noised"], out["hits"])
+
+        single = {}
         for with_adj in (False, True):
-            ms = []
+            host, devt = [], []
             for k in range(max(2, args.steps // 2)):
                 flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
                 e_f[0].record(stream)
-                for j, p in enumerate(poses):
-                    son.render(sid, p, theta, prm, SEED, fids[j], hits=True, fan=True, outputs=out)
-                    if with_adj:
-                        son.backward(sid, p, theta, prm, SEED, fids[j], g1, out["noised"], out["hits"])
+                frames(with_adj)
                 e_f[1].record(stream)
                 torch.cuda.synchronize()
-                ms.append(e_f[0].elapsed_time(e_f[1]))
-            extras["single_fwd_adj_fps" if with_adj else "single_fwd_fps"] = B / (np.mean(ms) / 1000.0)
+                host.append(1e3 * (time.perf_counter() - t0))
+                flush.zero_()
+                torch.cuda._sleep(60_000_000)          # about 30 ms of GPU time, longer than the host loop
+                e_f[0].record(stream)
+                frames(with_adj)
+                e_f[1].record(stream)
+                torch.cuda.synchronize()
+                devt.append(e_f[0].elapsed_time(e_f[1]))
+            tag = "fwd_adj" if with_adj else "fwd"
+            hms, dms = float(np.mean(host)) / B, float(np.mean(devt)) / B
+            single[tag] = {"fps": 1e3 / hms, "host_ms_per_frame": hms, "device_ms_per_frame": dms,
+                           "device_fps": 1e3 / dms,
+                           "roofline": leg_roofline(fwd_bytes + (adj_bytes if with_adj else 0), dms)}
+            extras["single_fwd_adj_fps" if with_adj else "single_fwd_fps"] = single[tag]["fps"]
+        single["launches_per_frame"] = {"fwd": 4, "adjoint": 3}
+        single["note"] = ("host_ms_per_frame: the Python loop of one sonar_render (+ sonar_render_backward) "
+                          "call per frame; device_ms_per_frame: the same calls with the host ahead of the "
+                          "GPU (queued behind a sleep kernel), i.e. the frame's kernels and their "
+                          "device-side launch gaps alone")
+        extras["single"] = single
         # end to end through the public API with host buffers: every step copies
         # its inputs (theta, the upstream gradient image, the pose descriptors)
         # from pinned host memory and reads its outputs (polar and fan images,
@@ -698,24 +914,9 @@ def run_ours(args):
                "Mbeams_s": 4 * nv * ns / float(np.mean(dms)) / 1e3,
                "valid_fraction": float(((fl & 16) != 0).float().mean().item())}
         del dp, dv, o
-    # algorithmic bytes of one ray-cast launch: per frame, the 4-wide BVH nodes
-    # (128 B) and triangles (48 B) its rays touch, plus the 16-byte hit record of
-    # every ray; summed over the B frames the launch renders
-    alg = 0
-    visits = tests = exact = 0
-    for p in poses:
-        st = son.trace_stats(sid, p, prm)
-        alg += st["nodes_touched"] * 128 + st["tris_touched"] * 48 + p.n_rays * 16
-        visits += st["visits"]
-        tests += st["tests"]
-        exact += st["exact_tests"]
+    # the dominant kernel's roofline: one ray-cast launch's algorithmic bytes
+    # (summed over the B frames it renders) over its in-graph time
     achieved = alg / (trace_ms / 1000.0) / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
     tune_row = [r for r in son.tune_get().tolist() if r[:4] == [base.n_beams, base.n_elev, base.n_range_bins,
                                                                  base.n_az_bins]]
     tb = traffic_from_profile(tune_row[0][5], tune_row[0][7]) if tune_row else None
@@ -743,27 +944,36 @@ def run_ours(args):
     extras["node4_visits_per_ray"] = visits / (B * base.n_rays)
     extras["tri_tests_per_ray"] = tests / (B * base.n_rays)
     extras["fp64_tests_per_ray"] = exact / (B * base.n_rays)
+    # the whole forward + adjoint step against the HBM roofline, and per phase
+    ph_mean = {k: float(np.mean([p[k] for p in phase])) for k in phase[0]}
+    extras["step_roofline"] = dict(leg_roofline(fwd_bytes + adj_bytes, total_ms / args.steps / B),
+                                   phase_frac={k: bytes_frame[k] * B / (ph_mean[k] / 1e3) / 1e9 / peak
+                                               for k in ph_mean})
 
-    configs = measure_configs(son, args.steps, peak) if (args.configs and rank == 0) else None
-
-    cpu = None
+    cpu = oracle_frame = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(mesh, mu, poses[0], min(args.cpu_rays, base.n_rays))
+        cpu, r0, t_frame = cpu_baseline(mesh, mu, poses[0])
+        oracle_frame = (r0, t_frame, poses[0], mesh, mu)
+
+    tune_rows = son.tune_get().tolist()     # the headline batch's tune (the configurations re-tune)
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        batch.close()
+        configs = measure_configs(son, args, peak, oracle_frame)
+        batch = None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "frames_per_step": B, "rays_per_frame": rays_per_frame,
-                           "step": "batched forward (graph) + batched adjoint (graph)",
-                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world}"},
+                "config": arm_config(B, rays_per_frame, world),
                 "Mrays_s": value * rays_per_frame / 1e6,
                 "scene_build_ms": build_ms,
-                "phase_ms": {k: float(np.mean([p[k] for p in phase])) for k in phase[0]},
-                "batch": info, "tune": son.tune_get().tolist(),
+                "phase_ms": ph_mean,
+                "batch": info, "tune": tune_rows,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": (kern["forward"] + kern["adjoint"]) * args.steps}
-        line.update({k: float(v) for k, v in extras.items()})
+        line.update({k: (v if isinstance(v, dict) else float(v)) for k, v in extras.items()})
         if uw is not None:
             line["uw_image"] = uw
         if dvl is not None:
@@ -771,7 +981,8 @@ def run_ours(args):
         if configs is not None:
             line["configs"] = configs
         print(json.dumps(line), flush=True)
-    batch.close()
+    if batch is not None:
+        batch.close()
     son.close()
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -89,7 +89,7 @@ __device__ __forceinline__ int mt32(float3 o, float3 d, float4 a, float4 b, floa
     const float inv = 1.0f / det;
     const float u = un * inv, v = vn * inv, w = 1.0f - u - v;
     t = tn * inv;
-    const float ia = 1.0f / adet;
+    const float ia = fabsf(inv);   // = 1 / |det| exactly (the rounding of 1/x is odd in x)
     const float eu = (g * as * ad * ae2 + fabsf(u) * Edet) * ia;
     const float ev = (g * ad * as * ae1 + fabsf(v) * Edet) * ia;
     const float ew = eu + ev + 0x1p-22f;

@@ -183,6 +183,11 @@ def test_fan_of_batch_frame(setup):
     bad = ~flag & ~np.isclose(F, fr, rtol=1e-4, atol=1e-5)
     assert not bad.any(), bad.sum()
     assert (F[~flag] != 0).mean() > 0.3
+    # the fused normalisation + fan resamples I~ scaled by the row maxima: the
+    # same bits as resampling the N it wrote
+    again = d["son"].fan_resample(spec, v["polar"], spec.fan_w, spec.fan_h)
+    torch.cuda.synchronize()
+    assert torch.equal(again, v["fan"])
 
 
 def test_adjoint_full_size_stored_equals_recomputed(setup):

@@ -115,6 +115,29 @@ def test_uneven_beam_and_azimuth_counts(son, tiny, tiny_sid, nb, naz):
     full_check(son, tiny_sid, mesh, mu, 0.05, 1.0, spec, RenderParams())
 
 
+@pytest.mark.parametrize("octant", [(1, 1, 1), (-1, 1, 1), (1, -1, -1), (-1, -1, -1)])
+def test_ray_octants(son, octant):
+    """Every ray of the sensor in one octant of directions, including all
+    components positive and all negative (the cases where a box slot left
+    empty in a 4-wide node sits at +inf along every axis that the ray runs
+    up), against a soup of triangles ahead of it; a larger soup so that the
+    tree has empty slots at several levels."""
+    sx, sy, sz = octant
+    yaw = math.atan2(-sx, sy)                       # forward along (sx, sy) in the x-y plane
+    pitch_down = -sz * math.radians(35.0)
+    fwd = np.array([sx, sy, 0.0]) / math.sqrt(2.0)
+    c = 6.0 * (fwd * math.cos(math.radians(35.0)) + np.array([0.0, 0.0, sz * math.sin(math.radians(35.0))]))
+    mesh = S.random_soup(1500, 40 + sx + 2 * sy + 4 * sz, center=tuple(c), spread=3.0)
+    spec = S.SensorSpec(np.zeros(3, np.float32), S.pose_matrix(yaw, pitch_down), 40, 16, 120, 40,
+                        math.radians(60.0), math.radians(20.0), 0.5, 15.0, 120, 68)
+    d = O.ray_dirs(spec)
+    assert (np.sign(d) == np.array(octant)).all()     # the sensor's rays really lie in the octant
+    sid = son.upload_mesh(mesh)
+    mu = np.array([0.2, 0.5, 0.7, 0.9], np.float32)
+    out, ref = full_check(son, sid, mesh, mu, 0.03, 1.7, spec, RenderParams())
+    assert (ref["hits"]["tri"] >= 0).mean() > 0.3
+
+
 def test_empty_scene(son):
     mesh = S.Mesh(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros(0, np.int32))
     sid = son.upload_mesh(mesh)
