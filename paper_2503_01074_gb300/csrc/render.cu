@@ -586,8 +586,39 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
         float m = -CUDART_INF_F;
         int am = 0x7FFFFFFF;
         float dl = 0.0f;                      // per-lane partial of sum G I~ (few terms)
-        if (((s.polar_off | s.naz) & 3) == 0) {
-            // 16-byte rows: each lane takes 4 consecutive bins per load, in index order
+        if (((s.polar_off | s.naz) & 3) == 0 && s.naz <= 512) {
+            // 16-byte rows of up to 512 bins: every load of the row (I~ and G) is
+            // issued before the first compare, then each lane takes its 4
+            // consecutive bins per vector in index order
+            const float4* In4 = reinterpret_cast<const float4*>(In);
+            const float4* G4 = reinterpret_cast<const float4*>(G);
+            const int n4 = s.naz >> 2;
+            float4 xs[4], ys[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = lane + 32 * k;
+                if (q < n4) {
+                    xs[k] = __ldg(In4 + q);
+                    ys[k] = __ldg(G4 + q);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = lane + 32 * k;
+                if (q >= n4) continue;
+                const float4 x = xs[k], y = ys[k];
+                const int j = q << 2;
+                if (x.x > m) { m = x.x; am = j; }
+                if (x.y > m) { m = x.y; am = j + 1; }
+                if (x.z > m) { m = x.z; am = j + 2; }
+                if (x.w > m) { m = x.w; am = j + 3; }
+                dl = fmaf(y.x, x.x, dl);
+                dl = fmaf(y.y, x.y, dl);
+                dl = fmaf(y.z, x.z, dl);
+                dl = fmaf(y.w, x.w, dl);
+            }
+        } else if (((s.polar_off | s.naz) & 3) == 0) {
+            // wider 16-byte rows: each lane takes 4 consecutive bins per load, in index order
             const float4* In4 = reinterpret_cast<const float4*>(In);
             const float4* G4 = reinterpret_cast<const float4*>(G);
 #pragma unroll 4
