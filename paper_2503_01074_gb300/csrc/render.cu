@@ -216,8 +216,13 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         const int drow = nt / cw, dcol = nt - drow * cw;
         int row = tid / cw, col = tid - row * cw;
         const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
+        // the sensor fields this loop reads, in registers (the loop's shared-memory
+        // stores would otherwise make the compiler reload them every bin)
+        const uint32_t naz_r = (uint32_t)S.naz, c0_r = (uint32_t)U.c0, flo = S.frame_lo, fhi = S.frame_hi;
+        const float rmin_r = S.rmin;
+        float* const noised_r = a.noised + S.polar_off;
         for (int k = tid; k < nbin; k += nt) {
-            const uint32_t b = (uint32_t)(row * S.naz + U.c0 + col);
+            const uint32_t b = (uint32_t)row * naz_r + c0_r + (uint32_t)col;
             float P;
             if (per_beam) {
                 P = 0.0f;
@@ -225,16 +230,16 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
             } else {
                 P = acc[k];
             }
-            const U4 x = bin_draws(b, S, K);
+            const U4 x = philox10(U4{b, flo, 0u, fhi}, K);   // bin_draws with the frame words held
             const float w_sa = rayleigh_of(x, sig_sa);
-            const float rc = fmaf(small_u2f(row) + 0.5f, dr, S.rmin);
+            const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin_r);
             const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
             if (a.binned) a.binned[S.polar_off + b] = P;
             if (P != 0.0f) {
                 acc[k] = P;
                 list[atomicAdd(&s_count, 1)] = k;
             } else {
-                a.noised[S.polar_off + b] = additive;
+                noised_r[b] = additive;
                 acc[k] = additive;
             }
             row += drow;
@@ -455,10 +460,10 @@ __device__ __forceinline__ float fan_blend(uint4 c, const float* P) {
     return __fadd_rn(__fmul_rn(ur, top), __fmul_rn(wr, bot));
 }
 
-// One block = a kFanSide x kFanSide square of one sensor's fan (a square maps
-// to a compact patch of the polar image, so its gathers stay in cache); lane
-// x of a 64-thread row takes column x, rows step by 4.  A sensor with a
-// coordinate table reads its pixels' coordinates from it.
+// One block = a kTileSide x kTileSide square of one sensor's fan (a square
+// maps to a compact patch of the polar image, so its gathers stay in cache);
+// lane x of a kTileSide-thread row takes column x, rows step by 256 / kTileSide.
+// A sensor with a coordinate table reads its pixels' coordinates from it.
 __global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
     __shared__ SensorDev S;
     __shared__ int s_sq;
@@ -473,15 +478,15 @@ __global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
         }
     }
     __syncthreads();
-    const int sx = (S.fan_w + kFanSide - 1) / kFanSide;
-    const int u = (s_sq % sx) * kFanSide + (threadIdx.x & (kFanSide - 1));
-    const int v0 = (s_sq / sx) * kFanSide + (threadIdx.x / kFanSide);
+    const int sx = (S.fan_w + kTileSide - 1) / kTileSide;
+    const int u = (s_sq % sx) * kTileSide + (threadIdx.x & (kTileSide - 1));
+    const int v0 = (s_sq / sx) * kTileSide + (threadIdx.x / kTileSide);
     if (u >= S.fan_w) return;
     const float* P = a.polar + S.polar_off;
     float* F = a.fan + S.fan_off;
     const uint4* lut = S.fan_lut;
 #pragma unroll 4
-    for (int k = 0; k < kFanSide; k += 256 / kFanSide) {
+    for (int k = 0; k < kTileSide; k += 256 / kTileSide) {
         const int v = v0 + k;
         if (v >= S.fan_h) break;
         const int64_t pix = (int64_t)v * S.fan_w + u;

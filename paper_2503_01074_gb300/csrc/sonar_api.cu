@@ -392,7 +392,7 @@ sonar_status single_post(sonar_ctx* ctx, const SensorDev& S, int normalise, cons
         f.one = S;
         f.polar = polar;
         f.fan = fan;
-        CU(launch_fan_tiles(f, fan_squares(S.fan_w, S.fan_h), s), "fan launch");
+        CU(launch_fan_tiles(f, tile_squares(S.fan_w, S.fan_h), s), "fan launch");
     }
     return SONAR_OK;
 }
@@ -462,7 +462,7 @@ extern "C" sonar_status sonar_fan_resample(sonar_ctx_t ctx, const sonar_sensor* 
     f.one = S;
     f.polar = d_polar;
     f.fan = d_fan;
-    CU(launch_fan_tiles(f, fan_squares(S.fan_w, S.fan_h), (cudaStream_t)stream), "fan launch");
+    CU(launch_fan_tiles(f, tile_squares(S.fan_w, S.fan_h), (cudaStream_t)stream), "fan launch");
     return SONAR_OK;
 }
 
@@ -682,7 +682,7 @@ sonar_status batch_plan(sonar_batch* b) {
         polar_end = std::max<int64_t>(polar_end, it.polar_offset + (int64_t)S.nr * S.naz);
         b->hs[k] = S;
         b->fan_prefix[k + 1] =
-            b->fan_prefix[k] + (S.fan_w > 0 ? fan_squares(S.fan_w, S.fan_h) : 0);
+            b->fan_prefix[k] + (S.fan_w > 0 ? tile_squares(S.fan_w, S.fan_h) : 0);
         b->trace_prefix[k + 1] = b->trace_prefix[k] + S.trace_blocks;
         block_votes[t.block] += (int64_t)S.nb * S.ne;
         for (int tile = 0; tile < S.n_tiles; ++tile) {

@@ -238,6 +238,13 @@ constexpr int kFanSide = 64;    // resample blocks are kFanSide x kFanSide pixel
 __host__ __device__ inline int32_t fan_squares(int32_t w, int32_t h) {
     return ((w + kFanSide - 1) / kFanSide) * ((h + kFanSide - 1) / kFanSide);
 }
+// The fan of a sensor that shares no coordinate table (single frames, sensors
+// of unique geometry) goes in smaller squares: one frame's fan is then several
+// blocks per SM instead of about one.
+constexpr int kTileSide = 32;
+__host__ __device__ inline int32_t tile_squares(int32_t w, int32_t h) {
+    return ((w + kTileSide - 1) / kTileSide) * ((h + kTileSide - 1) / kTileSide);
+}
 
 // DVL measurement of n poses (four beams each).
 struct DvlArgs {
