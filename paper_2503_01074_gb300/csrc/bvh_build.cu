@@ -8,10 +8,11 @@
 //   5. bottom-up refit                leaf-to-root climb, second visitor merges boxes
 //   6. packing                        runs of <= kLeafMax triangles collapsed into
 //                                     leaves; 48-byte triangles
-//   7. 4-wide collapse                top-down, one 4-wide level per pass: a node
-//                                     opens its largest-area internal child until
-//                                     it has four children; 128-byte SoA nodes in
-//                                     breadth-first order
+//   7. 4-wide collapse                a bottom-up dynamic programme gives each
+//                                     subtree's least SAH cost in 1..4 child slots;
+//                                     top-down, one 4-wide level per pass, each node
+//                                     takes the children it chose; 128-byte SoA nodes
+//                                     in breadth-first order
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -394,7 +395,7 @@ __global__ void k_pack_tris(const float* verts, const int32_t* tris, const int32
     mat_orig[o] = m;
 }
 
-// ---- greedy 4-wide collapse (top-down, one level of the 4-wide tree per pass) ----
+// ---- 4-wide collapse (top-down, one level of the 4-wide tree per pass) ----
 // A child under construction is a side of a binary node: x = 2 * p + side, its
 // box and handle at pairs[2 x] (lo, handle bits) and pairs[2 x + 1] (hi).
 
@@ -403,29 +404,99 @@ __device__ __forceinline__ float half_area(float4 lo, float4 hi) {
     return dx * dy + dy * dz + dz * dx;
 }
 
-// The children of entry e (internal binary node q[e]): start from its two
-// sides; while there are fewer than four and one of them is internal, replace
-// the internal child with the largest surface area by its two sides.
-__global__ void k_collapse_pick(const int32_t* q, int64_t nq, const float4* pairs, int32_t* picks,
-                                uint32_t* nint) {
+constexpr float kSahTri = 0.7f;   // SAH cost of a triangle test relative to a 4-wide node visit
+// ---- SAH-driven collapse: a bottom-up dynamic programme over the binary tree ----
+// cost(x, k): the least SAH cost of the subtree at side x (a leaf run or a
+// binary node) when it may take up to k (1..4) child slots of the 4-wide node
+// above it.  One slot: the side itself, a leaf (area x triangles x kSahTri) or
+// a 4-wide node (area + the cost of its subtree spread over four slots); k
+// slots: the better of that and opening the node, its two sides sharing the k
+// slots.  dec[p] keeps, for k = 2..4, the split of p's slots between its sides
+// (2 bits each) and whether p is better opened (bit 6 + k).
+__device__ __forceinline__ float side_cost(const float4* pairs, const float4* cost, int64_t x, int k) {
+    const float4 lo = pairs[2 * x], hi = pairs[2 * x + 1];
+    const int32_t h = __float_as_int(lo.w);
+    if (h < 0) return half_area(lo, hi) * kSahTri * (float)(((~h) & 7) + 1);
+    const float4 c = __ldcg(cost + h);
+    return k == 1 ? c.x : k == 2 ? c.y : k == 3 ? c.z : c.w;
+}
+
+__global__ void k_sah_dp(int64_t n, const int32_t* parent, int32_t* visits, const float4* pairs, float4* cost,
+                         int32_t* dec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t p = parent[(n - 1) + i];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&visits[p], 1) == 0) return;   // the other child is still on its way
+        float S0[5], S1[5];
+        for (int k = 1; k <= 4; ++k) {
+            S0[k] = side_cost(pairs, cost, 2 * (int64_t)p, k);
+            S1[k] = side_cost(pairs, cost, 2 * (int64_t)p + 1, k);
+        }
+        // opening p into m slots: the best split j | m - j
+        float open[5];
+        int split[5];
+        for (int m = 2; m <= 4; ++m) {
+            open[m] = 3.0e38f;
+            split[m] = 1;
+            for (int j = 1; j < m; ++j) {
+                const float v = S0[j] + S1[m - j];
+                if (v < open[m]) { open[m] = v; split[m] = j; }
+            }
+        }
+        const float4 l0 = pairs[4 * (int64_t)p], h0 = pairs[4 * (int64_t)p + 1];
+        const float4 l1 = pairs[4 * (int64_t)p + 2], h1 = pairs[4 * (int64_t)p + 3];
+        const float4 ul = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.0f);
+        const float4 uh = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.0f);
+        const float wide = half_area(ul, uh) + open[4];
+        float c[5];
+        c[1] = wide;
+        int d = 0;
+        for (int k = 2; k <= 4; ++k) {
+            const bool opened = open[k] < wide;
+            c[k] = opened ? open[k] : wide;
+            d |= (split[k] << (2 * (k - 2))) | (opened ? (1 << (6 + k)) : 0);
+        }
+        d |= split[4] << 16;   // the split of a 4-wide node's own four slots (k = 4 above, opened or not)
+        __stcg(cost + p, make_float4(c[1], c[2], c[3], c[4]));
+        dec[p] = d;
+        __threadfence();
+        p = parent[p];
+    }
+}
+
+// The children of entry e (internal binary node q[e]) from the programme: p's
+// four slots split between its sides, each side taking its slots as a leaf, a
+// 4-wide node (one slot) or opened further.
+__global__ void k_collapse_pick(const int32_t* q, int64_t nq, const float4* pairs, const int32_t* dec,
+                                    int32_t* picks, uint32_t* nint) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nq) return;
     const int32_t p = q[e];
-    int32_t c[4] = {2 * p, 2 * p + 1, -1, -1};
-    int cnt = 2;
-    while (cnt < 4) {
-        int best = -1;
-        float best_a = -1.0f;
-        for (int k = 0; k < cnt; ++k) {
-            const float4 lo = pairs[2 * (int64_t)c[k]];
-            if (__float_as_int(lo.w) < 0) continue;   // a leaf
-            const float a = half_area(lo, pairs[2 * (int64_t)c[k] + 1]);
-            if (a > best_a) { best_a = a; best = k; }
+    int32_t c[4] = {-1, -1, -1, -1};
+    int cnt = 0;
+    // work list of (side, slots)
+    int32_t ws[8];
+    int wk[8];
+    int nw = 0;
+    {
+        const int j = (dec[p] >> 16) & 3;
+        ws[nw] = 2 * p + 1; wk[nw++] = 4 - j;
+        ws[nw] = 2 * p;     wk[nw++] = j;
+    }
+    while (nw > 0) {
+        const int32_t x = ws[--nw];
+        const int k = wk[nw];
+        const int32_t h = __float_as_int(pairs[2 * (int64_t)x].w);
+        const bool opened = h >= 0 && k >= 2 && ((dec[h] >> (6 + k)) & 1);
+        if (!opened) {
+            c[cnt++] = x;
+            continue;
         }
-        if (best < 0) break;
-        const int32_t h = __float_as_int(pairs[2 * (int64_t)c[best]].w);
-        c[best] = 2 * h;
-        c[cnt++] = 2 * h + 1;
+        const int j = (dec[h] >> (2 * (k - 2))) & 3;
+        ws[nw] = 2 * h + 1; wk[nw++] = k - j;
+        ws[nw] = 2 * h;     wk[nw++] = j;
     }
     uint32_t ni = 0;
     for (int k = 0; k < 4; ++k) {
@@ -621,7 +692,12 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
                                                                blo, bhi);
         k_pack_nodes<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, range,
                                                                         blo, bhi, pad, pairs);
-        // greedy collapse, level by level: picks and prefixes of all levels are
+        float4* sah_cost = S.get<float4>(n);
+        int32_t* sah_dec = S.get<int32_t>(n);
+        if (S.err != cudaSuccess) { *msg = "out of device memory (build scratch)"; return SONAR_ERR_OOM; }
+        cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
+        k_sah_dp<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, parent, visits, pairs, sah_cost, sah_dec);
+        // collapse, level by level: picks and prefixes of all levels are
         // kept (indexed by 4-wide node), nodes written once their count is known
         float4 root_hi;
         e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
@@ -634,7 +710,7 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
             lbase.push_back(base);
             lcount.push_back(nq);
             const int64_t ch = (nq + kScanChunk - 1) / kScanChunk;
-            k_collapse_pick<<<blocks_for(nq, kThreads), kThreads, 0, st>>>(qa, nq, pairs, picks + 4 * base,
+            k_collapse_pick<<<blocks_for(nq, kThreads), kThreads, 0, st>>>(qa, nq, pairs, sah_dec, picks + 4 * base,
                                                                             nint + base);
             k_scan_sums<<<(unsigned)ch, kThreads, 0, st>>>(nint + base, nq, fsums);
             k_scan_top<<<1, 1024, 0, st>>>(fsums, ch);
