@@ -553,8 +553,9 @@ def measure_configs(son, args, peak, oracle_frame):
     return out
 
 
+# the kernel's sources, and the scene build whose tree shape decides what it reads
 RAY_CAST_SOURCES = ("paper_2503_01074_gb300/csrc/trace.cu", "paper_2503_01074_gb300/csrc/devmath.cuh",
-                    "paper_2503_01074_gb300/csrc/sonar_internal.cuh")
+                    "paper_2503_01074_gb300/csrc/sonar_internal.cuh", "paper_2503_01074_gb300/csrc/bvh_build.cu")
 
 
 def ray_cast_sources_sha():
