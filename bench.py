@@ -326,17 +326,47 @@ def timed(fn, steps, stream):
     return float(np.mean(ms))
 
 
+WIDE = 16   # ray-cast variant flag of a tuning row: the 8-wide tree (256-byte nodes)
+
+
+def shape_of(spec):
+    return [spec.n_beams, spec.n_elev, spec.n_range_bins, spec.n_az_bins]
+
+
+def trace_bytes(son, sid, spec, prm, wide=None):
+    """Algorithmic bytes of one sensor's ray cast, from the counter mode: the
+    distinct nodes (128 bytes 4-wide, 256 bytes 8-wide) and 48-byte triangles
+    its rays touch plus a 16-byte record per ray.  The counter mode walks the
+    tree of the shape's tuning row; `wide` (True / False) walks the 8-wide or
+    4-wide tree instead, by a temporary row."""
+    rows = son.tune_get().tolist()
+    row = next((r for r in rows if r[:4] == shape_of(spec)), None)
+    if wide is not None:
+        forced = list(row) if row else shape_of(spec) + [1, 8, 128, 8]
+        forced[7] = (forced[7] | WIDE) if wide else (forced[7] & ~WIDE)
+        son.tune_set([forced])
+        row = forced
+    try:
+        st = son.trace_stats(sid, spec, prm)
+    finally:
+        if wide is not None:
+            if rows:
+                son.tune_set(rows)
+            # a temporary row for an untuned shape cannot be removed; it names the
+            # tiles that shape would default to
+    node = 256 if (row and row[7] & WIDE) else 128
+    return st["nodes_touched"] * node + st["tris_touched"] * 48 + spec.n_rays * 16, st
+
+
 def trace_roofline(son, items, trace_ms, peak, scale=1.0):
     """The ray-cast launch's HBM roofline for a batch: algorithmic bytes (per
-    item, the distinct 128-byte nodes and 48-byte triangles its rays touch
-    plus a 16-byte record per ray, from the counter mode) over the launch's
-    in-graph time.  `items` may be a sample of the batch, `scale` the batch
-    size over the sample size."""
+    item, the distinct nodes and triangles its rays touch plus a 16-byte record
+    per ray, from the counter mode) over the launch's in-graph time.  `items`
+    may be a sample of the batch, `scale` the batch size over the sample size."""
     from paper_2503_01074_gb300.sonar import RenderParams
     alg = 0
     for sid, spec in items:
-        st = son.trace_stats(sid, spec, RenderParams())
-        alg += st["nodes_touched"] * 128 + st["tris_touched"] * 48 + spec.n_rays * 16
+        alg += trace_bytes(son, sid, spec, RenderParams())[0]
     alg *= scale
     gbs = alg / (trace_ms / 1000.0) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
@@ -683,16 +713,16 @@ def run_ours(args):
     extras = {}
     e2e = None
     # algorithmic bytes per frame (the per-kernel figures of the design notes):
-    # the ray cast reads the 4-wide nodes (128 B) and triangles (48 B) its rays
-    # touch and writes a 16-byte record per ray; binning reads the records and
+    # the ray cast reads the nodes (128 B 4-wide, 256 B 8-wide) and triangles
+    # (48 B) its rays touch and writes a 16-byte record per ray; binning reads the records and
     # writes I~; the normalisation + fan reads I~, writes N and the fan image
     # and reads the shared coordinate table (16 B a pixel, once per launch);
     # the adjoint reads I~ and G per bin, the records and a G gather per ray
     alg = 0
     visits = tests = exact = 0
     for p in poses:
-        st = son.trace_stats(sid, p, prm)
-        alg += st["nodes_touched"] * 128 + st["tris_touched"] * 48 + p.n_rays * 16
+        b_, st = trace_bytes(son, sid, p, prm)
+        alg += b_
         visits += st["visits"]
         tests += st["tests"]
         exact += st["exact_tests"]
@@ -755,7 +785,16 @@ def run_ours(args):
                 if with_adj:
                     son.backward(sid, p, theta, prm, SEED, fids[j], g1, out["noised"], out["hits"])
 
-        single = {}
+        # the single-sensor path walks the tree its own launch calls for: the
+        # 8-wide one when the frame's ray cast is at most two waves of one-warp
+        # blocks (64 per SM), as the library decides
+        row = next((r for r in son.tune_get().tolist() if r[:4] == shape_of(base)), None)
+        tbw = row[5] if row else 8
+        blocks1 = -(-base.n_beams // tbw) * -(-base.n_elev // (32 // tbw))
+        wide1 = blocks1 <= 2 * 32 * torch.cuda.get_device_properties(dev).multi_processor_count
+        tr1 = float(np.mean([trace_bytes(son, sid, p, prm, wide=wide1)[0] for p in poses]))
+        fwd_bytes1 = fwd_bytes - bytes_frame["trace"] + tr1
+        single = {"tree": "8-wide" if wide1 else "4-wide"}
         for with_adj in (False, True):
             host, devt = [], []
             for k in range(max(2, args.steps // 2)):
@@ -778,7 +817,7 @@ def run_ours(args):
             hms, dms = float(np.mean(host)) / B, float(np.mean(devt)) / B
             single[tag] = {"fps": 1e3 / hms, "host_ms_per_frame": hms, "device_ms_per_frame": dms,
                            "device_fps": 1e3 / dms,
-                           "roofline": leg_roofline(fwd_bytes + (adj_bytes if with_adj else 0), dms)}
+                           "roofline": leg_roofline(fwd_bytes1 + (adj_bytes if with_adj else 0), dms)}
             extras["single_fwd_adj_fps" if with_adj else "single_fwd_fps"] = single[tag]["fps"]
         single["launches_per_frame"] = {"fwd": 4, "adjoint": 3}
         single["note"] = ("host_ms_per_frame: the Python loop of one sonar_render (+ sonar_render_backward) "
@@ -934,8 +973,9 @@ def run_ours(args):
             l2["frac"] = l2["achieved"] / l2["peak"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tb["dram"] * B if tb is not None else None), "l2": l2,
-                "warp_tile": (f"{tune_row[0][5]} beams x {32 // tune_row[0][5]} elevations, occupancy variant "
-                              f"{tune_row[0][7]}" if tune_row else None),
+                "warp_tile": (f"{tune_row[0][5]} beams x {32 // tune_row[0][5]} elevations, variant "
+                              f"{tune_row[0][7]} ({'8' if tune_row[0][7] & WIDE else '4'}-wide tree, registers "
+                              f"{'capped at 64' if tune_row[0][7] & 8 else 'uncapped'})" if tune_row else None),
                 "kernel": "k_trace (ray generation + LBVH walk + Moller-Trumbore + bin key)",
                 "avg_launch_ms": trace_ms, "algorithmic_bytes_per_launch": int(alg),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}

@@ -154,8 +154,9 @@ sonar_status sonar_scene_upload(sonar_ctx_t ctx, const float* d_verts, int64_t n
 /* Releases a scene (synchronises the device first). */
 sonar_status sonar_scene_release(sonar_ctx_t ctx, int32_t scene_id);
 
-/* Scene statistics: out[0] triangles, out[1] internal nodes, out[2] tree
- * height, out[3] maximum material id, out[4] device bytes held. */
+/* Scene statistics: out[0] triangles, out[1] nodes of the 4-wide tree, out[2]
+ * binary tree height, out[3] maximum material id, out[4] device bytes held
+ * (both trees and the triangles). */
 sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t scene_id, int64_t out[5]);
 
 /* One sonar frame (Sec. III-A-2): ray cast, intensity (Eq. 2), polar
@@ -330,8 +331,13 @@ sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
 /* Tuning cache entries: writes up to `cap` rows of 8 int32
  * (n_beams, n_elev, n_range_bins, n_az_bins, cols, tb, block, occ), tb =
  * beams per ray-cast warp (a power of two <= 32; elevations = 32 / tb), occ =
- * 8 to cap the ray-cast registers at 64 (32 one-warp blocks per SM), else 0
- * and returns the number of entries in *count. */
+ * the ray-cast variant, a sum of flags: 8 caps its registers at 64 (32
+ * one-warp blocks per SM), 16 walks the 8-wide tree instead of the 4-wide one
+ * (both are built per scene; the hit records are the same either way).  A
+ * batch takes the row's variant; a single-sensor call takes the 8-wide tree
+ * when its ray cast is at most two waves of one-warp blocks (64 per SM), the
+ * 4-wide one otherwise, and no register cap when it is at most one wave.
+ * Returns the number of entries in *count. */
 sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count);
 
 /* Adds or replaces cache entries (rows as above), e.g. loaded from a file. */
@@ -400,8 +406,9 @@ sonar_status sonar_dvl_schedule(sonar_ctx_t ctx, const float* d_period, int64_t 
 
 /* ---- counters (roofline evidence) ---- */
 
-/* Re-casts the rays of one sensor (with the warp tiles tuned for its shape)
- * and counts 4-wide BVH node visits (128 bytes each) and triangle tests;
+/* Re-casts the rays of one sensor (with the warp tiles and the tree its
+ * shape's tuning row names: 4-wide nodes of 128 bytes, or 8-wide ones of 256
+ * bytes with variant flag 16) and counts node visits and triangle tests;
  * also marks every node and triangle touched.  out[0] node visits, out[1]
  * triangle tests, out[2] distinct nodes touched, out[3] distinct triangles
  * touched, out[4] rays, out[5] decisions taken exactly in float-float

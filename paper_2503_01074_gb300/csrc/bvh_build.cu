@@ -8,11 +8,12 @@
 //   5. bottom-up refit                leaf-to-root climb, second visitor merges boxes
 //   6. packing                        runs of <= kLeafMax triangles collapsed into
 //                                     leaves; 48-byte triangles
-//   7. 4-wide collapse                a bottom-up dynamic programme gives each
-//                                     subtree's least SAH cost in 1..4 child slots;
-//                                     top-down, one 4-wide level per pass, each node
-//                                     takes the children it chose; 128-byte SoA nodes
-//                                     in breadth-first order
+//   7. wide collapse                  twice, into a 4-wide and an 8-wide tree: a
+//                                     bottom-up dynamic programme gives each subtree's
+//                                     least SAH cost in 1..W child slots; top-down,
+//                                     one level per pass, each node takes the children
+//                                     it chose; SoA nodes (128 or 256 bytes) in
+//                                     breadth-first order
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -404,24 +405,36 @@ __device__ __forceinline__ float half_area(float4 lo, float4 hi) {
     return dx * dy + dy * dz + dz * dx;
 }
 
-constexpr float kSahTri = 0.7f;   // SAH cost of a triangle test relative to a 4-wide node visit
+constexpr float kSahTri = 0.7f;   // SAH cost of a triangle test relative to a wide-node visit
 // ---- SAH-driven collapse: a bottom-up dynamic programme over the binary tree ----
 // cost(x, k): the least SAH cost of the subtree at side x (a leaf run or a
-// binary node) when it may take up to k (1..4) child slots of the 4-wide node
+// binary node) when it may take up to k (1..W) child slots of the W-wide node
 // above it.  One slot: the side itself, a leaf (area x triangles x kSahTri) or
-// a 4-wide node (area + the cost of its subtree spread over four slots); k
-// slots: the better of that and opening the node, its two sides sharing the k
-// slots.  dec[p] keeps, for k = 2..4, the split of p's slots between its sides
-// (2 bits each) and whether p is better opened (bit 6 + k).
-__device__ __forceinline__ float side_cost(const float4* pairs, const float4* cost, int64_t x, int k) {
+// a W-wide node (area + the cost of its subtree spread over W slots); k slots:
+// the better of that and opening the node, its two sides sharing the k slots.
+// dec[p] keeps, for k = 2..W, the split of p's slots between its sides
+// (SplitBits<W> bits each, from bit 0) and whether p is better opened (one bit
+// each above the splits).  cost holds W floats per binary node.
+template <int W>
+struct Wide {
+    static constexpr int kSplitBits = W == 8 ? 3 : 2;
+    static constexpr int kOpenBit = kSplitBits * (W - 1);
+    __host__ __device__ static constexpr int split(int32_t d, int k) {
+        return (d >> (kSplitBits * (k - 2))) & ((1 << kSplitBits) - 1);
+    }
+    __host__ __device__ static constexpr bool opened(int32_t d, int k) { return (d >> (kOpenBit + k - 2)) & 1; }
+};
+
+template <int W>
+__device__ __forceinline__ float side_cost(const float4* pairs, const float* cost, int64_t x, int k) {
     const float4 lo = pairs[2 * x], hi = pairs[2 * x + 1];
     const int32_t h = __float_as_int(lo.w);
     if (h < 0) return half_area(lo, hi) * kSahTri * (float)(((~h) & 7) + 1);
-    const float4 c = __ldcg(cost + h);
-    return k == 1 ? c.x : k == 2 ? c.y : k == 3 ? c.z : c.w;
+    return __ldcg(cost + (int64_t)W * h + (k - 1));
 }
 
-__global__ void k_sah_dp(int64_t n, const int32_t* parent, int32_t* visits, const float4* pairs, float4* cost,
+template <int W>
+__global__ void k_sah_dp(int64_t n, const int32_t* parent, int32_t* visits, const float4* pairs, float* cost,
                          int32_t* dec) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -429,15 +442,15 @@ __global__ void k_sah_dp(int64_t n, const int32_t* parent, int32_t* visits, cons
     while (p >= 0) {
         __threadfence();
         if (atomicAdd(&visits[p], 1) == 0) return;   // the other child is still on its way
-        float S0[5], S1[5];
-        for (int k = 1; k <= 4; ++k) {
-            S0[k] = side_cost(pairs, cost, 2 * (int64_t)p, k);
-            S1[k] = side_cost(pairs, cost, 2 * (int64_t)p + 1, k);
+        float S0[W + 1], S1[W + 1];
+        for (int k = 1; k <= W; ++k) {
+            S0[k] = side_cost<W>(pairs, cost, 2 * (int64_t)p, k);
+            S1[k] = side_cost<W>(pairs, cost, 2 * (int64_t)p + 1, k);
         }
         // opening p into m slots: the best split j | m - j
-        float open[5];
-        int split[5];
-        for (int m = 2; m <= 4; ++m) {
+        float open[W + 1];
+        int split[W + 1];
+        for (int m = 2; m <= W; ++m) {
             open[m] = 3.0e38f;
             split[m] = 1;
             for (int j = 1; j < m; ++j) {
@@ -449,17 +462,15 @@ __global__ void k_sah_dp(int64_t n, const int32_t* parent, int32_t* visits, cons
         const float4 l1 = pairs[4 * (int64_t)p + 2], h1 = pairs[4 * (int64_t)p + 3];
         const float4 ul = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.0f);
         const float4 uh = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.0f);
-        const float wide = half_area(ul, uh) + open[4];
-        float c[5];
-        c[1] = wide;
-        int d = 0;
-        for (int k = 2; k <= 4; ++k) {
+        // one slot: p as a W-wide node of its own, its two sides sharing the W slots
+        const float wide = half_area(ul, uh) + open[W];
+        __stcg(cost + (int64_t)W * p, wide);
+        int32_t d = 0;
+        for (int k = 2; k <= W; ++k) {
             const bool opened = open[k] < wide;
-            c[k] = opened ? open[k] : wide;
-            d |= (split[k] << (2 * (k - 2))) | (opened ? (1 << (6 + k)) : 0);
+            __stcg(cost + (int64_t)W * p + (k - 1), opened ? open[k] : wide);
+            d |= (split[k] << (Wide<W>::kSplitBits * (k - 2))) | (opened ? (1 << (Wide<W>::kOpenBit + k - 2)) : 0);
         }
-        d |= split[4] << 16;   // the split of a 4-wide node's own four slots (k = 4 above, opened or not)
-        __stcg(cost + p, make_float4(c[1], c[2], c[3], c[4]));
         dec[p] = d;
         __threadfence();
         p = parent[p];
@@ -467,89 +478,97 @@ __global__ void k_sah_dp(int64_t n, const int32_t* parent, int32_t* visits, cons
 }
 
 // The children of entry e (internal binary node q[e]) from the programme: p's
-// four slots split between its sides, each side taking its slots as a leaf, a
-// 4-wide node (one slot) or opened further.
+// W slots split between its sides, each side taking its slots as a leaf, a
+// W-wide node (one slot) or opened further.  Every side keeps at least one
+// slot, so at most W sides are pending at once.
+template <int W>
 __global__ void k_collapse_pick(const int32_t* q, int64_t nq, const float4* pairs, const int32_t* dec,
-                                    int32_t* picks, uint32_t* nint) {
+                                int32_t* picks, uint32_t* nint) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nq) return;
     const int32_t p = q[e];
-    int32_t c[4] = {-1, -1, -1, -1};
+    int32_t c[W];
+    for (int k = 0; k < W; ++k) c[k] = -1;
     int cnt = 0;
     // work list of (side, slots)
-    int32_t ws[8];
-    int wk[8];
+    int32_t ws[W + 1];
+    int wk[W + 1];
     int nw = 0;
     {
-        const int j = (dec[p] >> 16) & 3;
-        ws[nw] = 2 * p + 1; wk[nw++] = 4 - j;
+        const int j = Wide<W>::split(dec[p], W);
+        ws[nw] = 2 * p + 1; wk[nw++] = W - j;
         ws[nw] = 2 * p;     wk[nw++] = j;
     }
     while (nw > 0) {
         const int32_t x = ws[--nw];
         const int k = wk[nw];
         const int32_t h = __float_as_int(pairs[2 * (int64_t)x].w);
-        const bool opened = h >= 0 && k >= 2 && ((dec[h] >> (6 + k)) & 1);
-        if (!opened) {
+        if (h < 0 || k < 2 || !Wide<W>::opened(dec[h], k)) {
             c[cnt++] = x;
             continue;
         }
-        const int j = (dec[h] >> (2 * (k - 2))) & 3;
+        const int j = Wide<W>::split(dec[h], k);
         ws[nw] = 2 * h + 1; wk[nw++] = k - j;
         ws[nw] = 2 * h;     wk[nw++] = j;
     }
     uint32_t ni = 0;
-    for (int k = 0; k < 4; ++k) {
-        picks[4 * e + k] = c[k];
+    for (int k = 0; k < W; ++k) {
+        picks[W * e + k] = c[k];
         if (c[k] >= 0 && __float_as_int(pairs[2 * (int64_t)c[k]].w) >= 0) ++ni;
     }
     nint[e] = ni;
 }
 
 // The next level's entries: the internal children, in entry and slot order.
+template <int W>
 __global__ void k_collapse_enqueue(const int32_t* picks, const uint32_t* prefix, int64_t nq, const float4* pairs,
                                    int32_t* q_next) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nq) return;
     uint32_t r = prefix[e];
-    for (int k = 0; k < 4; ++k) {
-        const int32_t x = picks[4 * e + k];
+    for (int k = 0; k < W; ++k) {
+        const int32_t x = picks[W * e + k];
         if (x < 0) continue;
         const int32_t h = __float_as_int(pairs[2 * (int64_t)x].w);
         if (h >= 0) q_next[r++] = h;
     }
 }
 
-// Writes the 4-wide nodes of one level: entry e is node base + e; its r-th
-// internal child is node base_next + prefix[e] + r.  Empty slots hold an
-// inverted box that no ray enters and the empty handle.
+// Writes the W-wide nodes of one level: entry e is node base + e, W / 4
+// halves in the 4-wide layout; its r-th internal child is node base_next +
+// prefix[e] + r.  Empty slots hold an inverted box that no ray enters and the
+// empty handle.
+template <int W>
 __global__ void k_collapse_write(const int32_t* picks, const uint32_t* prefix, int64_t nq, int64_t base,
-                                 int64_t base_next, const float4* pairs, float4* nodes4) {
+                                 int64_t base_next, const float4* pairs, float4* nodes) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nq) return;
-    float lo[3][4], hi[3][4];
-    int32_t hh[4];
     uint32_t r = prefix[e];
-    for (int k = 0; k < 4; ++k) {
-        const int32_t x = picks[4 * e + k];
-        if (x < 0) {
-            for (int a = 0; a < 3; ++a) lo[a][k] = hi[a][k] = __int_as_float(0x7F800000);
-            hh[k] = kEmpty;
-            continue;
+    for (int half = 0; half < W / 4; ++half) {
+        float lo[3][4], hi[3][4];
+        int32_t hh[4];
+        for (int k = 0; k < 4; ++k) {
+            const int32_t x = picks[W * e + 4 * half + k];
+            if (x < 0) {
+                for (int a = 0; a < 3; ++a) lo[a][k] = hi[a][k] = __int_as_float(0x7F800000);
+                hh[k] = kEmpty;
+                continue;
+            }
+            const float4 l = pairs[2 * (int64_t)x], h = pairs[2 * (int64_t)x + 1];
+            lo[0][k] = l.x; lo[1][k] = l.y; lo[2][k] = l.z;
+            hi[0][k] = h.x; hi[1][k] = h.y; hi[2][k] = h.z;
+            const int32_t c = __float_as_int(l.w);
+            hh[k] = c >= 0 ? (int32_t)(base_next + r++) : c;
         }
-        const float4 l = pairs[2 * (int64_t)x], h = pairs[2 * (int64_t)x + 1];
-        lo[0][k] = l.x; lo[1][k] = l.y; lo[2][k] = l.z;
-        hi[0][k] = h.x; hi[1][k] = h.y; hi[2][k] = h.z;
-        const int32_t c = __float_as_int(l.w);
-        hh[k] = c >= 0 ? (int32_t)(base_next + r++) : c;
+        float4* o = nodes + 2 * W * (base + e) + 8 * half;
+        for (int a = 0; a < 3; ++a) {
+            o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+            o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+        }
+        o[6] = make_float4(__int_as_float(hh[0]), __int_as_float(hh[1]), __int_as_float(hh[2]),
+                           __int_as_float(hh[3]));
+        o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
-    float4* o = nodes4 + 8 * (base + e);
-    for (int a = 0; a < 3; ++a) {
-        o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
-        o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
-    }
-    o[6] = make_float4(__int_as_float(hh[0]), __int_as_float(hh[1]), __int_as_float(hh[2]), __int_as_float(hh[3]));
-    o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -576,6 +595,69 @@ struct BuildScratch {
         for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], st);
     }
 };
+
+// Buffers of the wide collapse, sized for the widest tree and shared by both.
+struct CollapseScratch {
+    float* cost;       // [8 n] SAH cost per binary node and slot count
+    int32_t* dec;      // [n] the programme's decisions per binary node
+    int32_t *qa, *qb;  // [n] binary nodes of the current / next level
+    int32_t* picks;    // [8 n] per wide node: the binary sides in its slots
+    uint32_t *nint, *prefix, *fsums;
+};
+
+// One W-wide tree from the binary hierarchy in `pairs`: the cost programme
+// bottom-up, then top-down one level per pass (picks and prefixes of every
+// level kept, indexed by wide node), the nodes written once their count is
+// known.  *nodes_out is a new allocation owned by the caller.
+template <int W>
+cudaError_t collapse_tree(const CollapseScratch& C, int64_t n, const int32_t* parent, int32_t* visits,
+                          const float4* pairs, cudaStream_t st, float4** nodes_out, int64_t* count_out,
+                          int* depth_out) {
+    *nodes_out = nullptr;
+    cudaError_t e = cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
+    if (e != cudaSuccess) return e;
+    k_sah_dp<W><<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, parent, visits, pairs, C.cost, C.dec);
+    const int32_t zero = 0;
+    e = cudaMemcpyAsync(C.qa, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
+    std::vector<int64_t> lbase, lcount;
+    int64_t base = 0, nq = 1;
+    int32_t *qa = C.qa, *qb = C.qb;
+    while (e == cudaSuccess && nq > 0) {
+        if (base + nq > n) { e = cudaErrorInvalidValue; break; }   // cannot happen: nodes are distinct
+        lbase.push_back(base);
+        lcount.push_back(nq);
+        const int64_t ch = (nq + kScanChunk - 1) / kScanChunk;
+        k_collapse_pick<W><<<blocks_for(nq, kThreads), kThreads, 0, st>>>(qa, nq, pairs, C.dec, C.picks + W * base,
+                                                                          C.nint + base);
+        k_scan_sums<<<(unsigned)ch, kThreads, 0, st>>>(C.nint + base, nq, C.fsums);
+        k_scan_top<<<1, 1024, 0, st>>>(C.fsums, ch);
+        k_scan_apply<<<(unsigned)ch, kThreads, 0, st>>>(C.nint + base, nq, C.fsums, C.prefix + base);
+        k_collapse_enqueue<W><<<blocks_for(nq, kThreads), kThreads, 0, st>>>(C.picks + W * base, C.prefix + base,
+                                                                             nq, pairs, qb);
+        uint32_t last[2] = {0, 0};
+        e = cudaMemcpyAsync(&last[0], C.prefix + base + nq - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&last[1], C.nint + base + nq - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        base += nq;
+        nq = (int64_t)last[0] + last[1];
+        int32_t* t = qa; qa = qb; qb = t;
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t count = base;
+    float4* nodes = nullptr;
+    e = cudaMalloc(&nodes, sizeof(float4) * 2 * W * std::max<int64_t>(count, 1));
+    if (e != cudaSuccess) return e;
+    for (size_t L = 0; L < lbase.size(); ++L) {
+        const int64_t nxt = L + 1 < lbase.size() ? lbase[L + 1] : count;
+        k_collapse_write<W><<<blocks_for(lcount[L], kThreads), kThreads, 0, st>>>(
+            C.picks + W * lbase[L], C.prefix + lbase[L], lcount[L], lbase[L], nxt, pairs, nodes);
+    }
+    *nodes_out = nodes;
+    *count_out = count;
+    *depth_out = (int)lbase.size();
+    return cudaGetLastError();
+}
 
 sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, const int32_t* mat,
                          int64_t nt, cudaStream_t st, SceneStore* out, std::string* msg) {
@@ -667,7 +749,7 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
     out->bytes = sizeof(float4) * 3 * n + sizeof(int32_t) * n;
 
     k_pack_tris<<<blocks_for(n, kThreads), kThreads, 0, st>>>(verts, tris, mat, v0, n, tri_out, mat_orig);
-    int height = 0, depth4 = 0;
+    int height = 0, depth4 = 0, depth8 = 0;
     if (n <= kLeafMax) {
         out->root = leaf_handle(0, (int32_t)n);
         if (n > 1) {
@@ -678,13 +760,15 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
         }
     } else {
         float4* pairs = S.get<float4>(4 * (n - 1));
-        int32_t* qa = S.get<int32_t>(n);
-        int32_t* qb = S.get<int32_t>(n);
-        int32_t* picks = S.get<int32_t>(4 * n);
-        uint32_t* nint = S.get<uint32_t>(n);
-        uint32_t* prefix = S.get<uint32_t>(n);
-        const int64_t fchunks = (n + kScanChunk - 1) / kScanChunk;
-        uint32_t* fsums = S.get<uint32_t>(fchunks);
+        CollapseScratch C{};
+        C.cost = S.get<float>(8 * n);
+        C.dec = S.get<int32_t>(n);
+        C.qa = S.get<int32_t>(n);
+        C.qb = S.get<int32_t>(n);
+        C.picks = S.get<int32_t>(8 * n);
+        C.nint = S.get<uint32_t>(n);
+        C.prefix = S.get<uint32_t>(n);
+        C.fsums = S.get<uint32_t>((n + kScanChunk - 1) / kScanChunk);
         if (S.err != cudaSuccess) { *msg = "out of device memory (build scratch)"; return SONAR_ERR_OOM; }
         k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(k0, n, child, parent, range);
         cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
@@ -692,73 +776,44 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
                                                                blo, bhi);
         k_pack_nodes<<<blocks_for(n - 1, kThreads), kThreads, 0, st>>>(verts, tris, v0, n, child, range,
                                                                         blo, bhi, pad, pairs);
-        float4* sah_cost = S.get<float4>(n);
-        int32_t* sah_dec = S.get<int32_t>(n);
-        if (S.err != cudaSuccess) { *msg = "out of device memory (build scratch)"; return SONAR_ERR_OOM; }
-        cudaMemsetAsync(visits, 0, sizeof(int32_t) * (n - 1), st);
-        k_sah_dp<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, parent, visits, pairs, sah_cost, sah_dec);
-        // collapse, level by level: picks and prefixes of all levels are
-        // kept (indexed by 4-wide node), nodes written once their count is known
         float4 root_hi;
         e = cudaMemcpyAsync(&root_hi, bhi, sizeof root_hi, cudaMemcpyDeviceToHost, st);
-        const int32_t zero = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(qa, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
-        std::vector<int64_t> lbase, lcount;
-        int64_t base = 0, nq = 1;
-        while (e == cudaSuccess && nq > 0) {
-            if (base + nq > n) { e = cudaErrorInvalidValue; break; }   // cannot happen: nodes are distinct
-            lbase.push_back(base);
-            lcount.push_back(nq);
-            const int64_t ch = (nq + kScanChunk - 1) / kScanChunk;
-            k_collapse_pick<<<blocks_for(nq, kThreads), kThreads, 0, st>>>(qa, nq, pairs, sah_dec, picks + 4 * base,
-                                                                            nint + base);
-            k_scan_sums<<<(unsigned)ch, kThreads, 0, st>>>(nint + base, nq, fsums);
-            k_scan_top<<<1, 1024, 0, st>>>(fsums, ch);
-            k_scan_apply<<<(unsigned)ch, kThreads, 0, st>>>(nint + base, nq, fsums, prefix + base);
-            k_collapse_enqueue<<<blocks_for(nq, kThreads), kThreads, 0, st>>>(picks + 4 * base, prefix + base, nq,
-                                                                               pairs, qb);
-            uint32_t last[2] = {0, 0};
-            e = cudaMemcpyAsync(&last[0], prefix + base + nq - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(&last[1], nint + base + nq - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            base += nq;
-            nq = (int64_t)last[0] + last[1];
-            int32_t* t = qa; qa = qb; qb = t;
+        if (e == cudaSuccess)
+            e = collapse_tree<4>(C, n, parent, visits, pairs, st, &out->nodes, &out->n_pairs, &depth4);
+        if (e == cudaSuccess)
+            e = collapse_tree<8>(C, n, parent, visits, pairs, st, &out->nodes8, &out->n_nodes8, &depth8);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            *msg = std::string("build failed: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? SONAR_ERR_OOM : SONAR_ERR_CUDA;
         }
-        if (e != cudaSuccess) { *msg = std::string("build failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
         memcpy(&height, &root_hi.w, 4);
-        const int64_t n4 = base;
-        float4* nodes = nullptr;
-        if (cudaMalloc(&nodes, sizeof(float4) * 8 * std::max<int64_t>(n4, 1)) != cudaSuccess) {
-            *msg = "out of device memory (scene nodes)";
-            return SONAR_ERR_OOM;
-        }
-        out->nodes = nodes;
-        out->n_pairs = n4;
-        out->bytes += sizeof(float4) * 8 * n4;
-        for (size_t L = 0; L < lbase.size(); ++L) {
-            const int64_t nxt = L + 1 < lbase.size() ? lbase[L + 1] : n4;
-            k_collapse_write<<<blocks_for(lcount[L], kThreads), kThreads, 0, st>>>(
-                picks + 4 * lbase[L], prefix + lbase[L], lcount[L], lbase[L], nxt, pairs, nodes);
-        }
-        depth4 = (int)lbase.size();
+        out->bytes += sizeof(float4) * (8 * out->n_pairs + 16 * out->n_nodes8);
         out->root = 0;
     }
     out->height = height;
     e = cudaGetLastError();
     if (e != cudaSuccess) { *msg = std::string("build kernel launch failed: ") + cudaGetErrorString(e); return SONAR_ERR_CUDA; }
-    // a visit pushes at most three children, one visit per level of the 4-wide
-    // tree on any path: the walk never needs more than 3 * depth + 1 entries
+    // a visit pushes at most W - 1 children, one visit per level of the W-wide
+    // tree on any path: the walk never needs more than (W - 1) depth + 1
+    // entries.  An 8-wide tree too deep for the stack is dropped (rays then
+    // walk the 4-wide one).
     if (3 * depth4 + 1 > kStackMax) {
         *msg = "hierarchy too deep for the traversal stack (4-wide depth " + std::to_string(depth4) + ")";
         return SONAR_ERR_ARG;
+    }
+    if (out->nodes8 && 7 * depth8 + 1 > kStackMax) {
+        cudaFree(out->nodes8);
+        out->bytes -= sizeof(float4) * 16 * out->n_nodes8;
+        out->nodes8 = nullptr;
+        out->n_nodes8 = 0;
     }
     return SONAR_OK;
 }
 
 void free_scene(SceneStore* s) {
     cudaFree(s->nodes);
+    cudaFree(s->nodes8);
     cudaFree(s->tris);
     cudaFree(s->mat_orig);
     *s = SceneStore{};

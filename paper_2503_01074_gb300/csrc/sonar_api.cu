@@ -24,7 +24,8 @@ struct Tune {
     int cols = 0;     // binning: azimuth columns per work unit (0: derive)
     int tb = 0;       // tracing: beams per warp tile, elevations = 32 / tb (0: derive)
     int block = 128;  // binning: threads per block
-    int occ = 0;      // tracing: 8 = cap registers at 64 for 32 one-warp blocks per SM, 0 = no cap
+    int occ = 0;      // tracing variant: kTraceCap caps registers at 64 (32 one-warp blocks per SM),
+                      // kTraceWide walks the 8-wide tree
 };
 
 using ShapeKey = std::array<int, 4>;   // n_beams, n_elev, n_range_bins, n_az_bins
@@ -145,12 +146,33 @@ Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
     return t;
 }
 
+// The tree a ray-cast launch of `blocks` one-warp blocks walks: the 8-wide one
+// when the launch is at most two waves (32 resident blocks per SM), where a
+// ray's chain of dependent node loads sets the time, else the 4-wide one,
+// which costs fewer instructions per ray when the GPU is full.
+int wide_for_launch(const sonar_ctx* ctx, int64_t blocks) {
+    return blocks <= 2ll * 32 * ctx->sm_count ? kTraceWide : 0;
+}
+
+// The ray-cast variant of one sensor's own launch (tile tb from its tuning
+// row, variant `occ` of that row): the tree by the launch size, and no
+// register cap for a launch of at most one wave, which cannot use the
+// occupancy that the cap buys.
+int single_variant(const sonar_ctx* ctx, const sonar_sensor& s, int tb, int occ) {
+    const int64_t be = 32 / tb;
+    const int64_t blocks = ((s.n_beams + tb - 1) / tb) * ((s.n_elev + be - 1) / be);
+    if (blocks <= 32ll * ctx->sm_count) return kTraceWide;
+    return (occ & ~kTraceWide) | wide_for_launch(ctx, blocks);
+}
+
 // A single frame alone on the GPU: the tuned shapes, but at least two binning
-// units per SM (the batch tunes may favour few, large units).
+// units per SM (the batch tunes may favour few, large units), and the ray-cast
+// variant chosen by the frame's own launch size.
 Tune single_tune(const sonar_ctx* ctx, const sonar_sensor& s) {
     Tune t = tune_for(ctx, s);
     const int want = std::max(1, s.n_az_bins / (2 * ctx->sm_count));
     if (t.cols > want) t.cols = want;
+    t.occ = single_variant(ctx, s, t.tb, t.occ);
     return t;
 }
 
@@ -490,6 +512,7 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
         CU(grow(ctx->trig, sizeof(float4) * (size_t)(S.nb + S.ne), s), "scratch allocation");
         CU(grow(ctx->hits, sizeof(sonar_hit) * (size_t)S.nb * S.ne, s), "scratch allocation");
         S.trig = (float4*)ctx->trig.p;
+        S.occ = single_variant(ctx, *sensor, S.tb, S.occ);
         CU(launch_trig(nullptr, S, 1, S.nb + S.ne, s), "trig launch");
         TraceArgs tr{};
         tr.one = S;
@@ -705,10 +728,22 @@ sonar_status batch_plan(sonar_batch* b) {
     int64_t best = -1;
     for (auto& kv : block_votes)
         if (kv.second > best) { best = kv.second; b->block = kv.first; }
-    // the trace launch takes the occupancy variant of the sensor shape with most rays
+    // the trace launch takes the variant of the sensor shape with most rays; an
+    // untuned shape walks the tree the launch size calls for, and the 8-wide tree
+    // only when every scene of the batch has one
     int64_t most = -1;
-    for (const SensorDev& S : b->hs)
-        if ((int64_t)S.nb * S.ne > most) { most = (int64_t)S.nb * S.ne; b->trace_occ = S.occ; }
+    int kmost = 0;
+    for (int k = 0; k < n; ++k) {
+        const SensorDev& S = b->hs[k];
+        if ((int64_t)S.nb * S.ne > most) { most = (int64_t)S.nb * S.ne; b->trace_occ = S.occ; kmost = k; }
+    }
+    if (n > 0) {
+        const sonar_sensor& ms = b->items[kmost].sensor;
+        if (!ctx->tune.count(ShapeKey{ms.n_beams, ms.n_elev, ms.n_range_bins, ms.n_az_bins}))
+            b->trace_occ = (b->trace_occ & ~kTraceWide) | wide_for_launch(ctx, b->trace_prefix[n]);
+        for (const sonar_batch_item& it : b->items)
+            if (!ctx->scenes[it.scene_id].nodes8) b->trace_occ &= ~kTraceWide;
+    }
     b->total_rows = rows;
     b->total_polar = polar_end;
     int64_t all_rays = 0;
@@ -1332,7 +1367,7 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
         float best_ms = 1e30f;
         // the trace warp tile (beams x elevations per warp) and register budget,
         // with default binning shapes
-        for (int occ : {0, 8}) {
+        for (int occ : {0, kTraceCap, kTraceWide, kTraceCap | kTraceWide}) {
             for (int tb : {1, 2, 4, 8, 16, 32}) {
                 ctx->tune[k] = Tune{0, tb, 128, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
@@ -1402,7 +1437,7 @@ extern "C" sonar_status sonar_tune_set(sonar_ctx_t ctx, const int32_t* rows, int
     for (int k = 0; k < count; ++k) {
         const int32_t* r = rows + 8 * k;
         if (r[0] < 1 || r[1] < 1 || r[2] < 1 || r[3] < 1 || r[4] < 1 || r[5] < 1 || r[5] > 32 ||
-            (r[5] & (r[5] - 1)) || r[6] < 32 || r[6] > 512 || (r[6] & 31) || (r[7] != 0 && r[7] != 8))
+            (r[5] & (r[5] - 1)) || r[6] < 32 || r[6] > 512 || (r[6] & 31) || (r[7] & ~(kTraceCap | kTraceWide)))
             return fail(ctx, SONAR_ERR_ARG, "bad tune row " + std::to_string(k));
         ctx->tune[ShapeKey{r[0], r[1], r[2], r[3]}] = Tune{r[4], r[5], r[6], r[7]};
     }

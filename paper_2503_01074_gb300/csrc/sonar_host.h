@@ -10,13 +10,15 @@
 
 namespace sonar {
 
-// A built scene: packed hierarchy and triangles (owned by the context).
+// A built scene: packed hierarchies (4-wide and 8-wide) and triangles (owned
+// by the context).  n_pairs counts 4-wide nodes, n_nodes8 8-wide ones.
 struct SceneStore {
     float4* nodes = nullptr;
+    float4* nodes8 = nullptr;
     float4* tris = nullptr;
     int32_t* mat_orig = nullptr;
     int32_t root = kEmpty;
-    int64_t n_tris = 0, n_pairs = 0;
+    int64_t n_tris = 0, n_pairs = 0, n_nodes8 = 0;
     int32_t height = 0;
     int32_t max_mat = -1;
     size_t bytes = 0;
@@ -27,7 +29,7 @@ sonar_status build_scene(const float* verts, int64_t nv, const int32_t* tris, co
 void free_scene(SceneStore* s);
 
 inline SceneDev scene_dev(const SceneStore& s) {
-    return SceneDev{s.nodes, s.tris, s.mat_orig, s.root, (int32_t)s.n_tris};
+    return SceneDev{s.nodes, s.tris, s.mat_orig, s.root, (int32_t)s.n_tris, s.nodes8};
 }
 
 // Kernel launchers (trace.cu: ray cast and counters; render.cu: binning, noise,

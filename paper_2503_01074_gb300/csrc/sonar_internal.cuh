@@ -5,6 +5,9 @@
 //               structure-of-arrays form: [0] lo.x of children 0..3, [1] hi.x,
 //               [2] lo.y, [3] hi.y, [4] lo.z, [5] hi.z, [6] the 4 child handles,
 //               [7] unused.  Empty slots: boxes at +inf (never entered), kEmpty.
+//   nodes8      8-wide, float4[16] = 256 B per node: two halves in the 4-wide
+//               layout, children 0..3 and 4..7.  Built from the same binary
+//               hierarchy; a handle >= 0 here indexes nodes8.
 //   handles     int32: >= 0 a node index; < 0 a leaf ~((first << 3) | (count - 1)),
 //               a run of 1..8 triangles in leaf order; kEmpty an empty slot.
 //   triangles   float4[3] per triangle in leaf order (48 B):
@@ -35,9 +38,15 @@ struct SceneDev {
     const float4* nodes;      // [n_nodes * 8], 4-wide
     const float4* tris;       // [n_tris * 3]
     const int32_t* mat_orig;  // [n_tris] material of the caller's triangle index
-    int32_t root;             // root handle (kEmpty if the scene has no triangles)
+    int32_t root;             // root handle (kEmpty if the scene has no triangles), both trees
     int32_t n_tris;
+    const float4* nodes8;     // [n_nodes8 * 16], 8-wide, or null (none built)
 };
+
+// SensorDev::occ, the ray-cast variant: bit kTraceCap caps registers at 64 so
+// that 32 one-warp blocks fit an SM; bit kTraceWide walks the 8-wide tree.
+constexpr int kTraceCap = 8;
+constexpr int kTraceWide = 16;
 
 // One sensor of a render, with everything the kernels derive from it.
 struct SensorDev {
@@ -53,7 +62,7 @@ struct SensorDev {
     int32_t cols;        // binning: azimuth columns per work unit
     int32_t n_tiles;     // binning work units of this sensor = ceil(naz / cols)
     int32_t tb;          // trace: beams per warp tile (elevations = 32 / tb)
-    int32_t occ;         // trace: 8 = register budget for 32 one-warp blocks per SM, else none
+    int32_t occ;         // trace: variant bits kTraceCap, kTraceWide
     int32_t trace_blocks;  // trace: one-warp blocks covering the sensor
     int32_t fold_beams;  // binning: deterministic fold into per-beam rows (fits in shared memory)
     int64_t polar_off, hits_off, fan_off, rowmax_off;

@@ -145,20 +145,58 @@ __device__ __forceinline__ int az_bin(const SensorDev& s, int i) {
 // trace: one ray per thread, hit record out
 // ---------------------------------------------------------------------------
 
+// Sorts W child keys ascending in registers: a 5-comparator network for 4,
+// Batcher's odd-even merge sort (19 comparators) for 8.
+template <int W>
+__device__ __forceinline__ void sort_keys(uint32_t (&key)[W]) {
+#define SONAR_USORT(x, y)                            \
+    {                                                \
+        const uint32_t mn = min(key[x], key[y]);     \
+        key[y] = max(key[x], key[y]);                \
+        key[x] = mn;                                 \
+    }
+    if constexpr (W == 4) {
+        SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
+    } else {
+        SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(4, 5) SONAR_USORT(6, 7)
+        SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(4, 6) SONAR_USORT(5, 7)
+        SONAR_USORT(1, 2) SONAR_USORT(5, 6)
+        SONAR_USORT(0, 4) SONAR_USORT(1, 5) SONAR_USORT(2, 6) SONAR_USORT(3, 7)
+        SONAR_USORT(2, 4) SONAR_USORT(3, 5)
+        SONAR_USORT(1, 2) SONAR_USORT(3, 4) SONAR_USORT(5, 6)
+    }
+#undef SONAR_USORT
+}
+
+// The handle in slot k (0 <= k < W) of a node's handles held in registers.
+template <int W>
+__device__ __forceinline__ int32_t child_at(const int32_t (&hs)[W], uint32_t k) {
+    if constexpr (W == 4) {
+        return k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
+    } else {
+        const int32_t h01 = (k & 1) ? hs[1] : hs[0], h23 = (k & 1) ? hs[3] : hs[2];
+        const int32_t h45 = (k & 1) ? hs[5] : hs[4], h67 = (k & 1) ? hs[7] : hs[6];
+        const int32_t h03 = (k & 2) ? h23 : h01, h47 = (k & 2) ? h67 : h45;
+        return (k & 4) ? h47 : h03;
+    }
+}
+
 // Each block is one warp on a tile of tb beams x (32 / tb) elevations of one
 // sensor: lane l traces beam i0 + l % tb, elevation j0 + l / tb, so that the
 // warp's rays sample a compact patch of the field of view.  (One-warp blocks
 // free their slot as soon as their rays are done.)  Records go to their
 // canonical index i * n_elev + j.
 //
-// The walk over the 4-wide hierarchy is a while-while loop: a lane descends
+// The walk over the W-wide hierarchy (W = 4, or 8 for launches too small to
+// fill the GPU, where fewer dependent node loads per ray matter more than the
+// extra box tests per visit) is a while-while loop: a lane descends
 // nearest child first, pushing the other entered children; a lane that
 // reaches a leaf parks it and keeps descending until every active lane of the
 // warp holds one, so that the triangle tests run together.  A lane whose ray
 // is finished writes its record at once and idles until the warp is done.
 // With STATS the kernel also counts node visits and triangle tests and marks
 // the nodes and triangles it touches (records are then not written).
-template <int MINB, bool STATS>
+template <int MINB, bool STATS, int W>
 __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
@@ -208,53 +246,53 @@ __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
     for (;;) {
         if (live) {
             while (node >= 0) {
-                const float4* pn = sc.nodes + 8 * (int64_t)node;
-                float4 lx, hx, ly, hy, lz, hz, chf, unused;
-                ld_node_pair(pn, lx, hx);
-                ld_node_pair(pn + 2, ly, hy);
-                ld_node_pair(pn + 4, lz, hz);
-                ld_node_pair(pn + 6, chf, unused);
-                const int4 ch = make_int4(__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),
-                                          __float_as_int(chf.w));
+                const float4* pn = W == 4 ? sc.nodes + 8 * (int64_t)node : sc.nodes8 + 16 * (int64_t)node;
                 if (STATS) {
                     ++visits;
                     atomicOr(a.tc.node_bits + (node >> 5), 1u << (node & 31));
                 }
                 const float tcut = best_t * 1.00002f;
-                const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
-                const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
-                const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
-                const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
                 // sort key per child: entry distance bits (>= 0, so integer order
-                // is distance order) with the child slot in the two low bits; a
+                // is distance order) with the child slot in the low bits; a
                 // missed child sorts last as 0xFFFFFFFF
-                uint32_t key[4];
+                uint32_t key[W];
+                int32_t hs[W];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
-                    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-                    t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
-                    lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
-                    t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
-                    lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
-                    // an empty slot's box lies at +inf on every axis: along an axis
-                    // the ray travels in the + direction its entry distance is +inf,
-                    // and if it travels in the - direction along all three its exit
-                    // distance is -inf; the exit is also at most tcut, which is
-                    // finite, so an empty slot never passes and needs no handle check
-                    const bool hit = lo <= hi * 1.0000005f;
-                    key[c] = hit ? ((__float_as_uint(lo) & ~3u) | (uint32_t)c) : 0xFFFFFFFFu;
+                for (int half = 0; half < W / 4; ++half) {   // a 4-wide node, or the halves of an 8-wide one
+                    float4 lx, hx, ly, hy, lz, hz, chf, unused;
+                    ld_node_pair(pn + 8 * half, lx, hx);
+                    ld_node_pair(pn + 8 * half + 2, ly, hy);
+                    ld_node_pair(pn + 8 * half + 4, lz, hz);
+                    ld_node_pair(pn + 8 * half + 6, chf, unused);
+                    hs[4 * half + 0] = __float_as_int(chf.x);
+                    hs[4 * half + 1] = __float_as_int(chf.y);
+                    hs[4 * half + 2] = __float_as_int(chf.z);
+                    hs[4 * half + 3] = __float_as_int(chf.w);
+                    const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
+                    const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
+                    const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
+                        float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+                        t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
+                        lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
+                        t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
+                        lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
+                        // an empty slot's box lies at +inf on every axis: along an axis
+                        // the ray travels in the + direction its entry distance is +inf,
+                        // and if it travels in the - direction along all three its exit
+                        // distance is -inf; the exit is also at most tcut, which is
+                        // finite, so an empty slot never passes and needs no handle check
+                        const bool hit = lo <= hi * 1.0000005f;
+                        key[4 * half + c] =
+                            hit ? ((__float_as_uint(lo) & ~(uint32_t)(W - 1)) | (uint32_t)(4 * half + c)) : 0xFFFFFFFFu;
+                    }
                 }
-#define SONAR_USORT(x, y)                                    \
-                {                                            \
-                    const uint32_t mn = min(key[x], key[y]); \
-                    key[y] = max(key[x], key[y]);            \
-                    key[x] = mn;                             \
-                }
-                SONAR_USORT(0, 1) SONAR_USORT(2, 3) SONAR_USORT(0, 2) SONAR_USORT(1, 3) SONAR_USORT(1, 2)
-#undef SONAR_USORT
-                const int nhit = (key[0] != 0xFFFFFFFFu) + (key[1] != 0xFFFFFFFFu) + (key[2] != 0xFFFFFFFFu) +
-                                 (key[3] != 0xFFFFFFFFu);
+                sort_keys<W>(key);
+                int nhit = 0;
+#pragma unroll
+                for (int c = 0; c < W; ++c) nhit += key[c] != 0xFFFFFFFFu;
                 if (nhit == 0) {
                     node = sp > 0 ? stack[--sp] : kEmpty;
                 } else {
@@ -267,14 +305,10 @@ __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
                         break;
                     }
 #pragma unroll
-                    for (int c = 3; c >= 1; --c) {
-                        if (c < nhit) {
-                            const uint32_t k = key[c] & 3u;
-                            stack[sp++] = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
-                        }
+                    for (int c = W - 1; c >= 1; --c) {
+                        if (c < nhit) stack[sp++] = child_at<W>(hs, key[c] & (uint32_t)(W - 1));
                     }
-                    const uint32_t k = key[0] & 3u;
-                    node = k == 0 ? hs[0] : k == 1 ? hs[1] : k == 2 ? hs[2] : hs[3];
+                    node = child_at<W>(hs, key[0] & (uint32_t)(W - 1));
                 }
                 if (node < 0 && node != kEmpty && leaf == 0) {   // park the leaf, keep descending
                     leaf = node;
@@ -387,8 +421,17 @@ cudaError_t launch_trig(const SensorDev* sensors, const SensorDev& one, int n_se
 
 cudaError_t launch_trace(const TraceArgs& a, int blocks, int occupancy, cudaStream_t st) {
     if (blocks > 0) {
-        if (occupancy >= 8) k_trace<32, false><<<blocks, 32, 0, st>>>(a);
-        else k_trace<4, false><<<blocks, 32, 0, st>>>(a);
+        const bool cap = occupancy & kTraceCap;
+        // one sensor's launch on a scene without an 8-wide tree walks the 4-wide
+        // one (a batch's variant is checked against all its scenes on the host)
+        const bool wide = (occupancy & kTraceWide) && (a.sensors || a.one_scene.nodes8);
+        if (wide) {
+            if (cap) k_trace<32, false, 8><<<blocks, 32, 0, st>>>(a);
+            else k_trace<4, false, 8><<<blocks, 32, 0, st>>>(a);
+        } else {
+            if (cap) k_trace<32, false, 4><<<blocks, 32, 0, st>>>(a);
+            else k_trace<4, false, 4><<<blocks, 32, 0, st>>>(a);
+        }
     }
     return cudaGetLastError();
 }
@@ -402,7 +445,10 @@ cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_par
     a.params = p;
     a.err = err;
     a.tc = tc;
-    if (s.trace_blocks > 0) k_trace<4, true><<<s.trace_blocks, 32, 0, st>>>(a);
+    if (s.trace_blocks > 0) {
+        if ((s.occ & kTraceWide) && sc.nodes8) k_trace<4, true, 8><<<s.trace_blocks, 32, 0, st>>>(a);
+        else k_trace<4, true, 4><<<s.trace_blocks, 32, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
