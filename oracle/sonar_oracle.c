@@ -82,18 +82,23 @@ void oracle_philox_batch(const uint32_t* ctr, int64_t n, const uint32_t key[2], 
 /* uniform on (0, 1]: (x + 1) / 2^32, exact in FP64 */
 static double u01(uint32_t x) { return ((double)x + 1.0) * 0x1p-32; }
 
-/* The per-bin draws: counter = (bin, frame lo, 0, frame hi), key = seed.
- * Word 0 -> Rayleigh(sigma_sa) by inversion; words 1, 2 -> Box-Muller cosine
- * branch for N(0, sigma_sm); word 3 unused. */
+/* The per-bin draws of Eq. 4 and 5, key = seed.  Additive term: Rayleigh(sigma_sa)
+ * by inversion of word (bin mod 4) of counter (bin / 4, frame lo, 1, frame hi),
+ * so four neighbouring bins share one block of the stream.  Multiplicative term:
+ * N(0, sigma_sm) by the Box-Muller cosine branch of words 1, 2 of counter (bin,
+ * frame lo, 0, frame hi); its words 0 and 3 are unused.  Counter word 2 tells
+ * the two streams apart. */
 static void bin_draws(uint64_t bin, uint64_t seed, uint64_t frame, double sigma_sa,
                       double sigma_sm, double* w_sa, double* w_sm)
 {
-    const uint32_t ctr[4] = {(uint32_t)bin, (uint32_t)frame, 0u, (uint32_t)(frame >> 32)};
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t x[4];
-    oracle_philox4x32_10(ctr, key, x);
-    *w_sa = sigma_sa * sqrt(-2.0 * log(u01(x[0])));
-    *w_sm = sigma_sm * sqrt(-2.0 * log(u01(x[1]))) * cos(2.0 * M_PI * u01(x[2]));
+    const uint32_t ca[4] = {(uint32_t)(bin >> 2), (uint32_t)frame, 1u, (uint32_t)(frame >> 32)};
+    const uint32_t cm[4] = {(uint32_t)bin, (uint32_t)frame, 0u, (uint32_t)(frame >> 32)};
+    uint32_t xa[4], xm[4];
+    oracle_philox4x32_10(ca, key, xa);
+    oracle_philox4x32_10(cm, key, xm);
+    *w_sa = sigma_sa * sqrt(-2.0 * log(u01(xa[bin & 3u])));
+    *w_sm = sigma_sm * sqrt(-2.0 * log(u01(xm[1]))) * cos(2.0 * M_PI * u01(xm[2]));
 }
 
 void oracle_noise_draws(int64_t n_bins, uint64_t seed, uint64_t frame, double sigma_sa,

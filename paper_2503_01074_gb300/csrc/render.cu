@@ -51,7 +51,7 @@ __device__ __forceinline__ void load_unit(const BinArgs& a, int u, SensorDev* S,
 // shared-memory atomics); then Eq. 3-6 noise per bin and I~ to HBM.
 template <int DET>
 __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
-    extern __shared__ float acc[];
+    extern __shared__ __align__(16) float acc[];
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
     __shared__ Unit U;
@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
             }
         }
         __syncthreads();
-        // Eq. 3-6 per bin.  Pass 1 visits every bin: Philox words, the additive
-        // Rayleigh term, and the final value of bins without returns (P = 0 makes
+        // Eq. 3-6 per bin.  Pass 1 visits every bin: the additive Rayleigh term,
+        // which is already the final value of a bin without returns (P = 0 makes
         // the multiplicative term exactly 0); bins with returns are listed.  Pass 2
         // finishes the listed bins with the Gaussian multiplicative term.  (row,
         // col) advance incrementally: no division and no integer-to-float
@@ -213,53 +213,108 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         }
         if (tid == 0) s_count = 0;
         __syncthreads();
-        const int drow = nt / cw, dcol = nt - drow * cw;
-        int row = tid / cw, col = tid - row * cw;
         const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
         // the sensor fields this loop reads, in registers (the loop's shared-memory
         // stores would otherwise make the compiler reload them every bin)
         const uint32_t naz_r = (uint32_t)S.naz, c0_r = (uint32_t)U.c0, flo = S.frame_lo, fhi = S.frame_hi;
         const float rmin_r = S.rmin;
         float* const noised_r = a.noised + S.polar_off;
-        for (int k = tid; k < nbin; k += nt) {
-            const uint32_t b = (uint32_t)row * naz_r + c0_r + (uint32_t)col;
-            float P;
-            if (per_beam) {
-                P = 0.0f;
-                for (int bb = s_b0[col]; bb < s_b0[col + 1]; ++bb) P += accb[bb * S.nr + row];
-            } else {
-                P = acc[k];
+        float* const binned_r = a.binned ? a.binned + S.polar_off : nullptr;
+        // Pass 1 writes every bin's additive term to I~ (pass 2 adds the
+        // multiplicative term of the listed bins to it).  When the unit's bins
+        // come in aligned fours (row width, first column and unit width multiples
+        // of 4) a thread takes four neighbouring bins: one Philox block gives
+        // their four additive draws, and they move as 16-byte vectors.
+        if (((naz_r | c0_r | (uint32_t)cw) & 3u) == 0) {
+            const int cq = cw >> 2, nquad = S.nr * cq;
+            const int dqr = nt / cq, dqc = nt - dqr * cq;
+            int row = tid / cq, qc = tid - row * cq;
+            const bool vec = ((reinterpret_cast<uintptr_t>(noised_r) |
+                               reinterpret_cast<uintptr_t>(binned_r)) & 15u) == 0;
+            for (int g = tid; g < nquad; g += nt) {
+                const int k0 = row * cw + 4 * qc;
+                const uint32_t b0 = (uint32_t)row * naz_r + c0_r + 4u * (uint32_t)qc;
+                float P[4];
+                if (per_beam) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        P[j] = 0.0f;
+                        for (int bb = s_b0[4 * qc + j]; bb < s_b0[4 * qc + j + 1]; ++bb) P[j] += accb[bb * S.nr + row];
+                    }
+                } else {
+                    const float4 v = *reinterpret_cast<const float4*>(acc + k0);
+                    P[0] = v.x; P[1] = v.y; P[2] = v.z; P[3] = v.w;
+                }
+                const U4 x = additive_words(b0 >> 2, flo, fhi, K);
+                const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+                const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin_r);
+                float add[4], keep[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float w_sa = rayleigh_of(xw[j], sig_sa);
+                    add[j] = rc * rc * inv_rmax2 * (1.0f + s_pat[4 * qc + j] * w_sa);
+                    keep[j] = add[j];
+                    if (P[j] != 0.0f) {
+                        keep[j] = P[j];
+                        list[atomicAdd(&s_count, 1)] = k0 + j;
+                    }
+                }
+                if (vec) {
+                    *reinterpret_cast<float4*>(noised_r + b0) = make_float4(add[0], add[1], add[2], add[3]);
+                    if (binned_r) *reinterpret_cast<float4*>(binned_r + b0) = make_float4(P[0], P[1], P[2], P[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        noised_r[b0 + j] = add[j];
+                        if (binned_r) binned_r[b0 + j] = P[j];
+                    }
+                }
+                *reinterpret_cast<float4*>(acc + k0) = make_float4(keep[0], keep[1], keep[2], keep[3]);
+                row += dqr;
+                qc += dqc;
+                if (qc >= cq) { qc -= cq; ++row; }
             }
-            const U4 x = philox10(U4{b, flo, 0u, fhi}, K);   // bin_draws with the frame words held
-            const float w_sa = rayleigh_of(x, sig_sa);
-            const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin_r);
-            const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
-            if (a.binned) a.binned[S.polar_off + b] = P;
-            if (P != 0.0f) {
-                acc[k] = P;
-                list[atomicAdd(&s_count, 1)] = k;
-            } else {
+        } else {
+            const int drow = nt / cw, dcol = nt - drow * cw;
+            int row = tid / cw, col = tid - row * cw;
+            for (int k = tid; k < nbin; k += nt) {
+                const uint32_t b = (uint32_t)row * naz_r + c0_r + (uint32_t)col;
+                float P;
+                if (per_beam) {
+                    P = 0.0f;
+                    for (int bb = s_b0[col]; bb < s_b0[col + 1]; ++bb) P += accb[bb * S.nr + row];
+                } else {
+                    P = acc[k];
+                }
+                const U4 x = additive_words(b >> 2, flo, fhi, K);
+                const float w_sa = rayleigh_of(word_of(x, b & 3u), sig_sa);
+                const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin_r);
+                const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
+                if (binned_r) binned_r[b] = P;
                 noised_r[b] = additive;
-                acc[k] = additive;
+                if (P != 0.0f) {
+                    acc[k] = P;
+                    list[atomicAdd(&s_count, 1)] = k;
+                } else {
+                    acc[k] = additive;
+                }
+                row += drow;
+                col += dcol;
+                if (col >= cw) { col -= cw; ++row; }
             }
-            row += drow;
-            col += dcol;
-            if (col >= cw) { col -= cw; ++row; }
         }
         __syncthreads();
+        // Pass 2: the listed bins (P != 0) add P (0.5 + w_sm) to the additive
+        // term that pass 1 wrote (visible to the block after the barrier)
         const int nlist = s_count;
         for (int q = tid; q < nlist; q += nt) {
             const int k = list[q];
             const int rw = k / cw, cl = k - rw * cw;
             const uint32_t b = (uint32_t)(rw * S.naz + U.c0 + cl);
             const float P = acc[k];
-            const U4 x = bin_draws(b, S, K);
-            const float w_sa = rayleigh_of(x, sig_sa);
-            const float rc = fmaf(small_u2f(rw) + 0.5f, dr, S.rmin);
-            const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[cl] * w_sa);
-            const float w_sm = gauss_of(x, sig_sm);
-            const float In = P * (0.5f + w_sm) + additive;
-            a.noised[S.polar_off + b] = In;
+            const float w_sm = gauss_of(bin_draws(b, S, K), sig_sm);
+            const float In = P * (0.5f + w_sm) + noised_r[b];
+            noised_r[b] = In;
             acc[k] = In;
         }
         __syncthreads();

@@ -839,8 +839,32 @@ sonar_status batch_plan(sonar_batch* b) {
     }
     std::vector<int2> tmap, fmap;
     std::vector<int32_t> rmap;
+    // Ray-cast blocks in decreasing order of the upward component (world z) of
+    // their tile's central ray.  Over a seabed the rays closest to the horizon
+    // run farthest, so the longest blocks start first and the launch's tail is
+    // short (longest-processing-time-first); results do not depend on the order.
+    {
+        std::vector<std::pair<float, int64_t>> order;
+        for (int k = 0; k < n; ++k) {
+            const SensorDev& S = b->hs[k];
+            const int tb = S.tb, te = 32 / S.tb, tiles_b = (S.nb + tb - 1) / tb;
+            for (int t = 0; t < S.trace_blocks; ++t) {
+                const int ty = t / tiles_b, tx = t - ty * tiles_b;
+                const double i = std::min(tx * tb + 0.5 * tb, (double)S.nb);
+                const double j = std::min(ty * te + 0.5 * te, (double)S.ne);
+                const double phi = i * S.hfov / S.nb - 0.5 * S.hfov, th = j * S.vfov / S.ne - 0.5 * S.vfov;
+                const double up = S.rot[6] * std::sin(phi) * std::cos(th) + S.rot[7] * std::cos(phi) * std::cos(th) +
+                                  S.rot[8] * std::sin(th);
+                order.push_back({(float)-up, ((int64_t)k << 32) | (uint32_t)t});
+            }
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<float, int64_t>& x, const std::pair<float, int64_t>& y) {
+                             return x.first < y.first;
+                         });
+        for (const auto& q : order) tmap.push_back(make_int2((int)(q.second >> 32), (int)(q.second & 0xFFFFFFFF)));
+    }
     for (int k = 0; k < n; ++k) {
-        for (int t = 0; t < b->hs[k].trace_blocks; ++t) tmap.push_back(make_int2(k, t));
         if (b->lut_owner[k] < 0)   // sensors with a shared table are resampled by the grouped launch
             for (int t = 0; t < b->fan_prefix[k + 1] - b->fan_prefix[k]; ++t) fmap.push_back(make_int2(k, t));
         for (int r = 0; r < b->hs[k].nr; ++r) rmap.push_back(k);

@@ -168,14 +168,24 @@ __device__ __forceinline__ float neg2log_u(uint32_t x) {
 // sqrt(v) for v >= 0 from the reciprocal square root (a few ulp).
 __device__ __forceinline__ float sqrt_nonneg(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
 
-// Per-bin noise draws: counter (bin, frame lo, 0, frame hi), key = seed.
-// Word 0 -> Rayleigh(sigma_sa) by inversion; words 1, 2 -> the cosine branch
-// of Box-Muller for N(0, sigma_sm); word 3 unused.
+// The two noise streams of a frame (Eq. 4 and 5), key = seed.  Additive term:
+// Rayleigh(sigma_sa) by inversion of word (bin mod 4) of counter (bin / 4,
+// frame lo, 1, frame hi), so that four neighbouring bins share one Philox
+// block.  Multiplicative term: the cosine branch of Box-Muller for N(0,
+// sigma_sm) on words 1, 2 of counter (bin, frame lo, 0, frame hi) (words 0
+// and 3 unused).  Counter word 2 tells the streams apart.
+__device__ __forceinline__ U4 additive_words(uint32_t quad, uint32_t frame_lo, uint32_t frame_hi,
+                                             const PhiloxKey& K) {
+    return philox10(U4{quad, frame_lo, 1u, frame_hi}, K);
+}
 __device__ __forceinline__ U4 bin_draws(uint32_t bin, const SensorDev& s, const PhiloxKey& K) {
     return philox10(U4{bin, s.frame_lo, 0u, s.frame_hi}, K);
 }
-__device__ __forceinline__ float rayleigh_of(const U4& x, float sigma_sa) {
-    return sigma_sa * sqrt_nonneg(neg2log_u(x.x));
+__device__ __forceinline__ uint32_t word_of(const U4& x, uint32_t j) {
+    return j == 0 ? x.x : j == 1 ? x.y : j == 2 ? x.z : x.w;
+}
+__device__ __forceinline__ float rayleigh_of(uint32_t word, float sigma_sa) {
+    return sigma_sa * sqrt_nonneg(neg2log_u(word));
 }
 __device__ __forceinline__ float gauss_of(const U4& x, float sigma_sm) {
     const float u2 = fmaf((float)x.z, 0x1p-32f, 0x1p-32f);

@@ -8,7 +8,9 @@ I~ = (r_c^2 / r_max^2) (1 + 0.5 exp(-phi_c^2 / sigma_phi) w_sa), so w_sa is
 recovered from I~ bin by bin and compared with the oracle's FP64 draw from
 the same Philox word.  sigma_sa = 2^26 makes the w_sa term dominate the 1 it
 is added to, so FP32 rounding of I~ costs only a few units in the last place
-of w_sa, even for u within 2^-32 of 1.  The draws are grouped by their word:
+of w_sa, even for u within 2^-32 of 1.  Bin b draws word b mod 4 of the
+Philox block of counter (b / 4, frame lo, 1, frame hi).  The draws are grouped
+by their word:
 near 0 (u near 2^-32), near 2^32 - 1 (u near 1) and around 0xB504F333, where
 the kernel switches between its two forms of ln u.
 """
@@ -50,7 +52,6 @@ def test_rayleigh_log_against_fp64():
         pc = -H / 2 + (np.arange(naz) + 0.5) * H / naz
         c = (rc * rc / (rmax * rmax))[:, None]
         pat = (0.5 * np.exp(-pc * pc / prm.sigma_phi))[None, :]
-        bins = np.arange(nr * naz, dtype=np.uint64)
         key = np.array([SEED & 0xFFFFFFFF, SEED >> 32], np.uint32)
         groups = {"near 0": [], "near 2^32-1": [], "around 0xB504F333": [], "all": []}
         for frame in range(FRAMES):
@@ -58,10 +59,12 @@ def test_rayleigh_log_against_fp64():
             torch.cuda.synchronize()
             w_gpu = (In.double().cpu().numpy() / c - 1.0) / pat
             w_ref, _ = O.noise_draws(nr * naz, SEED, frame, SIGMA_SA, 0.0)
-            ctr = np.zeros((nr * naz, 4), np.uint32)
-            ctr[:, 0] = bins
+            # the additive draw of bin b: word b mod 4 of counter (b / 4, frame, 1, 0)
+            ctr = np.zeros((nr * naz // 4, 4), np.uint32)
+            ctr[:, 0] = np.arange(nr * naz // 4, dtype=np.uint32)
             ctr[:, 1] = frame
-            x = O.philox(ctr, key)[:, 0].astype(np.int64)
+            ctr[:, 2] = 1
+            x = O.philox(ctr, key).reshape(-1).astype(np.int64)
             # relative error, on a floor of w_sa = 1 (1.5e-8 sigma_sa): at w_sa = 0 the
             # recovery's own rounding of r_c^2 / r_max^2 leaves about 1e-6
             err = np.abs(w_gpu.ravel() - w_ref) / np.maximum(w_ref, 1.0)

@@ -73,6 +73,21 @@ def test_noise_draw_distributions():
     # different frame -> independent stream
     w2, _ = O.noise_draws(1000, seed=123, frame=5, sigma_sa=sa, sigma_sm=sm)
     assert abs(np.corrcoef(w_sa[:1000], w2)[0, 1]) < 0.15
+    # the additive and multiplicative draws of a bin are independent, and so are
+    # the four bins that share one Philox block of the additive stream
+    assert abs(np.corrcoef(w_sa, w_sm)[0, 1]) < 5 / math.sqrt(n)
+    q = w_sa.reshape(-1, 4)
+    for i in range(4):
+        for j in range(i + 1, 4):
+            assert abs(np.corrcoef(q[:, i], q[:, j])[0, 1]) < 5 / math.sqrt(n / 4)
+    # the additive draws are the Rayleigh inverse of the words of counters
+    # (bin / 4, frame lo, 1, frame hi), bin b taking word b mod 4
+    ctr = np.zeros((256, 4), np.uint32)
+    ctr[:, 0] = np.arange(256)
+    ctr[:, 1] = 4
+    ctr[:, 2] = 1
+    words = O.philox(ctr, np.array([123, 0], np.uint32)).reshape(-1).astype(np.float64)
+    assert np.allclose(w_sa[:1024], sa * np.sqrt(-2.0 * np.log((words + 1.0) / 2.0 ** 32)), rtol=1e-14, atol=0)
 
 
 # --------------------------------------------------------------------------
