@@ -839,10 +839,12 @@ sonar_status batch_plan(sonar_batch* b) {
     }
     std::vector<int2> tmap, fmap;
     std::vector<int32_t> rmap;
-    // Ray-cast blocks in decreasing order of the upward component (world z) of
-    // their tile's central ray.  Over a seabed the rays closest to the horizon
-    // run farthest, so the longest blocks start first and the launch's tail is
-    // short (longest-processing-time-first); results do not depend on the order.
+    // Ray-cast blocks in eight bands of decreasing upward component (world z) of
+    // their tile's central ray, sensor by sensor inside a band.  Over a seabed
+    // the rays closest to the horizon run farthest, so the longest blocks start
+    // first and the launch's tail is short (longest-processing-time-first); the
+    // bands keep a sensor's neighbouring tiles together, which share nodes in L2.
+    // Results do not depend on the order.
     {
         std::vector<std::pair<float, int64_t>> order;
         for (int k = 0; k < n; ++k) {
@@ -857,6 +859,14 @@ sonar_status batch_plan(sonar_batch* b) {
                                   S.rot[8] * std::sin(th);
                 order.push_back({(float)-up, ((int64_t)k << 32) | (uint32_t)t});
             }
+        }
+        if (!order.empty()) {
+            constexpr int kBands = 8;
+            float lo = order[0].first, hi = order[0].first;
+            for (const auto& q : order) { lo = std::min(lo, q.first); hi = std::max(hi, q.first); }
+            const float width = (hi - lo) / kBands;
+            for (auto& q : order)
+                q.first = width > 0.0f ? std::min((float)(kBands - 1), std::floor((q.first - lo) / width)) : 0.0f;
         }
         std::stable_sort(order.begin(), order.end(),
                          [](const std::pair<float, int64_t>& x, const std::pair<float, int64_t>& y) {
