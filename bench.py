@@ -764,6 +764,20 @@ def run_ours(args):
             "phase_frac": {k: bytes_frame[k] * B / (float(np.mean([q[k] for q in fwd_ph])) / 1e3) / 1e9 / peak
                            for k in ("trace", "bin_noise", "normalise_fan")}}
         extras["batched_fwd_fps"] = extras["batched_fwd"]["fps"]
+        # the same forward + adjoint as one graph (sonar_render_batch_step): the
+        # adjoint branch runs beside the normalisation and fan
+        st_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            e_f[0].record(stream)
+            batch.step(theta, prm, G, out=dtheta)
+            e_f[1].record(stream)
+            torch.cuda.synchronize()
+            st_ms.append(e_f[0].elapsed_time(e_f[1]))
+        sms = float(np.mean(st_ms))
+        extras["combined_step"] = {"fps": B / (sms / 1e3), "device_ms_per_step": sms,
+                                   "roofline": leg_roofline(fwd_bytes + adj_bytes, sms / B),
+                                   "graph_kernels": batch.kernels()}
         # the plain single-sensor path: one sonar_render (and sonar_render_backward)
         # call per frame, no batching, no graph.  Host loop: the Python loop as a
         # caller runs it.  Device: the same calls queued behind a long sleep

@@ -292,17 +292,36 @@ sonar_status sonar_render_batch_backward(sonar_batch_t batch, const sonar_params
                                          const sonar_hit* d_hits, float* d_dtheta,
                                          void* stream);
 
+/* One step of forward and adjoint for a caller whose upstream gradient is known
+ * before the forward runs (a fixed target's sensitivity, a gradient image from
+ * the caller's own pipeline): renders like sonar_render_batch into `out`, and
+ * writes d_dtheta [2 + n_mat], the adjoint of d_grad_polar (packed like the
+ * polar output) through this forward's I~ and hit records (out->noised and
+ * out->hits, or the batch's scratch when NULL).  The adjoint needs I~ and the
+ * records only, so one CUDA graph runs it beside the normalisation and fan
+ * launches.  Results equal sonar_render_batch followed by
+ * sonar_render_batch_backward with the same arguments (bitwise).  Captured once
+ * per (params, theta, outputs, grad, dtheta) and replayed after. */
+sonar_status sonar_render_batch_step(sonar_batch_t batch, const sonar_params* params,
+                                     const float* d_theta, int32_t n_mat,
+                                     const sonar_batch_outputs* out, const float* d_grad_polar,
+                                     float* d_dtheta, void* stream);
+
 /* Plan statistics: out[0] work units, out[1] total rays, out[2] persistent
  * grid size, out[3] block size, out[4] graphs captured so far. */
 sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
 
 /* Kernel launches per replay: out[0] kernel nodes of the current forward
  * graph, out[1] of the current adjoint graph (0 for a graph not captured yet;
- * -1 if the graph could not be inspected).  Host only, no synchronisation. */
+ * -1 if the graph could not be inspected); the step graph of
+ * sonar_render_batch_step holds the kernels of both.  Host only, no
+ * synchronisation. */
 sonar_status sonar_batch_kernels(sonar_batch_t batch, int32_t out[2]);
 
 /* Device durations, in milliseconds, of the phases of the most recent
- * sonar_render_batch and sonar_render_batch_backward replays, measured by CUDA
+ * sonar_render_batch and sonar_render_batch_backward replays (or of both
+ * branches of a sonar_render_batch_step replay, where ms[3] and ms[4] overlap
+ * ms[2]), measured by CUDA
  * events captured inside their graphs: ms[0] the ray-cast launch, ms[1] the
  * binning/noise launch, ms[2] the normalisation and fan launches, ms[3] the
  * adjoint row-term launch, ms[4] the adjoint gather and final-reduction

@@ -606,12 +606,14 @@ struct sonar_batch {
     int stage_next = 0;
     // graphs
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t fwd = nullptr, bwd = nullptr;
+    cudaStream_t side = nullptr;      // the adjoint branch of the combined step graph
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaGraphExec_t fwd = nullptr, bwd = nullptr, step = nullptr;
     cudaEvent_t ev[7] = {};           // phase boundaries recorded inside the graphs
     bool ran_fwd = false, ran_bwd = false;
-    std::vector<unsigned char> fwd_key, bwd_key;
+    std::vector<unsigned char> fwd_key, bwd_key, step_key;
     int graphs = 0;
-    int fwd_kernels = 0, bwd_kernels = 0;   // kernel nodes of the current graphs
+    int fwd_kernels = 0, bwd_kernels = 0, step_kernels = 0;   // kernel nodes of the current graphs
 };
 
 namespace {
@@ -645,9 +647,11 @@ void batch_free_device(sonar_batch* b) {
     b->d_counters = nullptr;
     if (b->fwd) cudaGraphExecDestroy(b->fwd);
     if (b->bwd) cudaGraphExecDestroy(b->bwd);
-    b->fwd = b->bwd = nullptr;
+    if (b->step) cudaGraphExecDestroy(b->step);
+    b->fwd = b->bwd = b->step = nullptr;
     b->fwd_key.clear();
     b->bwd_key.clear();
+    b->step_key.clear();
 }
 
 // Fan pixels sample the same bins with the same weights exactly when these agree.
@@ -960,48 +964,54 @@ void append_bytes(std::vector<unsigned char>& v, const T& x) {
     v.insert(v.end(), p, p + sizeof(T));
 }
 
+// The forward's launches: part 1 up to binning (trig tables, ray cast, binning
+// and noise), part 2 the normalisation and fan, part 0 both.
 sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
-                                    const sonar_batch_outputs* out, cudaStream_t s, bool events = false) {
+                                    const sonar_batch_outputs* out, cudaStream_t s, bool events = false,
+                                    int part = 0) {
     sonar_ctx* ctx = b->ctx;
     const int det = p->accumulate == 0;
-    CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
-    if (p->normalise == 2)
-        CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
-    sonar_hit* hits = out->hits ? out->hits : b->d_hits;   // scratch allocated by the caller, outside capture
-    if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
-    CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
-    TraceArgs t{};
-    t.sensors = b->d_sens;
-    t.scenes = b->d_scenes;
-    t.block_map = b->d_trace_map;
-    t.n_sensors = (int32_t)b->items.size();
-    t.params = *p;
-    t.hits = hits;
-    t.err = ctx->d_err;
-    CU(launch_trace(t, b->trace_prefix.back(), b->trace_occ, s), "batch trace launch");
-    if (events) CU(cudaEventRecordWithFlags(b->ev[6], s, cudaEventRecordExternal), "cudaEventRecord");
-    BinArgs a{};
-    a.sensors = b->d_sens;
-    a.units = b->d_units;
-    a.scenes = b->d_scenes;
-    a.work_counter = b->d_counters;
-    a.n_units = (int32_t)b->units.size();
-    a.n_mat = n_mat;
-    a.theta = d_theta;
-    a.params = *p;
-    a.noised = out->noised ? out->noised : b->d_noised;
-    a.binned = out->binned;
-    a.hits = hits;
-    a.rowmax = b->d_rowmax;
-    a.err = ctx->d_err;
-    CU(launch_bin(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch binning launch");
-    if (events) CU(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal), "cudaEventRecord");
+    if (part != 2) {
+        CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+        if (p->normalise == 2)
+            CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
+        sonar_hit* hits = out->hits ? out->hits : b->d_hits;   // scratch allocated by the caller, outside capture
+        if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
+        CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
+        TraceArgs t{};
+        t.sensors = b->d_sens;
+        t.scenes = b->d_scenes;
+        t.block_map = b->d_trace_map;
+        t.n_sensors = (int32_t)b->items.size();
+        t.params = *p;
+        t.hits = hits;
+        t.err = ctx->d_err;
+        CU(launch_trace(t, b->trace_prefix.back(), b->trace_occ, s), "batch trace launch");
+        if (events) CU(cudaEventRecordWithFlags(b->ev[6], s, cudaEventRecordExternal), "cudaEventRecord");
+        BinArgs a{};
+        a.sensors = b->d_sens;
+        a.units = b->d_units;
+        a.scenes = b->d_scenes;
+        a.work_counter = b->d_counters;
+        a.n_units = (int32_t)b->units.size();
+        a.n_mat = n_mat;
+        a.theta = d_theta;
+        a.params = *p;
+        a.noised = out->noised ? out->noised : b->d_noised;
+        a.binned = out->binned;
+        a.hits = hits;
+        a.rowmax = b->d_rowmax;
+        a.err = ctx->d_err;
+        CU(launch_bin(a, det, persistent_grid(b, det), b->block, b->smem1, s), "batch binning launch");
+        if (events) CU(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal), "cudaEventRecord");
+    }
+    if (part == 1) return SONAR_OK;
     NormArgs c{};
     c.sensors = b->d_sens;
     c.row_map = b->d_row_map;
     c.n_sensors = (int32_t)b->items.size();
     c.total_rows = b->total_rows;
-    c.noised = a.noised;
+    c.noised = out->noised ? out->noised : b->d_noised;
     c.gmax = b->d_rowmax;
     c.normalise = p->normalise;
     c.polar = out->polar;
@@ -1046,6 +1056,9 @@ extern "C" sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_it
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming);
     }
     if (st == SONAR_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (st == SONAR_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (st == SONAR_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    if (st == SONAR_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming);
     for (int k = 0; k < 7 && st == SONAR_OK && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     if (st == SONAR_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "batch staging");
     if (st != SONAR_OK) {
@@ -1263,6 +1276,79 @@ extern "C" sonar_status sonar_render_batch_backward(sonar_batch_t b, const sonar
     return SONAR_OK;
 }
 
+extern "C" sonar_status sonar_render_batch_step(sonar_batch_t b, const sonar_params* p, const float* d_theta,
+                                                int32_t n_mat, const sonar_batch_outputs* out, const float* d_grad,
+                                                float* d_dtheta, void* stream) {
+    if (!b) return SONAR_ERR_ARG;
+    sonar_ctx* ctx = b->ctx;
+    sonar_status st = check_params(ctx, p);
+    if (st) return st;
+    if (!d_theta || !out || !out->polar || !d_grad || !d_dtheta)
+        return fail(ctx, SONAR_ERR_ARG, "NULL theta, outputs, grad or dtheta");
+    if (out->hits && !aligned16(out->hits)) return fail(ctx, SONAR_ERR_ARG, "hits must be 16-byte aligned");
+    for (const sonar_batch_item& it : b->items)
+        if ((st = check_scene(ctx, it.scene_id)) || (st = check_nmat(ctx, it.scene_id, n_mat))) return st;
+    CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CU(batch_scratch(b, out), "batch scratch");
+    if (!out->hits && !b->d_hits)   // the adjoint reads the records the forward writes
+        CU(cudaMalloc(&b->d_hits, sizeof(sonar_hit) * std::max<int64_t>(1, b->total_rays)), "batch scratch");
+    if (n_mat > b->n_mat_cap) {
+        if (b->d_partials) cudaFree(b->d_partials);
+        b->d_partials = nullptr;
+        CU(cudaMalloc(&b->d_partials, sizeof(double) * b->adj_units.size() * (n_mat + 2)), "batch scratch");
+        b->n_mat_cap = n_mat;
+        if (b->bwd) cudaGraphExecDestroy(b->bwd);
+        if (b->step) cudaGraphExecDestroy(b->step);
+        b->bwd = b->step = nullptr;
+    }
+    std::vector<unsigned char> key;
+    append_bytes(key, *p);
+    append_bytes(key, d_theta);
+    append_bytes(key, n_mat);
+    append_bytes(key, *out);
+    append_bytes(key, d_grad);
+    append_bytes(key, d_dtheta);
+    if (!b->step || key != b->step_key) {
+        if (b->step) cudaGraphExecDestroy(b->step);
+        b->step = nullptr;
+        const float* noised = out->noised ? out->noised : b->d_noised;
+        const sonar_hit* hits = out->hits ? out->hits : b->d_hits;
+        // one graph, two branches after binning: the adjoint (which reads I~ and
+        // the hit records only) beside the normalisation and the fan
+        CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+        st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap, true, 1);
+        cudaError_t e = cudaSuccess;
+        bool forked = false;
+        if (st == SONAR_OK) {
+            e = cudaEventRecord(b->fork_ev, b->cap);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork_ev, 0);
+            forked = e == cudaSuccess;
+        }
+        if (st == SONAR_OK && forked)
+            st = batch_backward_launches(b, p, d_theta, n_mat, d_grad, noised, hits, d_dtheta, b->side, true);
+        if (st == SONAR_OK && forked) st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap, true, 2);
+        if (forked) {   // join the branch whatever happened, so that the capture can end
+            const cudaError_t e1 = cudaEventRecord(b->join_ev, b->side);
+            const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(b->cap, b->join_ev, 0) : e1;
+            if (e == cudaSuccess) e = e2;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
+        if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(ctx, e, "graph fork"); }
+        CU(e3, "graph capture");
+        b->step_kernels = kernel_nodes(g);
+        const cudaError_t e4 = cudaGraphInstantiate(&b->step, g, 0);
+        cudaGraphDestroy(g);
+        CU(e4, "graph instantiation");
+        b->step_key = key;
+        ++b->graphs;
+    }
+    CU(cudaGraphLaunch(b->step, (cudaStream_t)stream), "graph launch");
+    b->ran_fwd = b->ran_bwd = true;
+    return SONAR_OK;
+}
+
 extern "C" sonar_status sonar_batch_info(sonar_batch_t b, int64_t out[5]) {
     if (!b || !out) return SONAR_ERR_ARG;
     int64_t rays = 0;
@@ -1314,6 +1400,9 @@ extern "C" sonar_status sonar_batch_destroy(sonar_batch_t b) {
         if (b->stage_ev[k]) cudaEventDestroy(b->stage_ev[k]);
     }
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->join_ev) cudaEventDestroy(b->join_ev);
     delete b;
     return SONAR_OK;
 }

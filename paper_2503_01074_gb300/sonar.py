@@ -101,6 +101,8 @@ _SIG = {
     "sonar_render_batch_backward": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_int32,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p]),
+    "sonar_render_batch_step": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_int32,
+                                          C.POINTER(BatchOutputs), C.c_void_p, C.c_void_p, C.c_void_p]),
     "sonar_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "sonar_batch_kernels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "sonar_batch_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
@@ -485,6 +487,17 @@ class Batch:
         self.sonar._check(self.lib.sonar_render_batch_backward(
             self.h, C.byref(prm), _ptr(theta), theta.shape[0] - 2, _ptr(grad_polar), _ptr(self.noised),
             _ptr(self.hits) if hits else None, _ptr(d), _stream(stream)))
+        return d
+
+    def step(self, theta, params: RenderParams, grad_polar, hits=True, fan=True, stream=None, out=None):
+        """Forward into the batch's buffers and the adjoint of `grad_polar` in one
+        graph (sonar_render_batch_step); returns dtheta."""
+        t = self.sonar.torch
+        d = t.empty_like(theta) if out is None else out
+        o = self.outputs(hits, fan)
+        prm = params.c()
+        self.sonar._check(self.lib.sonar_render_batch_step(self.h, C.byref(prm), _ptr(theta), theta.shape[0] - 2,
+                                                           C.byref(o), _ptr(grad_polar), _ptr(d), _stream(stream)))
         return d
 
     def autotune(self, theta, params: RenderParams = RenderParams(), stream=None, hits=True):

@@ -472,3 +472,35 @@ def test_batch_without_hit_buffers(son, tiny, tiny_sid):
     st, bits = son.check()
     assert st == 0 and bits == 0
     b.close()
+
+
+@pytest.mark.parametrize("normalise", [0, 1, 2])
+def test_batch_step_equals_separate_calls(son, tiny, tiny_sid, normalise):
+    """sonar_render_batch_step runs the adjoint as a branch beside the
+    normalisation and fan in one graph: its images, records and gradient
+    equal a forward call followed by an adjoint call, bit for bit, through
+    graph replays and with the records in the batch's own scratch."""
+    mesh, mu = tiny
+    items = batch_items(son, tiny, tiny_sid)
+    theta = son.theta(0.05, 1.0, np.concatenate([mu, [0.4, 0.6]]).astype(np.float32))
+    prm = RenderParams(normalise=normalise)
+    ref = son.batch(items)
+    stp = son.batch(items)
+    G = torch.randn(ref.n_polar, generator=torch.Generator().manual_seed(5)).to(son.device)
+    for hits in (True, False):
+        ref.render(theta, prm, hits=True, fan=True)
+        d_ref = ref.backward(theta, prm, G, hits=True).clone()
+        for rep in range(2):          # capture, then replay
+            d = stp.step(theta, prm, G, hits=hits).clone()
+            torch.cuda.synchronize()
+            assert torch.equal(d, d_ref), (hits, rep)
+            assert torch.equal(stp.polar, ref.polar) and torch.equal(stp.noised, ref.noised)
+            assert torch.equal(stp.fan, ref.fan)
+            if hits:
+                assert torch.equal(stp.hits, ref.hits)
+    t = stp.timings()
+    assert all(t[k] > 0 for k in ("trace", "bin_noise", "normalise_fan", "adjoint_gather"))
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+    ref.close()
+    stp.close()
