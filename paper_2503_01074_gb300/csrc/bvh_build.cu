@@ -561,9 +561,9 @@ __global__ void k_collapse_write(const int32_t* picks, const uint32_t* prefix, i
             hh[k] = c >= 0 ? (int32_t)(base_next + r++) : c;
         }
         float4* o = nodes + 2 * W * (base + e) + 8 * half;
-        for (int a = 0; a < 3; ++a) {
-            o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
-            o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+        for (int a = 0; a < 3; ++a) {   // per axis: (lo, hi) of children 0, 1 | 2, 3
+            o[2 * a] = make_float4(lo[a][0], hi[a][0], lo[a][1], hi[a][1]);
+            o[2 * a + 1] = make_float4(lo[a][2], hi[a][2], lo[a][3], hi[a][3]);
         }
         o[6] = make_float4(__int_as_float(hh[0]), __int_as_float(hh[1]), __int_as_float(hh[2]),
                            __int_as_float(hh[3]));

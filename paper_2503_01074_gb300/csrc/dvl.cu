@@ -68,9 +68,10 @@ __device__ float closest_distance(const SceneDev& sc, float3 o, float3 d, float 
         const float4 lz = __ldg(pn + 4), hz = __ldg(pn + 5);
         const int4 ch = __ldg(reinterpret_cast<const int4*>(pn + 6));
         const float tcut = best_t * 1.00002f;
-        const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
-        const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
+        // per axis, the (lo, hi) planes of children 0, 1 | 2, 3
+        const float lxs[4] = {lx.x, lx.z, hx.x, hx.z}, hxs[4] = {lx.y, lx.w, hx.y, hx.w};
+        const float lys[4] = {ly.x, ly.z, hy.x, hy.z}, hys[4] = {ly.y, ly.w, hy.y, hy.w};
+        const float lzs[4] = {lz.x, lz.z, hz.x, hz.z}, hzs[4] = {lz.y, lz.w, hz.y, hz.w};
         const int32_t hs[4] = {ch.x, ch.y, ch.z, ch.w};
         uint32_t key[4];
 #pragma unroll

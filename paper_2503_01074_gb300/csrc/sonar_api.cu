@@ -591,6 +591,7 @@ struct sonar_batch {
     int fan_blocks = 0;               // blocks of the per-sensor fan launch
     sonar_hit* d_hits = nullptr;      // hit records when the caller asks for none
     float4* d_trig = nullptr;         // per-sensor exact-ray tables
+    uint32_t* d_trig_stamp = nullptr; // per sensor and k_trig block: the version its entries were built for
     int max_angles = 0;
     uint32_t* d_rowmax = nullptr;
     float* d_noised = nullptr;
@@ -621,7 +622,7 @@ namespace {
 void batch_free_device(sonar_batch* b) {
     for (void* p : {(void*)b->d_sens, (void*)b->d_units, (void*)b->d_adj_units, (void*)b->d_scenes,
                     (void*)b->d_fan_prefix, (void*)b->d_trace_prefix, (void*)b->d_trace_map,
-                    (void*)b->d_fan_map, (void*)b->d_row_map, (void*)b->d_hits, (void*)b->d_trig,
+                    (void*)b->d_fan_map, (void*)b->d_row_map, (void*)b->d_hits, (void*)b->d_trig, (void*)b->d_trig_stamp,
                     (void*)b->d_rowmax,
                     (void*)b->d_noised, (void*)b->d_rowinfo, (void*)b->d_partials, (void*)b->d_counters,
                     (void*)b->d_fan_lut, (void*)b->d_luts, (void*)b->d_lut_map, (void*)b->d_group_map,
@@ -640,6 +641,7 @@ void batch_free_device(sonar_batch* b) {
     b->d_row_map = nullptr;
     b->d_hits = nullptr;
     b->d_trig = nullptr;
+    b->d_trig_stamp = nullptr;
     b->n_mat_cap = 0;
     b->d_sens = nullptr; b->d_units = nullptr; b->d_adj_units = nullptr; b->d_scenes = nullptr;
     b->d_fan_prefix = nullptr;
@@ -894,11 +896,19 @@ sonar_status batch_plan(sonar_batch* b) {
         b->max_angles = std::max(b->max_angles, S.nb + S.ne);
     }
     alloc((void**)&b->d_trig, sizeof(float4) * angles);
+    // per sensor, one stamp per k_trig block (grid x = ceil(max_angles / 128)):
+    // stamps 0 and versions 1, so every block builds its entries once
+    const int trig_gx = (b->max_angles + 127) / 128;
+    alloc((void**)&b->d_trig_stamp, sizeof(uint32_t) * std::max<int64_t>(1, (int64_t)n * trig_gx));
+    if (e == cudaSuccess) e = cudaMemset(b->d_trig_stamp, 0, sizeof(uint32_t) * std::max<int64_t>(1, (int64_t)n * trig_gx));
     if (e == cudaSuccess) {
         int64_t off = 0;
-        for (SensorDev& S : b->hs) {
+        for (int k = 0; k < n; ++k) {
+            SensorDev& S = b->hs[k];
             S.trig = b->d_trig + off;
             off += S.nb + S.ne;
+            S.trig_stamp = b->d_trig_stamp + (int64_t)k * trig_gx;
+            S.trig_version = 1;
         }
     }
     alloc((void**)&b->d_rowmax, sizeof(uint32_t) * rows);
@@ -1117,6 +1127,9 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
         S.scene = it.scene_id;
         // an owner's table is rebuilt (inside the graph) once its fan geometry changes
         if (S.fan_stamp && !same_fan_geometry(S, b->hs[k]) && ++S.fan_version == 0) S.fan_version = 1;   // 0: never built
+        // and the exact-ray tables once a field of view changes
+        if (S.trig_stamp && (S.hfov != b->hs[k].hfov || S.vfov != b->hs[k].vfov) && ++S.trig_version == 0)
+            S.trig_version = 1;
         b->hs[k] = S;
         b->items[k] = it;
     }

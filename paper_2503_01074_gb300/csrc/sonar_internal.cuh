@@ -1,10 +1,11 @@
 // Internal device-side definitions of libsonar (GB300, sm_103a).
 //
 // Data layout in HBM
-//   nodes       4-wide, float4[8] = 128 B (one cache line) per node, children in
-//               structure-of-arrays form: [0] lo.x of children 0..3, [1] hi.x,
-//               [2] lo.y, [3] hi.y, [4] lo.z, [5] hi.z, [6] the 4 child handles,
-//               [7] unused.  Empty slots: boxes at +inf (never entered), kEmpty.
+//   nodes       4-wide, float4[8] = 128 B (one cache line) per node, per axis
+//               two float4 of (lo, hi) plane pairs: [0] (lo.x, hi.x) of children
+//               0, 1, [1] of children 2, 3, [2], [3] the same for y, [4], [5] for
+//               z, [6] the 4 child handles, [7] unused.  Empty slots: boxes at +inf
+//               (never entered), kEmpty.
 //   nodes8      8-wide, float4[16] = 256 B per node: two halves in the 4-wide
 //               layout, children 0..3 and 4..7.  Built from the same binary
 //               hierarchy; a handle >= 0 here indexes nodes8.
@@ -68,6 +69,8 @@ struct SensorDev {
     int64_t polar_off, hits_off, fan_off, rowmax_off;
     float4* trig;        // float-float sin/cos of the beam azimuths [nb] and elevations [ne]
     uint4* fan_lut;      // per-pixel fan coordinates shared with same-geometry sensors (nullptr: compute)
+    uint32_t* trig_stamp;  // batch: per k_trig block, the trig_version its table entries were built for
+    uint32_t trig_version; // batch: bumped whenever an update changes the fields of view
     uint32_t* fan_stamp;   // table owners: per table block, the fan_version it was last built for
     uint32_t fan_version;  // table owners: bumped whenever an update changes the fan geometry
     uint32_t pad_;

@@ -110,6 +110,10 @@ __device__ __noinline__ bool exact_closer(const SensorDev& s, int i, int j, cons
 // beams, trig[N_b + j] for elevations, each (sin hi, sin lo, cos hi, cos lo).
 __global__ void k_trig(const SensorDev* sensors, SensorDev one) {
     const SensorDev& s = sensors ? sensors[blockIdx.y] : one;
+    // a batch block whose entries were built for the sensor's current fields of
+    // view has nothing to do (block-uniform; only later launches read the table)
+    if (s.trig_stamp && s.trig_stamp[blockIdx.x] == s.trig_version) return;
+    if (s.trig_stamp && threadIdx.x == 0) s.trig_stamp[blockIdx.x] = s.trig_version;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.nb + s.ne) return;
     double a;
@@ -145,6 +149,19 @@ __device__ __forceinline__ int az_bin(const SensorDev& s, int i) {
 // trace: one ray per thread, hit record out
 // ---------------------------------------------------------------------------
 
+// A float twice, as the packed pair operand of fma.rn.f32x2.
+__device__ __forceinline__ unsigned long long pk2(float v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+    return r;
+}
+// (d0, d1) = (a0, a1) * b + c element by element in one packed FP32 FMA
+// (sm_100 and later), each element rounded exactly like fmaf
+__device__ __forceinline__ void fma2(float a0, float a1, unsigned long long b, unsigned long long c, float& d0,
+                                     float& d1) {
+    asm("{\n\t.reg .b64 ra, rd;\n\tmov.b64 ra, {%2, %3};\n\tfma.rn.f32x2 rd, ra, %4, %5;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1) : "f"(a0), "f"(a1), "l"(b), "l"(c));
+}
 // Sorts W child keys ascending in registers: a 5-comparator network for 4,
 // Batcher's odd-even merge sort (19 comparators) for 8.
 template <int W>
@@ -233,6 +250,9 @@ __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
                           1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
                           1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
     const float3 oinv = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    // (inv, inv) and (-o inv, -o inv) per axis as packed pairs for the box tests
+    const unsigned long long ivx = pk2(inv.x), ivy = pk2(inv.y), ivz = pk2(inv.z);
+    const unsigned long long novx = pk2(-oinv.x), novy = pk2(-oinv.y), novz = pk2(-oinv.z);
     int32_t stack[kStackMax];
     int sp = 0, best = -1;
     uint32_t best_id = 0xFFFFFFFFu;
@@ -268,16 +288,18 @@ __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
                     hs[4 * half + 1] = __float_as_int(chf.y);
                     hs[4 * half + 2] = __float_as_int(chf.z);
                     hs[4 * half + 3] = __float_as_int(chf.w);
-                    const float lxs[4] = {lx.x, lx.y, lx.z, lx.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
-                    const float lys[4] = {ly.x, ly.y, ly.z, ly.w}, hys[4] = {hy.x, hy.y, hy.z, hy.w};
-                    const float lzs[4] = {lz.x, lz.y, lz.z, lz.w}, hzs[4] = {hz.x, hz.y, hz.z, hz.w};
+                    // per axis, the (lo, hi) planes of children 0, 1 | 2, 3
+                    const float lxs[4] = {lx.x, lx.z, hx.x, hx.z}, hxs[4] = {lx.y, lx.w, hx.y, hx.w};
+                    const float lys[4] = {ly.x, ly.z, hy.x, hy.z}, hys[4] = {ly.y, ly.w, hy.y, hy.w};
+                    const float lzs[4] = {lz.x, lz.z, hz.x, hz.z}, hzs[4] = {lz.y, lz.w, hz.y, hz.w};
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        float t0 = fmaf(lxs[c], inv.x, -oinv.x), t1 = fmaf(hxs[c], inv.x, -oinv.x);
+                        float t0, t1;
+                        fma2(lxs[c], hxs[c], ivx, novx, t0, t1);
                         float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-                        t0 = fmaf(lys[c], inv.y, -oinv.y); t1 = fmaf(hys[c], inv.y, -oinv.y);
+                        fma2(lys[c], hys[c], ivy, novy, t0, t1);
                         lo = fmaxf(lo, fminf(t0, t1)); hi = fminf(hi, fmaxf(t0, t1));
-                        t0 = fmaf(lzs[c], inv.z, -oinv.z); t1 = fmaf(hzs[c], inv.z, -oinv.z);
+                        fma2(lzs[c], hzs[c], ivz, novz, t0, t1);
                         lo = fmaxf(fmaxf(lo, fminf(t0, t1)), 0.0f); hi = fminf(fminf(hi, fmaxf(t0, t1)), tcut);
                         // an empty slot's box lies at +inf on every axis: along an axis
                         // the ray travels in the + direction its entry distance is +inf,
