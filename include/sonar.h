@@ -22,11 +22,15 @@
  *    that stream has reached the call.  No call aborts, traps or prints.
  *  - Argument errors are detected on the host before anything is enqueued and
  *    return SONAR_ERR_ARG; sonar_last_error() then holds a message.
- *  - Kernels that detect a fault (a traversal stack overflow, a wait that
- *    timed out, an index out of range) set a sticky device error word instead
- *    of trapping; sonar_check(ctx) synchronises and reports it as
- *    SONAR_ERR_DEVICE, then clears it.
- *  - A context is used by one host thread at a time.
+ *  - Kernels that detect a fault (a traversal stack overflow, an index out of
+ *    range) set a sticky device error word instead of trapping;
+ *    sonar_check(ctx) synchronises and reports it as SONAR_ERR_DEVICE, then
+ *    clears it.
+ *  - A context is used by one host thread at a time, and its calls are
+ *    stream-ordered: the context's own scratch (outputs passed as NULL, the
+ *    single-sensor calls' exact-ray tables, which are rebuilt only when the
+ *    angular geometry changes) is reused from call to call, so calls on
+ *    different streams need the caller's synchronisation between them.
  *
  * World frame: z up.  Sensor frame: +y forward, +x right, +z up.  Ray (i, j)
  * of beam i in [0, n_beams) and elevation j in [0, n_elev) has azimuth

@@ -46,6 +46,11 @@ struct sonar_ctx {
     std::string last_error;
     uint32_t* d_err = nullptr;
     Scratch rowmax, noised, rowinfo, partials, counters, hits, trig;
+    // the exact-ray tables last built by a single-sensor call: their buffer and
+    // the angular geometry they hold (beams, elevations, fields of view)
+    const float4* trig_at = nullptr;
+    int trig_nb = 0, trig_ne = 0;
+    float trig_hfov = 0.0f, trig_vfov = 0.0f;
     std::map<ShapeKey, Tune> tune;
 };
 
@@ -369,12 +374,43 @@ size_t bin_smem(const SensorDev& s) {
     return (size_t)(bins + beams + std::min<int64_t>(unit_rays_max(s), bins)) * sizeof(float);
 }
 
+// The context's exact-ray table buffer, grown to `entries`; a new buffer holds
+// no tables yet.
+cudaError_t grow_trig(sonar_ctx* ctx, size_t entries, cudaStream_t s) {
+    const void* before = ctx->trig.p;
+    const cudaError_t e = grow(ctx->trig, sizeof(float4) * entries, s);
+    if (e != cudaSuccess || ctx->trig.p != before || ctx->trig.bytes < sizeof(float4) * entries) ctx->trig_at = nullptr;
+    return e;
+}
+
+// The exact-ray tables of one sensor's call.  They depend on the angular
+// geometry only, so a call with the same geometry and table buffer as the last
+// build skips the launch (calls on a context are stream-ordered); while the
+// stream is being captured into a graph the launch is always recorded, so that
+// a replay rebuilds the tables it reads.
+cudaError_t single_trig(sonar_ctx* ctx, const SensorDev& S, cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusNone && ctx->trig_at == S.trig && ctx->trig_nb == S.nb && ctx->trig_ne == S.ne &&
+        ctx->trig_hfov == S.hfov && ctx->trig_vfov == S.vfov)
+        return cudaSuccess;
+    e = launch_trig(nullptr, S, 1, S.nb + S.ne, s);
+    const bool keep = e == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+    ctx->trig_at = keep ? S.trig : nullptr;
+    ctx->trig_nb = S.nb;
+    ctx->trig_ne = S.ne;
+    ctx->trig_hfov = S.hfov;
+    ctx->trig_vfov = S.vfov;
+    return e;
+}
+
 // Trace, bin and noise of one sensor (polar_off = hits_off = rowmax_off = 0).
 sonar_status single_forward(sonar_ctx* ctx, const SensorDev& S, const SceneDev& sc, const sonar_params* p,
                             const float* d_theta, int32_t n_mat, sonar_hit* hits, float* noised, float* binned,
                             uint32_t* gmax, int block, cudaStream_t s) {
     if (p->normalise == 2) CU(cudaMemsetAsync(gmax, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
-    CU(launch_trig(nullptr, S, 1, S.nb + S.ne, s), "trig launch");
+    CU(single_trig(ctx, S, s), "trig launch");
     TraceArgs t{};
     t.one = S;
     t.one_scene = sc;
@@ -460,7 +496,7 @@ extern "C" sonar_status sonar_render(sonar_ctx_t ctx, int32_t scene_id, const so
         CU(grow(ctx->hits, sizeof(sonar_hit) * (size_t)S.nb * S.ne, s), "scratch allocation");
         hits = (sonar_hit*)ctx->hits.p;
     }
-    CU(grow(ctx->trig, sizeof(float4) * (size_t)(S.nb + S.ne), s), "scratch allocation");
+    CU(grow_trig(ctx, (size_t)(S.nb + S.ne), s), "scratch allocation");
     S.trig = (float4*)ctx->trig.p;
     sonar_status st2 = single_forward(ctx, S, scene_dev(ctx->scenes[scene_id]), params, d_theta, n_mat, hits, noised,
                                       out->binned, (uint32_t*)ctx->rowmax.p, t.block, s);
@@ -509,11 +545,11 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     CU(grow(ctx->rowinfo, sizeof(RowInfo) * groups, s), "scratch allocation");
     const sonar_hit* hits = d_hits;
     if (!hits) {   // recompute the hit records with the ray-cast kernel (bitwise the forward's)
-        CU(grow(ctx->trig, sizeof(float4) * (size_t)(S.nb + S.ne), s), "scratch allocation");
+        CU(grow_trig(ctx, (size_t)(S.nb + S.ne), s), "scratch allocation");
         CU(grow(ctx->hits, sizeof(sonar_hit) * (size_t)S.nb * S.ne, s), "scratch allocation");
         S.trig = (float4*)ctx->trig.p;
         S.occ = single_variant(ctx, *sensor, S.tb, S.occ);
-        CU(launch_trig(nullptr, S, 1, S.nb + S.ne, s), "trig launch");
+        CU(single_trig(ctx, S, s), "trig launch");
         TraceArgs tr{};
         tr.one = S;
         tr.one_scene = scene_dev(ctx->scenes[scene_id]);
