@@ -49,6 +49,19 @@ __device__ __forceinline__ void load_unit(const BinArgs& a, int u, SensorDev* S,
 // block (DET: in canonical ray order, warps taking turns and each group of
 // equal bins folded by its leader in lane order; otherwise warp-aggregated
 // shared-memory atomics); then Eq. 3-6 noise per bin and I~ to HBM.
+// The additive term of Eq. 3 for range row `row` (centre r_c) and a column
+// whose beam-pattern factor 0.5 exp(-phi_c^2 / sigma_phi) is `pat`, from the
+// bin's uniform word of the additive stream: (r_c^2 / r_max^2)(1 + pat w_sa),
+// w_sa ~ Rayleigh(sigma_sa) (Eq. 4).
+struct AdditiveTerm {
+    float dr, rmin, inv_rmax2, sig_sa;
+    __device__ __forceinline__ float operator()(int row, float pat, uint32_t word) const {
+        const float w_sa = rayleigh_of(word, sig_sa);
+        const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin);
+        return rc * rc * inv_rmax2 * (1.0f + pat * w_sa);
+    }
+};
+
 template <int DET>
 __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
     extern __shared__ __align__(16) float acc[];
@@ -62,6 +75,7 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
+    int clean_nbin = -1;   // block-uniform: the unit size whose accumulator and bitmap are known zero
     for (int iter = 0;; ++iter) {
         int u;
         if (a.work_counter) {
@@ -89,6 +103,140 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         const bool per_beam = DET && S.fold_beams;
         float* accb = acc + nbin;
         int* list = reinterpret_cast<int*>(acc + nbin + (per_beam ? nbeam * S.nr : 0));
+        // the list of bins with returns holds one entry per ray at most (only a
+        // bin that a ray lands in can be nonzero): the host sizes it so
+        const int lcap = (int)min((int64_t)nbin, r1 - r0);
+        // Noise first: with at most one beam per column and no whole-image
+        // maximum, a bin's additive term does not depend on the fold, so pass 1
+        // writes it for every bin before the rays are folded (the fold's record
+        // loads then meet a busy block rather than a barrier); the fold lists each
+        // bin at its first return (a shared bitmap), and pass 2 finishes and
+        // resets only the listed bins, which leaves the accumulator and bitmap
+        // zero for the next unit of the same size.
+        if (DET && !per_beam && S.nb <= S.naz && a.params.normalise != 2) {
+            uint32_t* bits = reinterpret_cast<uint32_t*>(acc + nbin);
+            const int nwords = (nbin + 31) >> 5;
+            int* flist = reinterpret_cast<int*>(bits + nwords);
+            if (clean_nbin != nbin)
+                for (int k = tid; k < nbin + nwords; k += nt) acc[k] = 0.0f;   // bitmap words too (0.0f is 0)
+            const float dr = (S.rmax - S.rmin) / (float)S.nr, da = S.hfov / (float)S.naz;
+            const float inv_rmax2 = 1.0f / (S.rmax * S.rmax);
+            const float inv_sphi = 1.0f / a.params.sigma_phi;
+            const float sig_sa = a.params.sigma_sa, sig_sm = a.params.sigma_sm;
+            for (int c = tid; c < cw; c += nt) {
+                const float pc = fmaf(small_u2f(U.c0 + c) + 0.5f, da, -0.5f * S.hfov);
+                s_pat[c] = 0.5f * expf(-pc * pc * inv_sphi);
+            }
+            if (tid == 0) s_count = 0;
+            __syncthreads();
+            const PhiloxKey K = philox_key(S.seed_lo, S.seed_hi);
+            const uint32_t naz_r = (uint32_t)S.naz, c0_r = (uint32_t)U.c0, flo = S.frame_lo, fhi = S.frame_hi;
+            const float rmin_r = S.rmin;
+            const AdditiveTerm additive{dr, rmin_r, inv_rmax2, sig_sa};
+            float* const noised_r = a.noised + S.polar_off;
+            float* const binned_r = a.binned ? a.binned + S.polar_off : nullptr;
+            if (((naz_r | c0_r | (uint32_t)cw) & 3u) == 0) {
+                const int cq = cw >> 2, nquad = S.nr * cq;
+                const int dqr = nt / cq, dqc = nt - dqr * cq;
+                int row = tid / cq, qc = tid - row * cq;
+                const bool vec = ((reinterpret_cast<uintptr_t>(noised_r) |
+                                   reinterpret_cast<uintptr_t>(binned_r)) & 15u) == 0;
+                for (int g = tid; g < nquad; g += nt) {
+                    const uint32_t b0 = (uint32_t)row * naz_r + c0_r + 4u * (uint32_t)qc;
+                    const U4 x = additive_words(b0 >> 2, flo, fhi, K);
+                    const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+                    float add[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) add[j] = additive(row, s_pat[4 * qc + j], xw[j]);
+                    if (vec) {
+                        *reinterpret_cast<float4*>(noised_r + b0) = make_float4(add[0], add[1], add[2], add[3]);
+                        if (binned_r) *reinterpret_cast<float4*>(binned_r + b0) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            noised_r[b0 + j] = add[j];
+                            if (binned_r) binned_r[b0 + j] = 0.0f;
+                        }
+                    }
+                    row += dqr;
+                    qc += dqc;
+                    if (qc >= cq) { qc -= cq; ++row; }
+                }
+            } else {
+                const int drow = nt / cw, dcol = nt - drow * cw;
+                int row = tid / cw, col = tid - row * cw;
+                for (int k = tid; k < nbin; k += nt) {
+                    const uint32_t b = (uint32_t)row * naz_r + c0_r + (uint32_t)col;
+                    const U4 x = additive_words(b >> 2, flo, fhi, K);
+                    noised_r[b] = additive(row, s_pat[col], word_of(x, b & 3u));
+                    if (binned_r) binned_r[b] = 0.0f;
+                    row += drow;
+                    col += dcol;
+                    if (col >= cw) { col -= cw; ++row; }
+                }
+            }
+            // the fold: warp w takes beams w, w + nw, ... of the unit, each in
+            // elevation order (its column's canonical order)
+            for (int bb = warp; bb < nbeam; bb += nw) {
+                const sonar_hit* Hb = H + (int64_t)(i0 + bb) * S.ne;
+                for (int jb = 0; jb < S.ne; jb += 32) {
+                    const int j = jb + lane;
+                    uint32_t lkey = kNoKey;
+                    float score = 0.0f;
+                    if (j < S.ne) {
+                        const uint4 h = __ldg(reinterpret_cast<const uint4*>(Hb + j));
+                        if (h.x != kNoKey) {
+                            const uint32_t br = h.x / naz_r, ba = h.x - br * naz_r;
+                            lkey = br * (uint32_t)cw + (ba - c0_r);
+                            if (lkey >= (uint32_t)nbin || h.y >= (uint32_t)SC.n_tris) {   // not this unit's bin: a corrupt record
+                                atomicOr(a.err, SONAR_DEVERR_INDEX);
+                                lkey = kNoKey;
+                            }
+                            int m = lkey == kNoKey ? 0 : SC.mat_orig[h.y];
+                            m = m < a.n_mat ? m : a.n_mat - 1;
+                            score = __ldg(a.theta + 2 + m) * __uint_as_float(h.w) *
+                                    expf(-2.0f * alpha * __uint_as_float(h.z)) * gain;
+                        }
+                    }
+                    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, lkey);
+                    if (lkey != kNoKey) {
+                        const int leader = __ffs(peers) - 1;
+                        float v = lane == leader ? acc[lkey] : 0.0f;
+                        for (uint32_t m = peers; m; m &= m - 1) v += __shfl_sync(peers, score, __ffs(m) - 1);
+                        if (lane == leader) {
+                            acc[lkey] = v;
+                            const uint32_t bit = 1u << (lkey & 31u);
+                            if (!(atomicOr(&bits[lkey >> 5], bit) & bit)) {
+                                const int q = atomicAdd(&s_count, 1);
+                                if (q < lcap) flist[q] = (int)lkey;
+                                else atomicOr(a.err, SONAR_DEVERR_INDEX);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // pass 2: the listed bins get P (0.5 + w_sm) on top of the additive
+            // term written by pass 1 (visible after the barrier), then are reset
+            const int nl = min(s_count, lcap);
+            for (int q = tid; q < nl; q += nt) {
+                const int k = flist[q];
+                const int rw = k / cw, cl = k - rw * cw;
+                const uint32_t b = (uint32_t)rw * naz_r + c0_r + (uint32_t)cl;
+                const float P = acc[k];
+                acc[k] = 0.0f;
+                bits[k >> 5] = 0u;
+                if (binned_r) binned_r[b] = P;
+                if (P != 0.0f) {
+                    const float w_sm = gauss_of(bin_draws(b, S, K), sig_sm);
+                    noised_r[b] = P * (0.5f + w_sm) + noised_r[b];
+                }
+            }
+            clean_nbin = nbin;
+            __syncthreads();
+            continue;
+        }
+        clean_nbin = -1;   // the path below leaves its accumulator in use
         if (per_beam) {
             for (int k = tid; k < nbeam * S.nr; k += nt) accb[k] = 0.0f;
             for (int c = tid; c <= cw; c += nt) s_b0[c] = first_beam_of_col(U.c0 + c, S.nb, S.naz) - i0;
@@ -218,6 +366,7 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         // stores would otherwise make the compiler reload them every bin)
         const uint32_t naz_r = (uint32_t)S.naz, c0_r = (uint32_t)U.c0, flo = S.frame_lo, fhi = S.frame_hi;
         const float rmin_r = S.rmin;
+        const AdditiveTerm additive{dr, rmin_r, inv_rmax2, sig_sa};
         float* const noised_r = a.noised + S.polar_off;
         float* const binned_r = a.binned ? a.binned + S.polar_off : nullptr;
         // Pass 1 writes every bin's additive term to I~ (pass 2 adds the
@@ -247,16 +396,16 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
                 }
                 const U4 x = additive_words(b0 >> 2, flo, fhi, K);
                 const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
-                const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin_r);
                 float add[4], keep[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float w_sa = rayleigh_of(xw[j], sig_sa);
-                    add[j] = rc * rc * inv_rmax2 * (1.0f + s_pat[4 * qc + j] * w_sa);
+                    add[j] = additive(row, s_pat[4 * qc + j], xw[j]);
                     keep[j] = add[j];
                     if (P[j] != 0.0f) {
                         keep[j] = P[j];
-                        list[atomicAdd(&s_count, 1)] = k0 + j;
+                        const int q = atomicAdd(&s_count, 1);
+                        if (q < lcap) list[q] = k0 + j;
+                        else atomicOr(a.err, SONAR_DEVERR_INDEX);
                     }
                 }
                 if (vec) {
@@ -287,16 +436,16 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
                     P = acc[k];
                 }
                 const U4 x = additive_words(b >> 2, flo, fhi, K);
-                const float w_sa = rayleigh_of(word_of(x, b & 3u), sig_sa);
-                const float rc = fmaf(small_u2f(row) + 0.5f, dr, rmin_r);
-                const float additive = rc * rc * inv_rmax2 * (1.0f + s_pat[col] * w_sa);
+                const float add = additive(row, s_pat[col], word_of(x, b & 3u));
                 if (binned_r) binned_r[b] = P;
-                noised_r[b] = additive;
+                noised_r[b] = add;
                 if (P != 0.0f) {
                     acc[k] = P;
-                    list[atomicAdd(&s_count, 1)] = k;
+                    const int q = atomicAdd(&s_count, 1);
+                    if (q < lcap) list[q] = k;
+                    else atomicOr(a.err, SONAR_DEVERR_INDEX);
                 } else {
-                    acc[k] = additive;
+                    acc[k] = add;
                 }
                 row += drow;
                 col += dcol;
@@ -306,7 +455,7 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
         __syncthreads();
         // Pass 2: the listed bins (P != 0) add P (0.5 + w_sm) to the additive
         // term that pass 1 wrote (visible to the block after the barrier)
-        const int nlist = s_count;
+        const int nlist = min(s_count, lcap);
         for (int q = tid; q < nlist; q += nt) {
             const int k = list[q];
             const int rw = k / cw, cl = k - rw * cw;

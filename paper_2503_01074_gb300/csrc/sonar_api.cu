@@ -143,7 +143,9 @@ Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
     if (it != ctx->tune.end()) t = it->second;
     const int bpc = std::max(1, s.n_beams / std::max(1, s.n_az_bins));
     if (t.cols <= 0) t.cols = std::max(1, t.block / std::max(1, s.n_elev * bpc));
-    const int max_cols_smem = std::max(1, (int)(kMaxDynSmem / 4 / 2) / s.n_range_bins);
+    // a unit's column block, its bitmap (a bit per bin) and its list (at most a
+    // word per bin) fit the dynamic shared memory: bins * 65 / 32 words
+    const int max_cols_smem = std::max(1, (int)(kMaxDynSmem / 4 * 32 / 65) / s.n_range_bins);
     t.cols = std::max(1, std::min({t.cols, s.n_az_bins, max_cols_smem, kMaxCols}));
     if (t.block < 32 || t.block > 512 || (t.block & 31)) t.block = 128;
     if (t.tb <= 0) t.tb = 8;
@@ -232,7 +234,7 @@ SensorDev make_sensor(const sonar_sensor& s, uint64_t seed, uint64_t frame, cons
     // same order; wider units are narrowed until they fit.
     auto fits = [&](const SensorDev& x) {
         const int64_t bins = (int64_t)x.nr * x.cols;
-        const int64_t need = bins + unit_beams_max(x) * x.nr + std::min<int64_t>(unit_rays_max(x), bins);
+        const int64_t need = bins + unit_beams_max(x) * x.nr + (bins + 31) / 32 + std::min<int64_t>(unit_rays_max(x), bins);
         return need * (int64_t)sizeof(float) <= (int64_t)kMaxDynSmem;
     };
     SensorDev one_col = d;
@@ -366,12 +368,13 @@ extern "C" sonar_status sonar_scene_info(sonar_ctx_t ctx, int32_t id, int64_t ou
 namespace {
 
 
-// Shared memory of a binning block: the column block of the unit plus the
-// list of its non-empty bins (no more entries than rays, nor than bins).
+// Shared memory of a binning block: the column block of the unit, the per-beam
+// rows of the fold if any, a bitmap of the bins with returns, and the list of
+// those bins (no more entries than rays, nor than bins).
 size_t bin_smem(const SensorDev& s) {
     const int64_t bins = (int64_t)s.nr * s.cols;
     const int64_t beams = s.fold_beams ? unit_beams_max(s) * s.nr : 0;   // per-beam rows of the fold
-    return (size_t)(bins + beams + std::min<int64_t>(unit_rays_max(s), bins)) * sizeof(float);
+    return (size_t)(bins + beams + (bins + 31) / 32 + std::min<int64_t>(unit_rays_max(s), bins)) * sizeof(float);
 }
 
 // The context's exact-ray table buffer, grown to `entries`; a new buffer holds
@@ -1557,7 +1560,7 @@ extern "C" sonar_status sonar_autotune(sonar_batch_t b, const sonar_params* p, c
         const int tb = best.tb, occ = best.occ;
         for (int block : {64, 128, 256}) {
             for (int cols : {1, 2, 4, 8, 16, 32}) {
-                if (cols > k[3] || (size_t)cols * k[2] * 4 > kMaxDynSmem / 2) continue;
+                if (cols > k[3] || (size_t)cols * k[2] * 4 * 65 > kMaxDynSmem * 32) continue;
                 ctx->tune[k] = Tune{cols, tb, block, occ};
                 if ((st = batch_plan(b)) != SONAR_OK) goto restore;
                 if (batch_scratch(b, out) != cudaSuccess) { st = fail(ctx, SONAR_ERR_OOM, "batch scratch"); goto restore; }
