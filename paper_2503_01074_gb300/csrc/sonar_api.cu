@@ -613,7 +613,8 @@ struct sonar_batch {
     SceneDev* d_scenes = nullptr;
     int32_t* d_fan_prefix = nullptr;
     int32_t* d_trace_prefix = nullptr;
-    int2* d_trace_map = nullptr;      // per trace block: (sensor, tile)
+    int4* d_trace_map = nullptr;      // per trace block: (sensor, tile, scene, 0)
+    std::vector<int4> h_trace_map;    // its host copy (an update that moves an item to another scene patches it)
     int2* d_fan_map = nullptr;        // per fan block: (sensor, block)
     int32_t* d_row_map = nullptr;     // per range row: sensor
     // fan coordinate tables: sensors with the same fan geometry share one,
@@ -882,7 +883,8 @@ sonar_status batch_plan(sonar_batch* b) {
                 e = cudaMemcpy(b->d_members, mem.data(), sizeof(int32_t) * mem.size(), cudaMemcpyHostToDevice);
         }
     }
-    std::vector<int2> tmap, fmap;
+    std::vector<int4> tmap;
+    std::vector<int2> fmap;
     std::vector<int32_t> rmap;
     // Ray-cast blocks in eight bands of decreasing upward component (world z) of
     // their tile's central ray, sensor by sensor inside a band.  Over a seabed
@@ -917,14 +919,17 @@ sonar_status batch_plan(sonar_batch* b) {
                          [](const std::pair<float, int64_t>& x, const std::pair<float, int64_t>& y) {
                              return x.first < y.first;
                          });
-        for (const auto& q : order) tmap.push_back(make_int2((int)(q.second >> 32), (int)(q.second & 0xFFFFFFFF)));
+        for (const auto& q : order) {
+            const int k = (int)(q.second >> 32);
+            tmap.push_back(make_int4(k, (int)(q.second & 0xFFFFFFFF), b->hs[k].scene, 0));
+        }
     }
     for (int k = 0; k < n; ++k) {
         if (b->lut_owner[k] < 0)   // sensors with a shared table are resampled by the grouped launch
             for (int t = 0; t < b->fan_prefix[k + 1] - b->fan_prefix[k]; ++t) fmap.push_back(make_int2(k, t));
         for (int r = 0; r < b->hs[k].nr; ++r) rmap.push_back(k);
     }
-    alloc((void**)&b->d_trace_map, sizeof(int2) * tmap.size());
+    alloc((void**)&b->d_trace_map, sizeof(int4) * tmap.size());
     alloc((void**)&b->d_fan_map, sizeof(int2) * std::max<size_t>(1, fmap.size()));
     b->fan_blocks = (int)fmap.size();
     alloc((void**)&b->d_row_map, sizeof(int32_t) * rmap.size());
@@ -966,7 +971,8 @@ sonar_status batch_plan(sonar_batch* b) {
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_trace_prefix, b->trace_prefix.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_trace_map, tmap.data(), sizeof(int2) * tmap.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_trace_map, tmap.data(), sizeof(int4) * tmap.size(), cudaMemcpyHostToDevice);
+    b->h_trace_map = std::move(tmap);
     if (e == cudaSuccess && !fmap.empty())
         e = cudaMemcpy(b->d_fan_map, fmap.data(), sizeof(int2) * fmap.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -1153,8 +1159,10 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
     const int slot = b->stage_next;
     b->stage_next ^= 1;
     CU(cudaEventSynchronize(b->stage_ev[slot]), "staging wait");
+    bool scene_moved = false;
     for (int k = 0; k < n; ++k) {
         SensorDev S = b->hs[k];
+        scene_moved |= S.scene != items[k].scene_id;
         const sonar_batch_item& it = items[k];
         const SensorDev fresh = make_sensor(it.sensor, it.seed, it.frame, Tune{S.cols, S.tb, b->block, S.occ},
                                             it.fan_w, it.fan_h);
@@ -1181,6 +1189,12 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(b->d_sens, b->h_stage[slot], sizeof(SensorDev) * n, cudaMemcpyHostToDevice, s),
        "descriptor upload");
+    if (scene_moved) {   // the ray-cast map carries each block's scene: patch it (rare, pageable copy)
+        for (int4& m : b->h_trace_map) m.z = b->hs[m.x].scene;
+        CU(cudaMemcpyAsync(b->d_trace_map, b->h_trace_map.data(), sizeof(int4) * b->h_trace_map.size(),
+                           cudaMemcpyHostToDevice, s),
+           "trace map upload");
+    }
     CU(cudaEventRecord(b->stage_ev[slot], s), "cudaEventRecord");
     return SONAR_OK;
 }

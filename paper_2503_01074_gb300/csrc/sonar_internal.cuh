@@ -212,7 +212,7 @@ struct TraceCounters {
 struct TraceArgs {
     const SensorDev* sensors;   // batch: device array; single: nullptr (use `one`)
     const SceneDev* scenes;     // batch: device table; single: nullptr (use `one_scene`)
-    const int2* block_map;      // batch: per block (sensor, tile of that sensor)
+    const int4* block_map;      // batch: per block (sensor, tile of that sensor, its scene, 0)
     int32_t n_sensors;
     SensorDev one;
     SceneDev one_scene;

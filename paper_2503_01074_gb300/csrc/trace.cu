@@ -217,23 +217,28 @@ template <int MINB, bool STATS, int W>
 __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
-    __shared__ int s_tile;
-    if (threadIdx.x == 0) {
-        if (a.sensors) {
-            const int2 m = a.block_map[blockIdx.x];
-            S = a.sensors[m.x];
-            SC = a.scenes[S.scene];
-            s_tile = m.y;
-        } else {
+    int tile;
+    if (a.sensors) {
+        // the warp copies the sensor and scene descriptors word by word, both at
+        // once (the map carries the scene index): one round trip after the map
+        const int4 m = a.block_map[blockIdx.x];
+        const uint32_t* s_src = reinterpret_cast<const uint32_t*>(a.sensors + m.x);
+        const uint32_t* c_src = reinterpret_cast<const uint32_t*>(a.scenes + m.z);
+        constexpr int kSW = (int)(sizeof(SensorDev) / 4), kCW = (int)(sizeof(SceneDev) / 4);
+        for (int i = threadIdx.x; i < kSW; i += 32) reinterpret_cast<uint32_t*>(&S)[i] = __ldg(s_src + i);
+        for (int i = threadIdx.x; i < kCW; i += 32) reinterpret_cast<uint32_t*>(&SC)[i] = __ldg(c_src + i);
+        tile = m.y;
+    } else {
+        if (threadIdx.x == 0) {
             S = a.one;
             SC = a.one_scene;
-            s_tile = blockIdx.x;
         }
+        tile = blockIdx.x;
     }
     __syncthreads();
     const int tb = S.tb, te = 32 / S.tb;
     const int tiles_b = (S.nb + tb - 1) / tb;
-    const int ty = s_tile / tiles_b, tx = s_tile - ty * tiles_b;
+    const int ty = tile / tiles_b, tx = tile - ty * tiles_b;
     const int lane = threadIdx.x;
     const int ri = tx * tb + (lane % tb);
     const int rj = ty * te + lane / tb;

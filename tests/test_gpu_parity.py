@@ -504,3 +504,31 @@ def test_batch_step_equals_separate_calls(son, tiny, tiny_sid, normalise):
     assert st == 0 and bits == 0
     ref.close()
     stp.close()
+
+
+def test_batch_update_moves_items_between_scenes(son, tiny, tiny_sid):
+    """An update may move items to another scene: the ray-cast block map,
+    which carries each block's scene, follows, and every item again equals
+    its single render bit for bit (graph replayed, not recaptured)."""
+    mesh, mu = tiny
+    items = batch_items(son, tiny, tiny_sid)
+    sids = sorted({sid for sid, _, _, _ in items})
+    assert len(sids) == 2
+    theta = son.theta(0.05, 1.0, np.concatenate([mu, [0.4, 0.6]]).astype(np.float32))
+    prm = RenderParams()
+    b = son.batch(items)
+    b.render(theta, prm)
+    graphs = b.info()["graphs"]
+    moved = [(sids[1] if sid == sids[0] else sids[0], spec, seed + 3, frame + 3) for sid, spec, seed, frame in items]
+    b.update(moved)
+    b.render(theta, prm)
+    torch.cuda.synchronize()
+    for k, (sid, spec, seed, frame) in enumerate(moved):
+        single = son.render(sid, spec, theta, prm, seed, frame, hits=True, fan=True)
+        v = b.view(k)
+        assert torch.equal(v["hits"], single["hits"]), k
+        assert torch.equal(v["polar"], single["polar"]), k
+    assert b.info()["graphs"] == graphs
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+    b.close()
