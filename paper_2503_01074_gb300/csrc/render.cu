@@ -76,18 +76,29 @@ __global__ void __launch_bounds__(512) k_bin(BinArgs a) {
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
     int clean_nbin = -1;   // block-uniform: the unit size whose accumulator and bitmap are known zero
+    int next_u = 0;   // thread 0: the unit taken ahead, while the block works on the current one
     for (int iter = 0;; ++iter) {
         int u;
         if (a.work_counter) {
-            if (tid == 0) s_unit = atomicAdd(a.work_counter, 1);
+            if (tid == 0) s_unit = iter == 0 ? atomicAdd(a.work_counter, 1) : next_u;
             __syncthreads();
             u = s_unit;
+            if (tid == 0 && u < a.n_units) next_u = atomicAdd(a.work_counter, 1);
         } else {
             if (iter > 0) break;
             u = blockIdx.x;
         }
         if (u >= a.n_units) break;
-        if (tid == 0) load_unit(a, u, &S, &SC, &U);
+        if (a.units) {   // warp 0 fetches the unit, then its sensor and scene descriptors at once
+            if (warp == 0) {
+                const Unit un = a.units[u];
+                copy_words(&S, a.sensors + un.sensor, lane);
+                copy_words(&SC, a.scenes + un.scene, lane);
+                if (lane == 0) U = un;
+            }
+        } else if (tid == 0) {
+            load_unit(a, u, &S, &SC, &U);
+        }
         __syncthreads();
         const int cw = U.c1 - U.c0;
         const int i0 = first_beam_of_col(U.c0, S.nb, S.naz), i1 = first_beam_of_col(U.c1, S.nb, S.naz);
@@ -930,29 +941,31 @@ __global__ void __launch_bounds__(512) k_adjoint(AdjArgs a) {
     const int nm = a.n_mat, nq = nm + 2;
     const float alpha = __ldg(a.theta), gain = __ldg(a.theta + 1);
     const int mode = a.params.normalise;
+    int next_u = 0;   // thread 0: the unit taken ahead
     for (int iter = 0;; ++iter) {
         int u;
         if (a.work_counter) {
-            if (tid == 0) s_unit = atomicAdd(a.work_counter, 1);
+            if (tid == 0) s_unit = iter == 0 ? atomicAdd(a.work_counter, 1) : next_u;
             __syncthreads();
             u = s_unit;
+            if (tid == 0 && u < a.n_units) next_u = atomicAdd(a.work_counter, 1);
         } else {
             if (iter > 0) break;
             u = blockIdx.x;
         }
         if (u >= a.n_units) break;
-        if (tid == 0) {
-            if (a.units) {
-                U = a.units[u];
-                S = a.sensors[U.sensor];
-                SC = a.scenes[S.scene];
-            } else {
-                S = a.one;
-                SC = a.one_scene;
-                U.sensor = 0;
-                U.r0 = u * a.chunk;
-                U.r1 = min(U.r0 + a.chunk, a.one.nb * a.one.ne);
-            }
+        if (a.units && warp == 0) {   // warp 0 fetches the unit, then its sensor and scene descriptors at once
+            const AdjUnit un = a.units[u];
+            copy_words(&S, a.sensors + un.sensor, lane);
+            copy_words(&SC, a.scenes + un.scene, lane);
+            if (lane == 0) U = un;
+        }
+        if (!a.units && tid == 0) {
+            S = a.one;
+            SC = a.one_scene;
+            U.sensor = 0;
+            U.r0 = u * a.chunk;
+            U.r1 = min(U.r0 + a.chunk, a.one.nb * a.one.ne);
         }
         for (int k = tid; k < nw * nm; k += nt) slab[k] = 0.0f;
         __syncthreads();

@@ -757,6 +757,7 @@ sonar_status batch_plan(sonar_batch* b) {
         for (int tile = 0; tile < S.n_tiles; ++tile) {
             Unit u;
             u.sensor = k;
+            u.scene = S.scene;
             u.c0 = tile * S.cols;
             u.c1 = std::min(u.c0 + S.cols, S.naz);
             const int64_t i0 = first_beam_of_col(u.c0, S.nb, S.naz), i1 = first_beam_of_col(u.c1, S.nb, S.naz);
@@ -799,7 +800,8 @@ sonar_status batch_plan(sonar_batch* b) {
     for (int k = 0; k < n; ++k) {
         const int64_t r = (int64_t)b->hs[k].nb * b->hs[k].ne;
         for (int64_t r0 = 0; r0 < r; r0 += b->adj_chunk)
-            b->adj_units.push_back(AdjUnit{k, (int32_t)r0, (int32_t)std::min<int64_t>(r, r0 + b->adj_chunk), 0});
+            b->adj_units.push_back(AdjUnit{k, (int32_t)r0, (int32_t)std::min<int64_t>(r, r0 + b->adj_chunk),
+                                           b->hs[k].scene});
     }
     const size_t nu = b->units.size(), na = b->adj_units.size();
     cudaError_t e = cudaSuccess;
@@ -1189,11 +1191,18 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(b->d_sens, b->h_stage[slot], sizeof(SensorDev) * n, cudaMemcpyHostToDevice, s),
        "descriptor upload");
-    if (scene_moved) {   // the ray-cast map carries each block's scene: patch it (rare, pageable copy)
+    if (scene_moved) {   // the ray-cast map and the work units carry their scene: patch them (rare, pageable copies)
         for (int4& m : b->h_trace_map) m.z = b->hs[m.x].scene;
+        for (Unit& x : b->units) x.scene = b->hs[x.sensor].scene;
+        for (AdjUnit& x : b->adj_units) x.scene = b->hs[x.sensor].scene;
         CU(cudaMemcpyAsync(b->d_trace_map, b->h_trace_map.data(), sizeof(int4) * b->h_trace_map.size(),
                            cudaMemcpyHostToDevice, s),
            "trace map upload");
+        CU(cudaMemcpyAsync(b->d_units, b->units.data(), sizeof(Unit) * b->units.size(), cudaMemcpyHostToDevice, s),
+           "unit upload");
+        CU(cudaMemcpyAsync(b->d_adj_units, b->adj_units.data(), sizeof(AdjUnit) * b->adj_units.size(),
+                           cudaMemcpyHostToDevice, s),
+           "unit upload");
     }
     CU(cudaEventRecord(b->stage_ev[slot], s), "cudaEventRecord");
     return SONAR_OK;

@@ -81,7 +81,8 @@ struct SensorDev {
 struct Unit {
     int32_t sensor;
     int32_t c0, c1;
-    int32_t rays;
+    int32_t rays;     // host: orders the work list
+    int32_t scene;    // the sensor's scene (its descriptor is fetched beside the sensor's)
 };
 
 // First beam whose azimuth bin floor((2i+1) naz / (2 nb)) is >= c.
@@ -196,6 +197,14 @@ __device__ __forceinline__ float gauss_of(const U4& x, float sigma_sm) {
 }
 __device__ __forceinline__ float w_sm_of(uint32_t bin, const SensorDev& s, float sigma_sm, const PhiloxKey& K) {
     return gauss_of(bin_draws(bin, s, K), sigma_sm);
+}
+
+// Copies a descriptor word by word with the lanes of one warp (lane < 32).
+template <class T>
+__device__ __forceinline__ void copy_words(T* dst, const T* src, int lane) {
+    static_assert(sizeof(T) % 4 == 0, "descriptor of whole words");
+    for (int i = lane; i < (int)(sizeof(T) / 4); i += 32)
+        reinterpret_cast<uint32_t*>(dst)[i] = __ldg(reinterpret_cast<const uint32_t*>(src) + i);
 }
 
 // ---- kernel argument blocks ----
@@ -322,7 +331,7 @@ struct FanLutArgs {
 
 // A work unit of the adjoint: canonical rays [r0, r1) of one sensor.
 struct AdjUnit {
-    int32_t sensor, r0, r1, pad;
+    int32_t sensor, r0, r1, scene;
 };
 
 struct RowInfo {
