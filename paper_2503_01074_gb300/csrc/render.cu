@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(256) k_fan_tiles(FanArgs a) {
         const int v = v0 + k;
         if (v >= S.fan_h) break;
         const int64_t pix = (int64_t)v * S.fan_w + u;
-        F[pix] = fan_blend(lut ? __ldg(lut + pix) : fan_coord(S, pix), P);
+        __stcs(F + pix, fan_blend(lut ? __ldg(lut + pix) : fan_coord(S, pix), P));   // never re-read here: stream past L2
     }
 }
 
@@ -750,7 +750,9 @@ __global__ void __launch_bounds__(256) k_fan_group(FanGroupArgs a) {
         for (int q = 0; q < kFanGroup; ++q) {
             if (q < nm) {
                 const uint4 cq = M[q].fan_lut ? c : fan_coord(M[q], pix);
-                a.fan[M[q].fan_off + pix] = fan_blend(cq, a.polar + M[q].polar_off);
+                // the fan is never re-read by the step: streaming stores leave L2
+                // to the polar images and the coordinate table
+                __stcs(a.fan + M[q].fan_off + pix, fan_blend(cq, a.polar + M[q].polar_off));
             }
         }
     }
