@@ -820,7 +820,7 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
             for (int k = 0; k < 4; ++k) {
                 const int q = lane + 32 * k;
                 if (q < n4) {
-                    xs[k] = __ldg(In4 + q);
+                    xs[k] = __ldcs(In4 + q);   // I~ is not read again by the adjoint: evict first, keep G in L2
                     ys[k] = __ldg(G4 + q);
                 }
             }
@@ -845,7 +845,7 @@ __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, Sen
             const float4* G4 = reinterpret_cast<const float4*>(G);
 #pragma unroll 4
             for (int q = lane; q < (s.naz >> 2); q += 32) {
-                const float4 x = __ldg(In4 + q), y = __ldg(G4 + q);
+                const float4 x = __ldcs(In4 + q), y = __ldg(G4 + q);
                 const int j = q << 2;
                 if (x.x > m) { m = x.x; am = j; }
                 if (x.y > m) { m = x.y; am = j + 1; }
