@@ -172,13 +172,17 @@ int single_variant(const sonar_ctx* ctx, const sonar_sensor& s, int tb, int occ)
     return (occ & ~kTraceWide) | wide_for_launch(ctx, blocks);
 }
 
-// A single frame alone on the GPU: the tuned shapes, but at least two binning
-// units per SM (the batch tunes may favour few, large units), and the ray-cast
-// variant chosen by the frame's own launch size.
+// A single frame alone on the GPU: the tuned shapes, but binning units of
+// about two per SM (the batch tunes may favour few, large units) and at least
+// four columns wide, a multiple of 4 where the row allows, so that the noise
+// pass draws four bins per Philox block; and the ray-cast variant chosen by the
+// frame's own launch size.
 Tune single_tune(const sonar_ctx* ctx, const sonar_sensor& s) {
     Tune t = tune_for(ctx, s);
-    const int want = std::max(1, s.n_az_bins / (2 * ctx->sm_count));
-    if (t.cols > want) t.cols = want;
+    int cols = std::max(4, s.n_az_bins / (2 * ctx->sm_count));
+    if (s.n_az_bins % 4 == 0) cols &= ~3;
+    const int max_cols_smem = std::max(1, (int)(kMaxDynSmem / 4 * 32 / 65) / s.n_range_bins);
+    t.cols = std::max(1, std::min({cols, s.n_az_bins, max_cols_smem, kMaxCols}));
     t.occ = single_variant(ctx, s, t.tb, t.occ);
     return t;
 }
