@@ -268,6 +268,7 @@ def arm_config(frames, rays_per_frame, world):
     """The workload description both arms print."""
     return {"workload": WORKLOAD, "frames_per_step": frames, "rays_per_frame": rays_per_frame,
             "step": "batched forward (graph) + batched adjoint (graph)",
+            "cast": "bounded at the sonar's maximum range r_max (returns beyond it are not searched)",
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world}"}
 
 
@@ -778,6 +779,26 @@ def run_ours(args):
         extras["combined_step"] = {"fps": B / (sms / 1e3), "device_ms_per_step": sms,
                                    "roofline": leg_roofline(fwd_bytes + adj_bytes, sms / B),
                                    "graph_kernels": batch.kernels()}
+        # the timed step with an unbounded cast (clip_tmax = 0): the same images,
+        # fans and gradient, with the rays that reach the seabed beyond r_max
+        # followed to their returns
+        prm_ub = RenderParams(clip_tmax=0)
+        ub_ms, ub_trace = [], []
+        for k in range(args.steps + 2):
+            flush.zero_()
+            e_f[0].record(stream)
+            batch.render(theta, prm_ub, hits=True, fan=True)
+            batch.backward(theta, prm_ub, G, hits=True, out=dtheta)
+            e_f[1].record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                ub_ms.append(e_f[0].elapsed_time(e_f[1]))
+                ub_trace.append(batch.timings()["trace"])
+        ums = float(np.mean(ub_ms))
+        extras["unbounded_cast"] = {"fps": B / (ums / 1e3), "device_ms_per_step": ums,
+                                    "trace_ms": float(np.mean(ub_trace))}
+        step()
+        torch.cuda.synchronize()
         # the plain single-sensor path: one sonar_render (and sonar_render_backward)
         # call per frame, no batching, no graph.  Host loop: the Python loop as a
         # caller runs it.  Device: the same calls queued behind a long sleep
@@ -800,12 +821,12 @@ def run_ours(args):
                     son.backward(sid, p, theta, prm, SEED, fids[j], g1, out["noised"], out["hits"])
 
         # the single-sensor path walks the tree its own launch calls for: the
-        # 8-wide one when the frame's ray cast is at most two waves of one-warp
-        # blocks (64 per SM), as the library decides
+        # 8-wide one when the frame's ray cast is at most one wave of one-warp
+        # blocks (32 per SM), as the library decides
         row = next((r for r in son.tune_get().tolist() if r[:4] == shape_of(base)), None)
         tbw = row[5] if row else 8
         blocks1 = -(-base.n_beams // tbw) * -(-base.n_elev // (32 // tbw))
-        wide1 = blocks1 <= 2 * 32 * torch.cuda.get_device_properties(dev).multi_processor_count
+        wide1 = blocks1 <= 32 * torch.cuda.get_device_properties(dev).multi_processor_count
         tr1 = float(np.mean([trace_bytes(son, sid, p, prm, wide=wide1)[0] for p in poses]))
         fwd_bytes1 = fwd_bytes - bytes_frame["trace"] + tr1
         single = {"tree": "8-wide" if wide1 else "4-wide"}

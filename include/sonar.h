@@ -88,7 +88,12 @@ typedef struct {
     float sigma_phi;     /* beam-pattern width in Eq. 3 (rad^2), > 0 */
     int32_t normalise;   /* 0 none, 1 range-row maximum (default), 2 global maximum */
     int32_t two_sided;   /* 1: incidence factor |d.n| (default); 0: max(0, -d.n) */
-    int32_t clip_tmax;   /* 1: only hits with r < r_max count; 0: trace to infinity */
+    int32_t clip_tmax;   /* 1: the cast ends at the sonar's maximum range, so only
+                               returns with r < r_max are found (default); 0: the
+                               cast is unbounded and records returns beyond r_max
+                               too.  The images and gradients are the same either
+                               way (returns at or beyond r_max are never binned);
+                               the bounded cast visits fewer nodes. */
     int32_t accumulate;  /* 0: deterministic fold of each bin's returns in canonical
                                ray order (default; bitwise reproducible);
                             1: warp-aggregated shared-memory atomics */
@@ -357,9 +362,9 @@ sonar_status sonar_autotune(sonar_batch_t batch, const sonar_params* params,
  * the ray-cast variant, a sum of flags: 8 caps its registers at 64 (32
  * one-warp blocks per SM), 16 walks the 8-wide tree instead of the 4-wide one
  * (both are built per scene; the hit records are the same either way).  A
- * batch takes the row's variant; a single-sensor call takes the 8-wide tree
- * when its ray cast is at most two waves of one-warp blocks (64 per SM), the
- * 4-wide one otherwise, and no register cap when it is at most one wave.
+ * batch takes the row's variant; a single-sensor call whose ray cast is at
+ * most one wave of one-warp blocks (32 per SM) walks the 8-wide tree without
+ * the register cap, and a larger one the 4-wide tree with its row's cap.
  * Returns the number of entries in *count. */
 sonar_status sonar_tune_get(sonar_ctx_t ctx, int32_t* rows, int32_t cap, int32_t* count);
 

@@ -13,6 +13,8 @@ which rays a comparison may exclude:
   tie      the nearest hit on another triangle is within 1e-6 * t
   graze    |d . n_hat| < 1e-6
   binedge  the range lies within 1e-4 m of a range-bin edge (r_min, r_max included)
+  limit    (a cast bounded at r_max) the nearest return lies within 1e-5 * r_max
+           of the bound, on either side of it
 
 Parity status: every step is pinned by tests/test_oracle_*.py (closed forms,
 invariants, brute force, an independent Philox implementation, moment tests,
@@ -80,7 +82,12 @@ class Params:
     sigma_phi: float = 1.0     # beam-pattern width (rad^2), Eq. 3
     normalise: int = 1         # 0 none, 1 range-row max, 2 global max
     two_sided: int = 1
-    clip_tmax: int = 0
+    clip_tmax: int = 1         # 1: the cast ends at r_max; 0: unbounded
+
+
+# relative width of the band around r_max inside which a bounded cast's
+# decision is left to rounding (the range tolerance of the parity tests)
+LIMIT_RTOL = 1e-5
 
 
 def sensor_desc(s) -> np.ndarray:
@@ -130,8 +137,10 @@ def closest_hits(tv, origin, dirs, t_max=np.inf, nthreads=0):
     return out
 
 
-def flags(sensor, hits):
-    """C13 flags: edge, tie, graze, binedge (bool arrays per ray)."""
+def flags(sensor, hits, limit=None):
+    """C13 flags: edge, tie, graze, binedge, limit (bool arrays per ray).
+    `limit` marks rays whose nearest return lies within the range tolerance of
+    the cast's r_max bound, on either side of it (None: an unbounded cast)."""
     hit = hits["tri"] >= 0
     u, v, t = hits["u"], hits["v"], hits["t"]
     edge = hit & (np.minimum(np.minimum(u, v), 1.0 - u - v) < 1e-6)
@@ -144,7 +153,8 @@ def flags(sensor, hits):
         e = np.clip(np.round((t - rmin) / dr), 0, sensor.n_range_bins)
         near = np.abs(t - (rmin + e * dr)) < 1e-4
     binedge = hit & (t > rmin - 1e-3) & (t < rmax + 1e-3) & near
-    return {"edge": edge, "tie": tie, "graze": graze, "binedge": binedge}
+    lim = np.zeros_like(hit) if limit is None else limit
+    return {"edge": edge, "tie": tie, "graze": graze, "binedge": binedge, "limit": lim}
 
 
 def render(mesh, mu, alpha, gain, sensor, params: Params = Params(), seed=0, frame=0,
@@ -158,8 +168,25 @@ def render(mesh, mu, alpha, gain, sensor, params: Params = Params(), seed=0, fra
         np.ascontiguousarray(np.asarray(ray_ids, np.int64))
     dirs = np.ascontiguousarray(dirs_all[ids])
     tv = tri_verts(mesh) if tv is None else tv
-    t_max = float(np.float32(sensor.r_max)) if params.clip_tmax else np.inf
-    h = closest_hits(tv, sd[0:3], dirs, t_max, nthreads)
+    limit = None
+    if params.clip_tmax:
+        # the cast ends at the sonar's maximum range (Sec. III-A-2: r_max, the
+        # range that scales Eq. 3).  It runs a hair past r_max so that returns
+        # within the range tolerance of the bound, on either side, are flagged;
+        # a nearest return at or beyond the bound then becomes a miss, which
+        # is exactly the cast bounded at r_max.
+        t_max = float(np.float32(sensor.r_max))
+        h = closest_hits(tv, sd[0:3], dirs, t_max * (1.0 + LIMIT_RTOL), nthreads)
+        limit = (h["tri"] >= 0) & (np.abs(h["t"] - t_max) <= LIMIT_RTOL * t_max)
+        far = (h["tri"] >= 0) & ~(h["t"] < t_max)
+        h["tri"][far] = -1
+        h["t"][far] = np.inf
+        h["u"][far] = 0.0
+        h["v"][far] = 0.0
+        h["dn"][far] = 0.0
+        h["t2"][~(h["t2"] < t_max)] = np.inf
+    else:
+        h = closest_hits(tv, sd[0:3], dirs, np.inf, nthreads)
     n = ids.shape[0]
     mu64 = np.ascontiguousarray(mu, np.float64)
     mat = np.ascontiguousarray(mesh.mat, np.int32)
@@ -169,7 +196,7 @@ def render(mesh, mu, alpha, gain, sensor, params: Params = Params(), seed=0, fra
     key = np.empty(n, np.int64)
     L.oracle_bin_keys(sd, n, ids, h["tri"], h["t"], key)
     out = {"ray_ids": ids, "dirs": dirs, "hits": h, "score": s, "key": key,
-           "flags": flags(sensor, h)}
+           "flags": flags(sensor, h, limit)}
     if ray_ids is not None:
         return out
     nb = sensor.n_range_bins * sensor.n_az_bins

@@ -154,11 +154,11 @@ Tune tune_for(const sonar_ctx* ctx, const sonar_sensor& s) {
 }
 
 // The tree a ray-cast launch of `blocks` one-warp blocks walks: the 8-wide one
-// when the launch is at most two waves (32 resident blocks per SM), where a
+// when the launch is at most one wave (32 resident blocks per SM), where a
 // ray's chain of dependent node loads sets the time, else the 4-wide one,
-// which costs fewer instructions per ray when the GPU is full.
+// which costs fewer instructions per ray once the SMs have warps to switch to.
 int wide_for_launch(const sonar_ctx* ctx, int64_t blocks) {
-    return blocks <= 2ll * 32 * ctx->sm_count ? kTraceWide : 0;
+    return blocks <= 32ll * ctx->sm_count ? kTraceWide : 0;
 }
 
 // The ray-cast variant of one sensor's own launch (tile tb from its tuning
@@ -168,8 +168,8 @@ int wide_for_launch(const sonar_ctx* ctx, int64_t blocks) {
 int single_variant(const sonar_ctx* ctx, const sonar_sensor& s, int tb, int occ) {
     const int64_t be = 32 / tb;
     const int64_t blocks = ((s.n_beams + tb - 1) / tb) * ((s.n_elev + be - 1) / be);
-    if (blocks <= 32ll * ctx->sm_count) return kTraceWide;
-    return (occ & ~kTraceWide) | wide_for_launch(ctx, blocks);
+    if (wide_for_launch(ctx, blocks)) return kTraceWide;
+    return occ & ~kTraceWide;
 }
 
 // A single frame alone on the GPU: the tuned shapes, but binning units of

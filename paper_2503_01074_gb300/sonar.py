@@ -168,7 +168,7 @@ class RenderParams:
     sigma_phi: float = 1.0
     normalise: int = 1
     two_sided: int = 1
-    clip_tmax: int = 0
+    clip_tmax: int = 1      # 1: the cast ends at r_max; 0: unbounded (same images)
     accumulate: int = 0
 
     def c(self) -> Params:

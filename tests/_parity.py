@@ -2,7 +2,8 @@
 
 Tolerances (the sonar path's stated bar):
   - hit/miss and triangle ids identical except for rays the oracle flags as
-    within 1e-6 (barycentric) of a triangle edge, as a near tie or as grazing;
+    within 1e-6 (barycentric) of a triangle edge, as a near tie, as grazing,
+    or (a cast bounded at r_max) as returning within 1e-5 relative of r_max;
   - hit range within 1e-5 relative;
   - polar bins within 1e-4 relative in FP32 (absolute floor 1e-6 of the image
     maximum), excluding the bins that receive a hit within 1e-4 m of a range
@@ -28,7 +29,7 @@ def hit_parity(ref, h, ids=None):
     if ids is not None:
         tri, key, r, cs = tri[ids], key[ids], r[ids], cs[ids]
     f = ref["flags"]
-    amb = f["edge"] | f["tie"] | f["graze"]
+    amb = f["edge"] | f["tie"] | f["graze"] | f["limit"]
     rt = ref["hits"]["tri"].astype(np.int64)
     bad = (tri != rt) & ~amb
     assert not bad.any(), f"{bad.sum()} unflagged rays hit different triangles: {np.flatnonzero(bad)[:10]}"
@@ -51,7 +52,7 @@ def excluded_bins(spec, ref, h):
     nr, naz = spec.n_range_bins, spec.n_az_bins
     _, key, _, _ = gpu_hits(h)
     f = ref["flags"]
-    bad = f["edge"] | f["tie"] | f["graze"] | f["binedge"] | (key != ref["key"])
+    bad = f["edge"] | f["tie"] | f["graze"] | f["limit"] | f["binedge"] | (key != ref["key"])
     mask = np.zeros(nr * naz, bool)
     for k in np.flatnonzero(bad):
         for kk in (key[k], ref["key"][k]):

@@ -199,3 +199,32 @@ def test_adjoint_full_size_stored_equals_recomputed(setup):
     torch.cuda.synchronize()
     assert torch.equal(g1, g2)
     assert torch.isfinite(g1).all() and float(g1.abs().sum()) > 0
+
+
+def test_bounded_cast_gives_the_unbounded_images(setup):
+    """The bench's batch with the cast bounded at r_max (the default) and
+    unbounded: the binned, noised and normalised images, the fans and the
+    gradient are the same bits; the hit records agree on every ray whose
+    unbounded return lies inside r_max, and the other rays are misses in the
+    bounded cast (about a tenth of this workload's rays reach the seabed
+    beyond r_max)."""
+    d = setup
+    b = d["batch"]
+    G = torch.randn(b.n_polar, generator=torch.Generator().manual_seed(5)).to(d["son"].device)
+    out = {}
+    for clip in (0, 1):
+        prm = RenderParams(clip_tmax=clip)
+        b.render(d["theta"], prm, hits=True, fan=True, binned=True)
+        g = b.backward(d["theta"], prm, G, hits=True)
+        torch.cuda.synchronize()
+        out[clip] = [t.clone() for t in (b.binned, b.noised, b.polar, b.fan, g)] + [hits_numpy(b.hits)]
+    for a, c in zip(out[0][:5], out[1][:5]):
+        assert torch.equal(a, c)
+    h0, h1 = out[0][5], out[1][5]
+    rmax = np.float32(d["poses"][0].r_max)
+    far = (h0["tri"] != 0xFFFFFFFF) & (h0["r"] >= rmax)
+    assert 0.02 < far.mean() < 0.5
+    assert (h1["tri"][far] == 0xFFFFFFFF).all()
+    assert np.array_equal(h0[~far], h1[~far])
+    st, bits = d["son"].check()
+    assert st == 0 and bits == 0

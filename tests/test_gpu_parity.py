@@ -73,15 +73,19 @@ def full_check(son, sid, mesh, mu, alpha, gain, spec, prm, seed=0, frame=0, fan=
     return out, ref
 
 
+@pytest.mark.parametrize("clip", [1, 0])
 @pytest.mark.parametrize("pitch", [40.0, 20.0])
-def test_tiny_parity(son, tiny, tiny_sid, pitch):
+def test_tiny_parity(son, tiny, tiny_sid, pitch, clip):
     mesh, mu = tiny
     spec = S.sensor_tiny(pitch)
-    out, ref = full_check(son, tiny_sid, mesh, mu, 0.05, 1.0, spec, RenderParams())
+    out, ref = full_check(son, tiny_sid, mesh, mu, 0.05, 1.0, spec, RenderParams(clip_tmax=clip))
     if pitch == 20.0:
         # the configuration as written: every return lies beyond r_max, so the image is noise only
         assert (ref["key"] < 0).all()
         assert float(out["binned"].abs().max()) == 0.0
+        # a cast bounded at r_max finds nothing; an unbounded one records the far returns
+        tri = hits_numpy(out["hits"])["tri"]
+        assert (tri == 0xFFFFFFFF).all() if clip else (tri != 0xFFFFFFFF).mean() > 0.5
     else:
         assert (ref["key"] >= 0).sum() > 900
 
@@ -92,19 +96,20 @@ def test_normalise_modes(son, tiny, tiny_sid, normalise):
     full_check(son, tiny_sid, mesh, mu, 0.05, 1.0, S.sensor_tiny(40.0), RenderParams(normalise=normalise))
 
 
-def test_one_sided_and_clip(son, tiny, tiny_sid):
+def test_one_sided_and_unbounded(son, tiny, tiny_sid):
     mesh, mu = tiny
-    full_check(son, tiny_sid, mesh, mu, 0.05, 1.0, S.sensor_tiny(40.0), RenderParams(two_sided=0, clip_tmax=1))
+    full_check(son, tiny_sid, mesh, mu, 0.05, 1.0, S.sensor_tiny(40.0), RenderParams(two_sided=0, clip_tmax=0))
 
 
+@pytest.mark.parametrize("clip", [1, 0])
 @pytest.mark.parametrize("seed,n", [(1, 1), (2, 5), (3, 300), (4, 2000)])
-def test_random_soups(son, seed, n):
+def test_random_soups(son, seed, n, clip):
     mesh = S.random_soup(n, seed)
     spec = S.SensorSpec(np.zeros(3, np.float32), S.pose_matrix(0.1, math.radians(15)), 48, 24, 200, 48,
                         math.radians(100.0), math.radians(30.0), 0.5, 20.0, 160, 90)
     sid = son.upload_mesh(mesh)
     mu = np.array([0.2, 0.5, 0.7, 0.9], np.float32)
-    full_check(son, sid, mesh, mu, 0.03, 1.7, spec, RenderParams())
+    full_check(son, sid, mesh, mu, 0.03, 1.7, spec, RenderParams(clip_tmax=clip))
 
 
 @pytest.mark.parametrize("nb,naz", [(100, 37), (64, 200), (37, 37)])
@@ -532,3 +537,32 @@ def test_batch_update_moves_items_between_scenes(son, tiny, tiny_sid):
     st, bits = son.check()
     assert st == 0 and bits == 0
     b.close()
+
+
+def test_single_calls_rebuild_exact_ray_tables_on_geometry_change(son, tiny, tiny_sid):
+    """Single-sensor calls keep the context's exact-ray tables while the angular
+    geometry is unchanged and rebuild them when it changes: alternating two
+    fields of view (and a beam count) gives each frame the same bits as its
+    first render, and the oracle's hits."""
+    mesh, mu = tiny
+    theta = son.theta(0.05, 1.0, mu)
+    prm = RenderParams()
+    a = S.sensor_tiny(40.0)
+    b = S.sensor_tiny(40.0)
+    b.hfov, b.vfov = b.hfov * 0.8, b.vfov * 1.2
+    c = S.sensor_tiny(40.0)
+    c.n_beams = a.n_beams + 8
+    first = {}
+    for rep in range(2):
+        for name, spec in (("a", a), ("b", b), ("c", c)):
+            o = son.render(tiny_sid, spec, theta, prm, 3, 1, hits=True, fan=False)
+            torch.cuda.synchronize()
+            if rep == 0:
+                first[name] = (o["hits"].clone(), o["polar"].clone())
+                ref = O.render(mesh, mu, 0.05, 1.0, spec, oparams(prm), seed=3, frame=1, fan=False)
+                hit_parity(ref, hits_numpy(o["hits"]))
+            else:
+                assert torch.equal(o["hits"], first[name][0]), name
+                assert torch.equal(o["polar"], first[name][1]), name
+    st, bits = son.check()
+    assert st == 0 and bits == 0

@@ -6,7 +6,7 @@ on how its boxes are grouped or in which order they are tested, so every
 ray-cast variant (registers capped or not, 4-wide or 8-wide tree) must give
 bitwise the same hit records, and with them the same images, fans and
 gradients.  Single-sensor calls walk the 8-wide tree for launches of at most
-two waves, so the oracle parity tests of the single path cover it; here a
+one wave, so the oracle parity tests of the single path cover it; here a
 batch is pinned to each variant by a tuning row and compared with the single
 path, with the other variants and with the oracle.
 """

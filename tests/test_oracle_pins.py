@@ -131,14 +131,15 @@ def test_azimuth_bin_integer_formula_exact():
 # closest hit: flat seabed closed form
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("clip", [1, 0])
 @pytest.mark.parametrize("n_az", [64, 24])
-def test_flat_seabed_closed_form(n_az):
+def test_flat_seabed_closed_form(n_az, clip):
     h = 5.0
     mesh = S.quad(-h, 500.0, 0)
     p = math.radians(30.0)
     s = S.SensorSpec(np.zeros(3, np.float32), S.pose_matrix(0.0, p), 64, 16, 200, n_az,
                      math.radians(130.0), math.radians(20.0), 0.5, 30.0)
-    r = O.render(mesh, np.array([0.7], np.float32), 0.05, 1.3, s, O.Params(), fan=False)
+    r = O.render(mesh, np.array([0.7], np.float32), 0.05, 1.3, s, O.Params(clip_tmax=clip), fan=False)
     H, V = float(np.float32(s.hfov)), float(np.float32(s.vfov))
     i = np.arange(s.n_beams).repeat(s.n_elev)
     j = np.tile(np.arange(s.n_elev), s.n_beams)
@@ -153,8 +154,16 @@ def test_flat_seabed_closed_form(n_az):
     sin_dep = -dz / nrm
     expect_r = h / sin_dep
     hits = r["hits"]
-    ok = ~(r["flags"]["edge"] | r["flags"]["tie"])
-    assert (hits["tri"] >= 0).all()
+    rmax = float(np.float32(s.r_max))
+    if clip:
+        # the cast bounded at the sonar's maximum range returns exactly the rays
+        # whose closed-form range is below it (some reach the plane beyond it)
+        assert (expect_r >= rmax).sum() > 20 and (expect_r < rmax).sum() > 500
+        assert np.array_equal(hits["tri"] >= 0, expect_r < rmax)
+        assert np.array_equal(r["flags"]["limit"], np.abs(expect_r - rmax) <= O.LIMIT_RTOL * rmax)
+    else:
+        assert (hits["tri"] >= 0).all() and not r["flags"]["limit"].any()
+    ok = ~(r["flags"]["edge"] | r["flags"]["tie"]) & (hits["tri"] >= 0)
     assert np.allclose(hits["t"][ok], expect_r[ok], rtol=1e-12)
     # incidence cosine of a horizontal plane is the sine of the depression
     assert np.allclose(np.abs(hits["dn"][ok]), sin_dep[ok], rtol=1e-12)
@@ -176,6 +185,27 @@ def test_flat_seabed_closed_form(n_az):
     # invariant: the noise-free polar total equals the sum of binned scores
     assert np.isclose(r["P"].sum(), r["score"][r["key"] >= 0].sum(), rtol=1e-12)
 
+
+
+def test_bounded_cast_changes_records_only():
+    """Returns at or beyond the sonar's maximum range fall outside the polar
+    grid (Sec. III-A-2), so a cast bounded at r_max differs from an unbounded
+    one only in the records of those rays, which become misses: the binned,
+    noised and normalised images and the fan are the same values."""
+    mesh, mu = S.tiny_scene()
+    spec = S.sensor_tiny(28.0)
+    spec.n_beams, spec.n_elev, spec.n_range_bins, spec.n_az_bins = 64, 8, 96, 48
+    spec.fan_w, spec.fan_h = 160, 120
+    a = O.render(mesh, mu, 0.05, 1.0, spec, O.Params(clip_tmax=0), seed=3, frame=2)
+    b = O.render(mesh, mu, 0.05, 1.0, spec, O.Params(clip_tmax=1), seed=3, frame=2)
+    far = (a["hits"]["tri"] >= 0) & (a["hits"]["t"] >= np.float32(spec.r_max))
+    assert far.sum() > 100 and (b["key"] >= 0).sum() > 100          # both kinds of ray occur
+    assert (b["hits"]["tri"][far] == -1).all() and np.isinf(b["hits"]["t"][far]).all()
+    for k in ("tri", "t", "dn"):
+        assert np.array_equal(a["hits"][k][~far], b["hits"][k][~far])
+    assert np.array_equal(a["key"], b["key"])
+    for k in ("P", "noised", "polar", "fan"):
+        assert np.array_equal(a[k], b[k]), k
 
 def test_accumulate_per_bin_closed_form():
     """oracle_accumulate bin by bin: on a flat seabed every ray's range, score,
