@@ -264,9 +264,14 @@ def cpu_baseline(mesh, mu, spec):
                        f"+ binning, noise, normalisation and fan of the full image ({t_bins:.2f} s)")}, r, total
 
 
-def arm_config(frames, rays_per_frame, world):
+SMALL_WORKLOAD = ("profiling case: 512^2-cell fBm heightfield over 100 m (524,288 tris) + 48 piles + 24 boxes "
+                  "= 527,648 tris, 16 materials; the single-frame sonar")
+
+
+def arm_config(frames, rays_per_frame, world, small=False):
     """The workload description both arms print."""
-    return {"workload": WORKLOAD, "frames_per_step": frames, "rays_per_frame": rays_per_frame,
+    return {"workload": SMALL_WORKLOAD if small else WORKLOAD, "frames_per_step": frames,
+            "rays_per_frame": rays_per_frame,
             "step": "batched forward (graph) + batched adjoint (graph)",
             "cast": "bounded at the sonar's maximum range r_max (returns beyond it are not searched)",
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world}"}
@@ -297,7 +302,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(walls)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": arm_config(args.frames, base.n_rays, 1),
+            "data": "synthetic", "config": arm_config(args.frames, base.n_rays, 1, args.small),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(threads), "kind": "oracle",
                              "sample": f"each step: {n} of the {base.n_rays} rays of one frame ({share:.3f} "
                                        f"of the frame) cast by brute force in FP64, then binning, noise, "
@@ -1042,7 +1047,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": arm_config(B, rays_per_frame, world),
+                "config": arm_config(B, rays_per_frame, world, args.small),
                 "Mrays_s": value * rays_per_frame / 1e6,
                 "scene_build_ms": build_ms,
                 "phase_ms": ph_mean,
