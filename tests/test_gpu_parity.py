@@ -74,7 +74,7 @@ def full_check(son, sid, mesh, mu, alpha, gain, spec, prm, seed=0, frame=0, fan=
 
 
 @pytest.mark.parametrize("clip", [1, 0])
-@pytest.mark.parametrize("pitch", [40.0, 20.0])
+@pytest.mark.parametrize("pitch", [40.0, 28.0, 20.0])
 def test_tiny_parity(son, tiny, tiny_sid, pitch, clip):
     mesh, mu = tiny
     spec = S.sensor_tiny(pitch)
@@ -86,6 +86,16 @@ def test_tiny_parity(son, tiny, tiny_sid, pitch, clip):
         # a cast bounded at r_max finds nothing; an unbounded one records the far returns
         tri = hits_numpy(out["hits"])["tri"]
         assert (tri == 0xFFFFFFFF).all() if clip else (tri != 0xFFFFFFFF).mean() > 0.5
+    elif pitch == 28.0:
+        # returns on both sides of r_max: the bounded cast misses exactly the far ones
+        h = hits_numpy(out["hits"])
+        rmax = np.float32(spec.r_max)
+        assert (ref["key"] >= 0).sum() > 200
+        if clip:
+            assert ((ref["hits"]["tri"] < 0) & ~ref["flags"]["limit"]).sum() > 200
+            assert (h["r"][h["tri"] != 0xFFFFFFFF] < rmax).all()
+        else:
+            assert ((ref["hits"]["tri"] >= 0) & ~(ref["hits"]["t"] < rmax)).sum() > 200
     else:
         assert (ref["key"] >= 0).sum() > 900
 
