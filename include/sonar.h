@@ -282,10 +282,13 @@ sonar_status sonar_batch_update(sonar_batch_t batch, const sonar_batch_item* ite
  * adds noise for all column work units (dynamic work list), one normalises
  * every range row, and the fans are resampled by one launch for the items
  * that share a fan geometry (after refreshing any coordinate table whose
- * geometry changed) and one for the others.  The first call for a given (params, theta, outputs)
- * captures the launches in a CUDA graph; later calls with the same arguments
- * replay it.  Results per item equal sonar_render's for the same item and
- * tile shape (bitwise, in deterministic accumulation). */
+ * geometry changed) and one for the others.  The first call for a given
+ * (params, theta, outputs) captures the launches in a CUDA graph; later calls
+ * with the same arguments replay it.  A call with no sonar_batch_update (and
+ * no re-plan) since the last forward replays a second graph without the two
+ * table launches, whose tables are then current (calls on one batch are
+ * stream-ordered, as for a context).  Results per item equal sonar_render's
+ * for the same item and tile shape (bitwise, in deterministic accumulation). */
 sonar_status sonar_render_batch(sonar_batch_t batch, const sonar_params* params,
                                 const float* d_theta, int32_t n_mat,
                                 const sonar_batch_outputs* out, void* stream);
@@ -320,8 +323,8 @@ sonar_status sonar_render_batch_step(sonar_batch_t batch, const sonar_params* pa
  * grid size, out[3] block size, out[4] graphs captured so far. */
 sonar_status sonar_batch_info(sonar_batch_t batch, int64_t out[5]);
 
-/* Kernel launches per replay: out[0] kernel nodes of the current forward
- * graph, out[1] of the current adjoint graph (0 for a graph not captured yet;
+/* Kernel launches per replay: out[0] kernel nodes of the forward graph replayed
+ * last (with or without the table launches), out[1] of the current adjoint graph (0 for a graph not captured yet;
  * -1 if the graph could not be inspected); the step graph of
  * sonar_render_batch_step holds the kernels of both.  Host only, no
  * synchronisation. */

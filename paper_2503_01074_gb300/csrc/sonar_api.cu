@@ -654,11 +654,17 @@ struct sonar_batch {
     cudaStream_t side = nullptr;      // the adjoint branch of the combined step graph
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraphExec_t fwd = nullptr, bwd = nullptr, step = nullptr;
+    // the forward without the two table kernels (exact-ray sin/cos, fan
+    // coordinates), replayed while the tables are known to be current: no
+    // update or plan since a forward that builds them was enqueued
+    cudaGraphExec_t fwd_lean = nullptr;
+    bool tables_dirty = true;
+    bool lean_last = false;           // the last forward replay was the lean graph
     cudaEvent_t ev[7] = {};           // phase boundaries recorded inside the graphs
     bool ran_fwd = false, ran_bwd = false;
-    std::vector<unsigned char> fwd_key, bwd_key, step_key;
+    std::vector<unsigned char> fwd_key, fwd_lean_key, bwd_key, step_key;
     int graphs = 0;
-    int fwd_kernels = 0, bwd_kernels = 0, step_kernels = 0;   // kernel nodes of the current graphs
+    int fwd_kernels = 0, fwd_lean_kernels = 0, bwd_kernels = 0, step_kernels = 0;   // kernel nodes of the current graphs
 };
 
 namespace {
@@ -692,12 +698,15 @@ void batch_free_device(sonar_batch* b) {
     b->d_rowmax = nullptr; b->d_noised = nullptr; b->d_rowinfo = nullptr; b->d_partials = nullptr;
     b->d_counters = nullptr;
     if (b->fwd) cudaGraphExecDestroy(b->fwd);
+    if (b->fwd_lean) cudaGraphExecDestroy(b->fwd_lean);
     if (b->bwd) cudaGraphExecDestroy(b->bwd);
     if (b->step) cudaGraphExecDestroy(b->step);
-    b->fwd = b->bwd = b->step = nullptr;
+    b->fwd = b->fwd_lean = b->bwd = b->step = nullptr;
     b->fwd_key.clear();
+    b->fwd_lean_key.clear();
     b->bwd_key.clear();
     b->step_key.clear();
+    b->tables_dirty = true;
 }
 
 // Fan pixels sample the same bins with the same weights exactly when these agree.
@@ -1029,7 +1038,7 @@ void append_bytes(std::vector<unsigned char>& v, const T& x) {
 // and noise), part 2 the normalisation and fan, part 0 both.
 sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const float* d_theta, int32_t n_mat,
                                     const sonar_batch_outputs* out, cudaStream_t s, bool events = false,
-                                    int part = 0) {
+                                    int part = 0, bool tables = true) {
     sonar_ctx* ctx = b->ctx;
     const int det = p->accumulate == 0;
     if (part != 2) {
@@ -1038,7 +1047,8 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
             CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
         sonar_hit* hits = out->hits ? out->hits : b->d_hits;   // scratch allocated by the caller, outside capture
         if (events) CU(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal), "cudaEventRecord");
-        CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
+        if (tables)
+            CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
         TraceArgs t{};
         t.sensors = b->d_sens;
         t.scenes = b->d_scenes;
@@ -1085,8 +1095,10 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
         f.polar = out->polar;
         f.fan = out->fan;
         if (b->lut_blocks > 0) {
-            FanLutArgs l{b->d_sens, b->d_lut_map, b->d_luts};
-            CU(launch_fan_lut(l, b->lut_blocks, s), "batch fan table launch");
+            if (tables) {
+                FanLutArgs l{b->d_sens, b->d_lut_map, b->d_luts};
+                CU(launch_fan_lut(l, b->lut_blocks, s), "batch fan table launch");
+            }
             FanGroupArgs g{b->d_sens, b->d_group_map, b->d_members, out->polar, out->fan};
             CU(launch_fan_group(g, b->group_blocks, s), "batch grouped fan launch");
         }
@@ -1132,6 +1144,7 @@ extern "C" sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_it
 
 extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_item* items, int32_t n, void* stream) {
     if (!b) return SONAR_ERR_ARG;
+    b->tables_dirty = true;   // the next forward replays the table kernels (they skip current entries)
     sonar_ctx* ctx = b->ctx;
     sonar_status st = check_items(ctx, items, n);
     if (st) return st;
@@ -1159,8 +1172,9 @@ extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_it
         b->d_scenes = d;
         b->n_scene_table = table.size();
         if (b->fwd) cudaGraphExecDestroy(b->fwd);
+        if (b->fwd_lean) cudaGraphExecDestroy(b->fwd_lean);
         if (b->bwd) cudaGraphExecDestroy(b->bwd);
-        b->fwd = b->bwd = nullptr;
+        b->fwd = b->fwd_lean = b->bwd = nullptr;
     }
     const int slot = b->stage_next;
     b->stage_next ^= 1;
@@ -1230,23 +1244,29 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
     append_bytes(key, d_theta);
     append_bytes(key, n_mat);
     append_bytes(key, *out);
-    if (!b->fwd || key != b->fwd_key) {
-        if (b->fwd) cudaGraphExecDestroy(b->fwd);
-        b->fwd = nullptr;
+    // the full forward while a table may be stale, else the lean one
+    const bool lean = !b->tables_dirty;
+    cudaGraphExec_t& exec = lean ? b->fwd_lean : b->fwd;
+    std::vector<unsigned char>& exec_key = lean ? b->fwd_lean_key : b->fwd_key;
+    if (!exec || key != exec_key) {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
         CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
-        st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap, true);
+        st = batch_forward_launches(b, p, d_theta, n_mat, out, b->cap, true, 0, !lean);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (st != SONAR_OK) { if (g) cudaGraphDestroy(g); return st; }
         CU(e, "graph capture");
-        b->fwd_kernels = kernel_nodes(g);
-        const cudaError_t e2 = cudaGraphInstantiate(&b->fwd, g, 0);
+        (lean ? b->fwd_lean_kernels : b->fwd_kernels) = kernel_nodes(g);
+        const cudaError_t e2 = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
         CU(e2, "graph instantiation");
-        b->fwd_key = key;
+        exec_key = key;
         ++b->graphs;
     }
-    CU(cudaGraphLaunch(b->fwd, s), "graph launch");
+    CU(cudaGraphLaunch(exec, s), "graph launch");
+    b->tables_dirty = false;   // built by this replay, in stream order, if they were stale
+    b->lean_last = lean;
     b->ran_fwd = true;
     return SONAR_OK;
 }
@@ -1442,7 +1462,7 @@ extern "C" sonar_status sonar_batch_info(sonar_batch_t b, int64_t out[5]) {
 
 extern "C" sonar_status sonar_batch_kernels(sonar_batch_t b, int32_t out[2]) {
     if (!b || !out) return SONAR_ERR_ARG;
-    out[0] = b->fwd ? b->fwd_kernels : 0;
+    out[0] = b->lean_last ? (b->fwd_lean ? b->fwd_lean_kernels : 0) : (b->fwd ? b->fwd_kernels : 0);
     out[1] = b->bwd ? b->bwd_kernels : 0;
     return SONAR_OK;
 }

@@ -346,19 +346,27 @@ def test_batch_equals_single_renders(son, tiny, tiny_sid):
             assert torch.equal(v["hits"], single["hits"]), k
             if spec.fan_w:
                 assert torch.equal(v["fan"], single["fan"]), k
-    assert b.info()["graphs"] == 1
-    # new poses through the update path, same graph
+    # the first replay builds the exact-ray and fan tables; the second, with no
+    # update in between, is the forward without the two table kernels
+    assert b.info()["graphs"] == 2
+    k_full, k_lean = None, b.kernels()["forward"]
+    # new poses through the update path: the full forward again (same graph),
+    # then the lean one
     new = [(sid, spec.replace_pose(spec.pos + np.float32(0.3), spec.rot), seed + 1, frame + 1)
            for sid, spec, seed, frame in items]
     b.update(new)
-    b.render(theta, prm)
-    torch.cuda.synchronize()
-    for k, (sid, spec, seed, frame) in enumerate(new):
-        single = son.render(sid, spec, theta, prm, seed, frame, hits=True, fan=True)
-        assert torch.equal(b.view(k)["polar"], single["polar"]), k
-        if spec.fan_w:   # the fan tables were kept (same geometry): still the single render's fan
-            assert torch.equal(b.view(k)["fan"], single["fan"]), k
-    assert b.info()["graphs"] == 1
+    for rep in range(2):
+        b.render(theta, prm)
+        torch.cuda.synchronize()
+        if rep == 0:
+            k_full = b.kernels()["forward"]
+        for k, (sid, spec, seed, frame) in enumerate(new):
+            single = son.render(sid, spec, theta, prm, seed, frame, hits=True, fan=True)
+            assert torch.equal(b.view(k)["polar"], single["polar"]), k
+            if spec.fan_w:   # the fan tables were kept (same geometry): still the single render's fan
+                assert torch.equal(b.view(k)["fan"], single["fan"]), k
+    assert b.info()["graphs"] == 2
+    assert k_lean == k_full - 2           # no sin/cos table and no fan table kernel
     b.close()
 
 
