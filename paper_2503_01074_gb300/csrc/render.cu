@@ -793,8 +793,10 @@ __global__ void __launch_bounds__(256) k_fan_lut(FanLutArgs a) {
 // ties) and c = sum G I~ / m^2.  Mode 1: one warp per range row; mode 2: one
 // block per sensor image.
 __global__ void k_adj_rows(const SensorDev* sensors, const int32_t* row_map, SensorDev one, int n_sensors,
-                           int64_t total, int mode, const float* noised, const float* grad, RowInfo* info) {
+                           int64_t total, int mode, const float* noised, const float* grad, RowInfo* info,
+                           int32_t* zero_word) {
     const int lane = threadIdx.x & 31;
+    if (zero_word && blockIdx.x == 0 && threadIdx.x == 0) *zero_word = 0;   // the gather's work counter
     __shared__ float s_m[32];
     __shared__ int s_a[32];
     __shared__ ff s_d[32];
@@ -1111,14 +1113,15 @@ cudaError_t launch_fan_lut(const FanLutArgs& a, int blocks, cudaStream_t st) {
 
 cudaError_t launch_adj_rows(const SensorDev* sensors, const int32_t* row_map, const SensorDev& one, int n_sensors,
                             int64_t total_groups, int normalise, const float* noised,
-                            const float* grad, RowInfo* info, cudaStream_t st) {
+                            const float* grad, RowInfo* info, int32_t* zero_word, cudaStream_t st) {
     if (normalise == 1) {
         const int64_t threads = total_groups * 32;
         k_adj_rows<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sensors, row_map, one, n_sensors,
-                                                                      total_groups, 1, noised, grad, info);
+                                                                      total_groups, 1, noised, grad, info,
+                                                                      zero_word);
     } else if (normalise == 2) {
         k_adj_rows<<<(unsigned)total_groups, 1024, 0, st>>>(sensors, row_map, one, n_sensors, total_groups, 2,
-                                                            noised, grad, info);
+                                                            noised, grad, info, zero_word);
     }
     return cudaGetLastError();
 }

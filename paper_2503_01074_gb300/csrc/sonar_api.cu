@@ -573,7 +573,7 @@ extern "C" sonar_status sonar_render_backward(sonar_ctx_t ctx, int32_t scene_id,
     CU(grow(ctx->partials, sizeof(double) * (size_t)n_units * nq, s), "scratch allocation");
     if (params->normalise != 0)
         CU(launch_adj_rows(nullptr, nullptr, S, 1, groups, params->normalise, d_noised, d_grad_polar,
-                           (RowInfo*)ctx->rowinfo.p, s),
+                           (RowInfo*)ctx->rowinfo.p, nullptr, s),
            "adjoint row launch");
     AdjArgs a{};
     a.n_units = n_units;
@@ -1042,7 +1042,6 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
     sonar_ctx* ctx = b->ctx;
     const int det = p->accumulate == 0;
     if (part != 2) {
-        CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
         if (p->normalise == 2)
             CU(cudaMemsetAsync(b->d_rowmax, 0, sizeof(uint32_t) * b->total_rows, s), "cudaMemsetAsync");
         sonar_hit* hits = out->hits ? out->hits : b->d_hits;   // scratch allocated by the caller, outside capture
@@ -1057,6 +1056,7 @@ sonar_status batch_forward_launches(sonar_batch* b, const sonar_params* p, const
         t.params = *p;
         t.hits = hits;
         t.err = ctx->d_err;
+        t.zero_word = b->d_counters;   // the binning's work counter, cleared for the launch after
         CU(launch_trace(t, b->trace_prefix.back(), b->trace_occ, s), "batch trace launch");
         if (events) CU(cudaEventRecordWithFlags(b->ev[6], s, cudaEventRecordExternal), "cudaEventRecord");
         BinArgs a{};
@@ -1277,7 +1277,10 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
                                      const float* grad, const float* noised, const sonar_hit* hits, float* dtheta,
                                      cudaStream_t s, bool events = false) {
     sonar_ctx* ctx = b->ctx;
-    CU(cudaMemsetAsync(b->d_counters, 0, sizeof(int32_t) * 4, s), "cudaMemsetAsync");
+    // the gather's work counter is cleared by a kernel before it (the ray cast
+    // of recomputed records, the row terms), else by a memset
+    if (hits && p->normalise == 0)
+        CU(cudaMemsetAsync(b->d_counters + 1, 0, sizeof(int32_t), s), "cudaMemsetAsync");
     if (events) CU(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal), "cudaEventRecord");
     if (!hits) {   // recompute the hit records with the ray-cast kernel into the batch scratch
         CU(launch_trig(b->d_sens, SensorDev{}, (int)b->items.size(), b->max_angles, s), "batch trig launch");
@@ -1289,13 +1292,14 @@ sonar_status batch_backward_launches(sonar_batch* b, const sonar_params* p, cons
         tr.params = *p;
         tr.hits = b->d_hits;
         tr.err = ctx->d_err;
+        tr.zero_word = b->d_counters + 1;
         CU(launch_trace(tr, b->trace_prefix.back(), b->trace_occ, s), "batch trace launch");
         hits = b->d_hits;
     }
     if (p->normalise != 0)
         CU(launch_adj_rows(b->d_sens, b->d_row_map, SensorDev{}, (int)b->items.size(),
                            p->normalise == 1 ? b->total_rows : (int64_t)b->items.size(), p->normalise, noised,
-                           grad, b->d_rowinfo, s),
+                           grad, b->d_rowinfo, b->d_counters + 1, s),
            "batch adjoint rows");
     if (events) CU(cudaEventRecordWithFlags(b->ev[4], s, cudaEventRecordExternal), "cudaEventRecord");
     AdjArgs a{};

@@ -49,7 +49,7 @@ cudaError_t launch_fan_lut(const FanLutArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_fan_group(const FanGroupArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_adj_rows(const SensorDev* sensors, const int32_t* row_map, const SensorDev& one, int n_sensors,
                             int64_t total_groups, int normalise, const float* noised,
-                            const float* grad, RowInfo* info, cudaStream_t st);
+                            const float* grad, RowInfo* info, int32_t* zero_word, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgs& a, int grid, int block, size_t smem, float* dtheta, cudaStream_t st);
 int adjoint_blocks_per_sm(int block, size_t smem);
 cudaError_t launch_stats(const SensorDev& s, const SceneDev& sc, const sonar_params& p,

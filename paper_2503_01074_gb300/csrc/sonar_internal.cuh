@@ -229,6 +229,7 @@ struct TraceArgs {
     sonar_hit* hits;            // written unless counting (the caller's buffer or scratch)
     uint32_t* err;
     TraceCounters tc;           // counting launches only
+    int32_t* zero_word;         // cleared for the launch after this one (a work counter), or nullptr
 };
 
 // Binning and noise over column-tile work units.

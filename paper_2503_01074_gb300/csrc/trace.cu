@@ -217,6 +217,7 @@ template <int MINB, bool STATS, int W>
 __global__ void __launch_bounds__(32, MINB) k_trace(TraceArgs a) {
     __shared__ SensorDev S;
     __shared__ SceneDev SC;
+    if (a.zero_word && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_word = 0;   // read by the next launch only
     int tile;
     if (a.sensors) {
         // the warp copies the sensor and scene descriptors word by word, both at
