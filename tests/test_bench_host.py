@@ -39,3 +39,11 @@ def test_source_hash_covers_the_ray_cast_sources():
     assert all(os.path.exists(os.path.join(ROOT, p)) for p in bench.RAY_CAST_SOURCES)
     assert any(p.endswith("trace.cu") for p in bench.RAY_CAST_SOURCES)
     assert len(bench.ray_cast_sources_sha()) == 16
+
+
+def test_config_names_the_workload_and_the_cast_bound():
+    full = bench.arm_config(64, 32768, 1)
+    small = bench.arm_config(8, 32768, 1, small=True)
+    assert full["workload"] == bench.WORKLOAD and "2,100,512 tris" in full["workload"]
+    assert small["workload"] == bench.SMALL_WORKLOAD and "527,648 tris" in small["workload"]
+    assert "r_max" in full["cast"] and full["frames_per_step"] == 64 and full["parallelism"] == "dp1"
