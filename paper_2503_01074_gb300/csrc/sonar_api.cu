@@ -656,9 +656,10 @@ struct sonar_batch {
     cudaGraphExec_t fwd = nullptr, bwd = nullptr, step = nullptr;
     // the forward without the two table kernels (exact-ray sin/cos, fan
     // coordinates), replayed while the tables are known to be current: no
-    // update or plan since a forward that builds them was enqueued
+    // update or plan since a forward that built them was enqueued (the fan
+    // coordinates are built only by a forward that writes fans)
     cudaGraphExec_t fwd_lean = nullptr;
-    bool tables_dirty = true;
+    bool trig_current = false, lut_current = false;
     bool lean_last = false;           // the last forward replay was the lean graph
     cudaEvent_t ev[7] = {};           // phase boundaries recorded inside the graphs
     bool ran_fwd = false, ran_bwd = false;
@@ -706,7 +707,7 @@ void batch_free_device(sonar_batch* b) {
     b->fwd_lean_key.clear();
     b->bwd_key.clear();
     b->step_key.clear();
-    b->tables_dirty = true;
+    b->trig_current = b->lut_current = false;
 }
 
 // Fan pixels sample the same bins with the same weights exactly when these agree.
@@ -1144,7 +1145,7 @@ extern "C" sonar_status sonar_batch_create(sonar_ctx_t ctx, const sonar_batch_it
 
 extern "C" sonar_status sonar_batch_update(sonar_batch_t b, const sonar_batch_item* items, int32_t n, void* stream) {
     if (!b) return SONAR_ERR_ARG;
-    b->tables_dirty = true;   // the next forward replays the table kernels (they skip current entries)
+    b->trig_current = b->lut_current = false;   // the next forward replays the table kernels (they skip current entries)
     sonar_ctx* ctx = b->ctx;
     sonar_status st = check_items(ctx, items, n);
     if (st) return st;
@@ -1244,8 +1245,8 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
     append_bytes(key, d_theta);
     append_bytes(key, n_mat);
     append_bytes(key, *out);
-    // the full forward while a table may be stale, else the lean one
-    const bool lean = !b->tables_dirty;
+    // the full forward while a table it reads may be stale, else the lean one
+    const bool lean = b->trig_current && (b->lut_current || !out->fan || b->lut_blocks == 0);
     cudaGraphExec_t& exec = lean ? b->fwd_lean : b->fwd;
     std::vector<unsigned char>& exec_key = lean ? b->fwd_lean_key : b->fwd_key;
     if (!exec || key != exec_key) {
@@ -1265,7 +1266,8 @@ extern "C" sonar_status sonar_render_batch(sonar_batch_t b, const sonar_params* 
         ++b->graphs;
     }
     CU(cudaGraphLaunch(exec, s), "graph launch");
-    b->tables_dirty = false;   // built by this replay, in stream order, if they were stale
+    b->trig_current = true;   // built by this replay, in stream order, if they were stale
+    if (out->fan) b->lut_current = true;
     b->lean_last = lean;
     b->ran_fwd = true;
     return SONAR_OK;

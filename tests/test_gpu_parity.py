@@ -414,6 +414,32 @@ def test_batch_shared_fan_tables(son, tiny, tiny_sid):
     b.close()
 
 
+def test_batch_fans_after_renders_without_fans(son, tiny, tiny_sid):
+    """A batch rendered without fans and then with them, no update between: the
+    shared fan coordinate table is built by the first forward that writes
+    fans (the replays without the table kernels wait for it), so every fan
+    equals a single render's."""
+    mesh, mu = tiny
+    theta = son.theta(0.05, 1.0, mu)
+    prm = RenderParams()
+    base = S.sensor_tiny(40.0)
+    base.fan_w, base.fan_h = 160, 96
+    items = [(tiny_sid, base.replace_pose((0.2 * k, 0.1 * k, 0.0), S.pose_matrix(0.05 * k, math.radians(40.0))),
+              5, k) for k in range(4)]
+    b = son.batch(items)
+    b.render(theta, prm, fan=False)
+    b.render(theta, prm, fan=False)
+    for rep in range(2):
+        b.render(theta, prm, fan=True)
+        torch.cuda.synchronize()
+        for k, (sid, spec, seed, frame) in enumerate(items):
+            one = son.render(sid, spec, theta, prm, seed, frame, fan=True)
+            assert torch.equal(one["fan"], b.view(k)["fan"]), (rep, k)
+            assert float(one["fan"].abs().sum()) > 0.0
+    st, bits = son.check()
+    assert st == 0 and bits == 0
+    b.close()
+
 def test_batch_backward_equals_sum_of_singles(son, tiny, tiny_sid):
     mesh, mu = tiny
     items = batch_items(son, tiny, tiny_sid)
